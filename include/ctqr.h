@@ -1,0 +1,214 @@
+/*
+ * ctqr.h -- C ABI of the GB300 (sm_103a) library for QR-based algebraic CT
+ * reconstruction (Chillaron, Quintana-Orti, Vidal, Verdu: "Computed tomography
+ * medical image reconstruction on affordable equipment by using out-of-core
+ * techniques", arXiv 1907.01891).
+ *
+ * The method models CT as the linear system A X = B (Eq. (sistema)): A is the
+ * M x N system matrix, a_ij the contribution of ray i to pixel j; B holds one
+ * sinogram per column; X one image per column.  It factors A = QR once
+ * (Eq. (QR)) and reconstructs every slice as X = R^{-1} (Q^T B) (Eq. (qr1)),
+ * applying Q^T implicitly through the Householder reflectors and solving with
+ * R by backward substitution (Sec. II-C-4).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are column-major: element (i, j) of a matrix with leading
+ *    dimension ld is at ptr[i + j*ld], ld >= rows.  Base pointers must be
+ *    16-byte aligned.  All matrix pointers are DEVICE pointers owned by the
+ *    caller unless stated otherwise.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work on that stream and returns;
+ *    argument errors are returned immediately.  Errors found on the device
+ *    (rank deficiency, non-finite data, a wait that timed out) are written to
+ *    a device status word and reported by ct_factor_status() or by the
+ *    synchronous ct_reconstruct_batch().
+ *  - No entry point falls back to the CPU.
+ */
+#ifndef CTQR_H
+#define CTQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CT_OK = 0,
+  CT_ERR_INVALID = 1,     /* bad argument (size, pointer, alignment, enum)   */
+  CT_ERR_NOMEM = 2,       /* device allocation failed                          */
+  CT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed              */
+  CT_ERR_RANK = 4,        /* R is numerically rank deficient                   */
+  CT_ERR_NONFINITE = 5,   /* NaN or Inf met in the data                        */
+  CT_ERR_NOCONVERGE = 6,  /* refinement hit its iteration cap                  */
+  CT_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up                */
+  CT_ERR_UNSUPPORTED = 8  /* valid request this build does not implement       */
+} ct_status;
+
+/* Element type of a caller-owned matrix. */
+typedef enum { CT_F64 = 0, CT_F32 = 1 } ct_dtype;
+
+/* Arithmetic of the factorization's trailing updates (the dense contraction
+ * C <- C - V T^T V^T C).  Panels, reflector norms and T factors are always
+ * computed in FP64.  CT_PREC_F64: plain FP64 everywhere, factor stored in FP64.
+ * CT_PREC_F32: factor stored in FP32, updates in FP32 (CUDA cores).
+ * CT_PREC_TF32: factor stored in FP32, updates on the tensor cores in TF32
+ * with FP32 accumulation. */
+typedef enum { CT_PREC_F64 = 0, CT_PREC_F32 = 1, CT_PREC_TF32 = 2 } ct_prec;
+
+/* Scanner geometry (Sec. II-A and Table (scanner) describe the paper's fan-beam
+ * scanner; this struct parameterises parallel and fan beams).
+ *  Image: nx*ny square pixels of side `pixel`, centred on the origin; pixel
+ *    j = iy*nx + ix covers [x0 + ix*pixel, x0 + (ix+1)*pixel) x [y0 + iy*pixel,
+ *    y0 + (iy+1)*pixel) with x0 = -nx*pixel/2, y0 = -ny*pixel/2 (half-open, so a
+ *    ray lying on a grid line belongs to the pixels above / right of it).
+ *  Rays: ray = view*n_bins + bin; view v has angle a_v = angle0 +
+ *    v*angle_span/n_views; c_b = bin - (n_bins-1)/2.
+ *  beam 0 (parallel): offset s = c_b*det_span/n_bins; the ray passes through
+ *    s*(-sin a_v, cos a_v) with direction (cos a_v, sin a_v).
+ *  beam 1 (equiangular fan): source at src_iso*(cos a_v, sin a_v), fan angle
+ *    g = c_b*det_span/(n_bins-1) (g = 0 if n_bins == 1), direction
+ *    (-cos(a_v+g), -sin(a_v+g)).
+ *  a_ij = length of ray i inside pixel j (parameter length along the unit
+ *  direction). */
+typedef struct {
+  int beam;          /* 0 parallel, 1 fan                                       */
+  int nx, ny;        /* image size in pixels                                    */
+  double pixel;      /* pixel side                                              */
+  int n_views;       /* projections                                             */
+  int n_bins;        /* detector bins per projection                            */
+  double angle0;     /* first view angle (radians)                              */
+  double angle_span; /* views are spread over [angle0, angle0 + angle_span)     */
+  double src_iso;    /* fan: source-to-isocentre distance                       */
+  double det_span;   /* parallel: detector width; fan: total fan angle (rad)    */
+} ct_geometry;
+
+/* Options of ct_qr_factor.  NULL selects the defaults. */
+typedef struct {
+  int nb;        /* panel width, 1..64 (0 = choose)                             */
+  int in_place;  /* 1: overwrite the caller's A with the factor and borrow it  */
+                 /*    (A must then have the factor's storage type and stay    */
+                 /*    alive until ct_factor_destroy); 0: copy A               */
+} ct_qr_opts;
+
+/* Opaque factorization: reflectors V and R (in the factored matrix), tau, and
+ * the per-panel T factors (Q_panel = I - V T V^T), all in device memory owned
+ * by the factor until ct_factor_destroy. */
+typedef struct ct_factor ct_factor;
+
+/* Options of ct_reconstruct_batch's FP64 refinement.  NULL = defaults. */
+typedef struct {
+  int max_iter;    /* iteration cap (default 30)                               */
+  double tol;      /* stop when every column has ||dx_c|| <= tol*||x_c||        */
+                   /* (default 1e-12)                                          */
+} ct_refine_opts;
+
+/* Optional report of ct_reconstruct_batch. */
+typedef struct {
+  int iterations;        /* refinement corrections applied after the first solve */
+  double last_update;    /* max_c ||dx_c|| / ||x_c|| of the last correction      */
+  double residual;       /* ||B - A X||_F / ||B||_F before the last correction   */
+  double ms_total;       /* wall time of the call (host clock, synchronised)     */
+} ct_report;
+
+/* Human-readable name of a status code (static storage). */
+const char* ct_status_str(ct_status s);
+
+/* Library build/version string (static storage). */
+const char* ct_version(void);
+
+/* Rows and columns of the system ct_build_system writes:
+ * m = n_views*n_bins (+ nx*ny when lambda > 0), n = nx*ny.
+ * Returns CT_ERR_INVALID for a malformed geometry. */
+ct_status ct_system_size(const ct_geometry* geom, double lambda, int64_t* m,
+                         int64_t* n);
+
+/* Build the dense system matrix A (Eq. (sistema); a_ij = length of ray i in
+ * pixel j) by Siddon-style ray traversal, written in `dtype` into the caller's
+ * m x n column-major device buffer A (leading dimension lda >= m, m, n from
+ * ct_system_size).  Every entry of the m x n block is written (zeros included).
+ * lambda > 0 appends lambda*I below the ray rows (Tikhonov stacking [A; lambda I]).
+ * Lengths are computed in FP64; CT_F32 stores them rounded. */
+ct_status ct_build_system(const ct_geometry* geom, ct_dtype dtype, double lambda,
+                          void* A, int64_t lda, void* stream);
+
+/* Householder QR A = QR (Eq. (QR)) of the m x n (m >= n) matrix A, blocked in
+ * panels of nb columns: per panel an FP64 panel factorization (reflector
+ * generation, norms) and its T factor (the paper's "S factor" of
+ * Compute_dense_QR, Sec. II-C-3), then the trailing update of the rest
+ * (Apply_left_Qt_of_dense_QR) in the arithmetic `prec` selects.
+ * A has type `dtype` (CT_F64 or CT_F32), leading dimension lda.  On success
+ * *out receives a new factor; A is read only (unless opts->in_place).
+ * Rank deficiency (|R_ii| <= max(m,n)*eps*max|R_ii|) and non-finite input are
+ * reported by ct_factor_status(). */
+ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n,
+                       int64_t lda, ct_prec prec, const ct_qr_opts* opts,
+                       ct_factor** out, void* stream);
+
+/* Shape and arithmetic of a factor (any pointer may be NULL). */
+ct_status ct_factor_info(const ct_factor* f, int64_t* m, int64_t* n, int* nb,
+                         ct_prec* prec);
+
+/* Device pointers of the factored matrix (R on and above the diagonal, the
+ * reflectors below it, element type *dtype, leading dimension *ld) and of tau
+ * (FP64, n entries).  The memory stays owned by the factor. */
+ct_status ct_factor_data(const ct_factor* f, const void** F, ct_dtype* dtype,
+                         int64_t* ld, const double** tau);
+
+/* Copy the factored matrix (R on and above the diagonal, the reflectors' v
+ * below it, v_0 = 1 implicit) into the caller's m x n device buffer F_out
+ * (element type = the factor's storage type from ct_factor_data, leading
+ * dimension ld_out >= m) and tau into the caller's n-element FP64 device
+ * buffer tau_out (either output may be NULL).  Asynchronous on `stream`. */
+ct_status ct_factor_copy(const ct_factor* f, void* F_out, int64_t ld_out, double* tau_out,
+                         void* stream);
+
+/* Synchronise `stream` and return the device status recorded by the work of
+ * this factor so far (CT_OK, CT_ERR_RANK, CT_ERR_NONFINITE, CT_ERR_TIMEOUT). */
+ct_status ct_factor_status(const ct_factor* f, void* stream);
+
+/* B <- Q^T B in place for the m x k FP64 device matrix B (ldb >= m): the first
+ * sub-step of X = R^{-1}(Q^T B) (Eq. (qr1)), applying each panel's block
+ * reflector I - V T^T V^T in factorization order (the Apply_left_Qt tasks of
+ * the solve, Sec. II-C-4).  k may be 0 (no-op). */
+ct_status ct_apply_qt(const ct_factor* f, double* B, int64_t ldb, int64_t k,
+                      void* stream);
+
+/* B[0:n, 0:k] <- R^{-1} B[0:n, 0:k] in place (FP64): backward substitution
+ * with the factor's upper triangular R, by blocks: a triangular solve of each
+ * diagonal block (Trsm_lunn) followed by the update of the blocks above it
+ * (Gemm_nn_mo), Sec. II-C-4.  ldb >= n. */
+ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k,
+                        void* stream);
+
+/* X = R^{-1} (Q^T B)[0:n] for k slices (Eq. (qr1)): B is m x k (ldb >= m,
+ * read only), X is n x k (ldx >= n), both FP64 device matrices.
+ * Without A (A == NULL) this is one Q^T application and one back-solve in
+ * FP64 arithmetic with the factor as stored.
+ * With A (the original m x n system matrix, type A_dtype, leading dimension
+ * lda; FP64 for full accuracy) the result is improved by classical iterative
+ * refinement: X_0 = R^{-1}(Q^T B)[0:n]; repeat  Res = B - A X  (FP64),
+ * D = R^{-1}(Q^T Res)[0:n] (in FP32 arithmetic for an FP32-stored factor,
+ * FP64 otherwise), X += D, until every column satisfies ||d_c|| <= tol ||x_c||.
+ * This is how a CT_PREC_F32 / CT_PREC_TF32 factor reaches FP64 accuracy; it
+ * converges to the least-squares solution when B is consistent (B = A X
+ * exactly), otherwise to the solution of a nearby projected problem.
+ * Synchronous: returns once X holds the result, with the factor's device
+ * status, or CT_ERR_NOCONVERGE if the cap was reached (X then holds the last
+ * iterate).  `report` (may be NULL) receives iteration counts and timings. */
+ct_status ct_reconstruct_batch(const ct_factor* f, const void* A,
+                               ct_dtype A_dtype, int64_t lda, const double* B,
+                               int64_t ldb, double* X, int64_t ldx, int64_t k,
+                               const ct_refine_opts* ropts, ct_report* report,
+                               void* stream);
+
+/* Release a factor and its device memory (NULL is a no-op).  Synchronises
+ * nothing: the caller must not destroy a factor whose work is still queued on
+ * a stream it cannot order the free after. */
+void ct_factor_destroy(ct_factor* f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTQR_H */

@@ -1,0 +1,271 @@
+// gemm_simt.cu -- application of a panel's block reflector on the CUDA cores.
+//
+// Q_p^T C = (I - V T V^T)^T C = C - V (T^T (V^T C)): the GPU form of the
+// paper's Apply_left_Qt_of_dense_QR task (Sec. II-C-3), used for the trailing
+// update of the factorization and for Q^T B in the solve.  Three kernels:
+//   1. k_vtc     partial products P_s = V^T C over row chunk s (split-K: V^T C
+//                has a short output (nbp x nc) and a long contraction (mr));
+//   2. k_tw      W' = T^T sum_s P_s, the splits summed in a fixed order so the
+//                result is bitwise reproducible;
+//   3. k_update  C -= V W' (contraction length nbp <= 64).
+// V is the unit lower trapezoid stored below the panel's diagonal: V(r, a) =
+// stored value for r > a, 1 for r == a, 0 above.  The same k_update also
+// serves the triangular solve (dense V = a block column of R).
+// FP64 on GB300 runs at ~1.2 TFLOP/s, so the FP64 instances are bound by the
+// FP64 pipe, not by memory; register tiles of 4 x TN per thread suffice.
+#include "internal.cuh"
+
+namespace ctqr {
+
+constexpr int kBM = 64;   // rows of V^T (reflectors, padded) / rows of a C tile
+constexpr int kBK = 16;   // contraction rows per shared-memory stage
+constexpr int kGT = 256;  // threads
+
+// V(r, a) of a unit-lower trapezoid (mask) or a dense block (!mask).
+template <typename Acc, typename TV>
+__device__ __forceinline__ Acc v_at(const TV* V, int64_t ldv, int64_t r, int a, int64_t rows,
+                                    int cols, bool mask) {
+  if (r >= rows || a >= cols) return (Acc)0;
+  if (mask) {
+    if (r < a) return (Acc)0;
+    if (r == a) return (Acc)1;
+  }
+  return (Acc)V[r + a * ldv];
+}
+
+template <typename TV, typename TC, typename Acc, int BN>
+__global__ void __launch_bounds__(kGT) k_vtc(const TV* __restrict__ V, int64_t ldv, int nbp,
+                                              const TC* __restrict__ C, int64_t ldc, int64_t mr,
+                                              int64_t nc, int64_t chunk, double* __restrict__ part) {
+  constexpr int TN = BN / 16;
+  __shared__ Acc Vs[kBK][kBM + 1];
+  __shared__ Acc Cs[kBK][BN + 1];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int64_t c0 = (int64_t)blockIdx.x * BN;
+  const int64_t rbeg = (int64_t)blockIdx.y * chunk;
+  const int64_t rend = rbeg + chunk < mr ? rbeg + chunk : mr;
+  Acc acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (Acc)0;
+
+  for (int64_t r0 = rbeg; r0 < rend; r0 += kBK) {
+#pragma unroll
+    for (int i = 0; i < kBM * kBK / kGT; ++i) {
+      const int e = tid + kGT * i, a = e / kBK, rr = e % kBK;
+      const int64_t r = r0 + rr;
+      Vs[rr][a] = r < rend ? v_at<Acc>(V, ldv, r, a, mr, nbp, true) : (Acc)0;
+    }
+#pragma unroll
+    for (int i = 0; i < (BN * kBK + kGT - 1) / kGT; ++i) {
+      const int e = tid + kGT * i;
+      if (e < BN * kBK) {
+        const int c = e / kBK, rr = e % kBK;
+        const int64_t r = r0 + rr, cg = c0 + c;
+        Cs[rr][c] = (r < rend && cg < nc) ? (Acc)C[r + cg * ldc] : (Acc)0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      Acc av[4], cv[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) cv[j] = Cs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * cv[j];
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.y * kBM * nc;
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t cg = c0 + tx * TN + j;
+    if (cg < nc)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) out[ty * 4 + i + cg * kBM] = (double)acc[i][j];
+  }
+}
+
+// W'(a, c) = sum_{b <= a} T(b, a) * sum_s P_s(b, c); 32 columns per CTA.
+template <typename Acc>
+__global__ void __launch_bounds__(kGT) k_tw(const double* __restrict__ part, int splits,
+                                            int64_t nc, const double* __restrict__ T, int ldt,
+                                            int nbp, double* __restrict__ W) {
+  __shared__ Acc Ts[kBM][kBM + 1];
+  __shared__ Acc Ss[32][kBM + 1];
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  for (int e = tid; e < kBM * kBM; e += kGT) {
+    const int b = e % kBM, a = e / kBM;  // T(b, a)
+    Ts[a][b] = (b < nbp && a < nbp && b <= a) ? (Acc)T[b + a * ldt] : (Acc)0;
+  }
+  for (int e = tid; e < 32 * kBM; e += kGT) {
+    const int b = e % kBM, c = e / kBM;
+    const int64_t cg = c0 + c;
+    double s = 0.0;
+    if (cg < nc)
+      for (int sp = 0; sp < splits; ++sp) s += part[(size_t)sp * kBM * nc + b + cg * kBM];
+    Ss[c][b] = (Acc)s;
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * kBM; e += kGT) {
+    const int a = e % kBM, c = e / kBM;
+    const int64_t cg = c0 + c;
+    if (cg >= nc) continue;
+    Acc s = (Acc)0;
+    for (int b = 0; b <= a && b < nbp; ++b) s += Ts[a][b] * Ss[c][b];
+    W[a + cg * kBM] = (double)s;
+  }
+}
+
+// C(r, c) -= sum_{a < K} V(r, a) W(a, c); 64 x BN tile per CTA, K <= 64.
+template <typename TV, typename TW, typename TC, typename Acc, int BN>
+__global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_t ldv, int K,
+                                                 bool mask, const TW* __restrict__ W,
+                                                 int64_t ldw, TC* __restrict__ C, int64_t ldc,
+                                                 int64_t mr, int64_t nc) {
+  constexpr int TN = BN / 16;
+  __shared__ Acc Vs[kBK][kBM + 1];
+  __shared__ Acc Ws[kBK][BN + 1];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int64_t r0 = (int64_t)blockIdx.x * kBM, c0 = (int64_t)blockIdx.y * BN;
+  Acc acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (Acc)0;
+  for (int a0 = 0; a0 < K; a0 += kBK) {
+#pragma unroll
+    for (int i = 0; i < kBM * kBK / kGT; ++i) {
+      const int e = tid + kGT * i, r = e % kBM, aa = e / kBM;
+      Vs[aa][r] = v_at<Acc>(V, ldv, r0 + r, a0 + aa, mr, K, mask);
+    }
+#pragma unroll
+    for (int i = 0; i < (BN * kBK + kGT - 1) / kGT; ++i) {
+      const int e = tid + kGT * i;
+      if (e < BN * kBK) {
+        const int aa = e % kBK, c = e / kBK;
+        const int64_t cg = c0 + c;
+        Ws[aa][c] = (a0 + aa < K && cg < nc) ? (Acc)W[a0 + aa + cg * ldw] : (Acc)0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      Acc av[4], wv[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) wv[j] = Ws[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * wv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t cg = c0 + tx * TN + j;
+    if (cg >= nc) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + ty * 4 + i;
+      if (r < mr) C[r + cg * ldc] = (TC)((Acc)C[r + cg * ldc] - acc[i][j]);
+    }
+  }
+}
+
+size_t reflector_work_elems(int sms, int nbp, int64_t nc) {
+  (void)nbp;
+  return (size_t)kBM * ((size_t)128 * sms + 2 * (size_t)nc) + 64;
+}
+
+namespace {
+
+template <typename TV, typename TC, typename Acc, int BN>
+ct_status run_reflector(const ReflectorArgs& a, double* work, size_t work_elems, int sms,
+                        cudaStream_t s) {
+  const int64_t tiles_n = (a.nc + BN - 1) / BN;
+  int64_t splits = (2 * sms + tiles_n - 1) / tiles_n;
+  const int64_t max_splits = (a.mr + 255) / 256;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  int64_t chunk = (a.mr + splits - 1) / splits;
+  chunk = (chunk + kBK - 1) / kBK * kBK;
+  splits = (a.mr + chunk - 1) / chunk;
+  if (splits < 1) splits = 1;
+  const size_t need = (size_t)splits * kBM * a.nc + (size_t)kBM * a.nc;
+  if (need > work_elems) return CT_ERR_INVALID;
+  double* part = work;
+  double* W = work + (size_t)splits * kBM * a.nc;
+  k_vtc<TV, TC, Acc, BN><<<dim3((unsigned)tiles_n, (unsigned)splits), kGT, 0, s>>>(
+      (const TV*)a.V, a.ldv, a.nbp, (const TC*)a.C, a.ldc, a.mr, a.nc, chunk, part);
+  k_tw<Acc><<<(unsigned)((a.nc + 31) / 32), kGT, 0, s>>>(part, (int)splits, a.nc, a.T, a.ldt, a.nbp, W);
+  k_update<TV, double, TC, Acc, BN><<<dim3((unsigned)((a.mr + kBM - 1) / kBM), (unsigned)tiles_n), kGT, 0, s>>>(
+      (const TV*)a.V, a.ldv, a.nbp, true, W, kBM, (TC*)a.C, a.ldc, a.mr, a.nc);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+template <typename TV, typename TC, typename Acc>
+ct_status run_reflector_bn(const ReflectorArgs& a, double* work, size_t work_elems, int sms,
+                           cudaStream_t s) {
+  if (a.nc <= 16) return run_reflector<TV, TC, Acc, 16>(a, work, work_elems, sms, s);
+  return run_reflector<TV, TC, Acc, 64>(a, work, work_elems, sms, s);
+}
+
+}  // namespace
+
+ct_status apply_block_reflector(const ReflectorArgs& a, double* work, size_t work_elems, int sms,
+                                cudaStream_t s) {
+  if (a.mr <= 0 || a.nc <= 0 || a.nbp <= 0) return CT_OK;
+  if (a.v_f64 && a.c_f64) return run_reflector_bn<double, double, double>(a, work, work_elems, sms, s);
+  if (!a.v_f64 && a.c_f64) return run_reflector_bn<float, double, double>(a, work, work_elems, sms, s);
+  if (!a.v_f64 && !a.c_f64) {
+    if (a.fp32_math) return run_reflector_bn<float, float, float>(a, work, work_elems, sms, s);
+    return run_reflector_bn<float, float, double>(a, work, work_elems, sms, s);
+  }
+  return CT_ERR_UNSUPPORTED;
+}
+
+// C(0:mr, 0:nc) -= V(0:mr, 0:K) W(0:K, 0:nc) with a dense V (the solve's block
+// updates and the residual B - A X).  W and C share one element type; V may be
+// FP64 or FP32; the products accumulate in FP64 unless fp32_math.
+namespace {
+template <typename TV, typename TB, typename Acc>
+void dense_update_t(const void* V, int64_t ldv, int K, const void* W, int64_t ldw, void* C,
+                    int64_t ldc, int64_t mr, int64_t nc, cudaStream_t s) {
+  if (nc <= 16) {
+    const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 15) / 16));
+    k_update<TV, TB, TB, Acc, 16><<<grid, kGT, 0, s>>>((const TV*)V, ldv, K, false, (const TB*)W, ldw,
+                                                       (TB*)C, ldc, mr, nc);
+  } else {
+    const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 63) / 64));
+    k_update<TV, TB, TB, Acc, 64><<<grid, kGT, 0, s>>>((const TV*)V, ldv, K, false, (const TB*)W, ldw,
+                                                       (TB*)C, ldc, mr, nc);
+  }
+}
+}  // namespace
+
+ct_status launch_dense_update(const void* V, bool v_f64, int64_t ldv, int K, const void* W,
+                              int64_t ldw, void* C, bool b_f64, int64_t ldc, int64_t mr, int64_t nc,
+                              cudaStream_t s) {
+  if (mr <= 0 || nc <= 0 || K <= 0) return CT_OK;
+  if (b_f64) {
+    if (v_f64) dense_update_t<double, double, double>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
+    else dense_update_t<float, double, double>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
+  } else {
+    if (v_f64) return CT_ERR_UNSUPPORTED;
+    dense_update_t<float, float, float>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
+  }
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+}  // namespace ctqr

@@ -1,0 +1,165 @@
+// internal.cuh -- declarations shared by the translation units of libctqr.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ctqr.h"
+
+namespace ctqr {
+
+// ---------------------------------------------------------------------------
+// Errors.  Host code returns ct_status; device code records the first error in
+// a status word (int) in device memory with atomicCAS(status, 0, code).
+// ---------------------------------------------------------------------------
+#define CT_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t e__ = (expr);                               \
+    if (e__ != cudaSuccess) {                               \
+      ctqr::note_cuda_error(e__, #expr, __FILE__, __LINE__); \
+      return e__ == cudaErrorMemoryAllocation ? CT_ERR_NOMEM : CT_ERR_CUDA; \
+    }                                                       \
+  } while (0)
+
+#define CT_LAUNCH_CHECK() CT_CUDA_TRY(cudaGetLastError())
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device-side failure recording (first error wins).
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *(const volatile int*)p;
+}
+
+// Bounded grid-wide barrier for kernels launched cooperatively (all CTAs
+// co-resident).  `counter` is a 64-bit arrival counter zeroed before the
+// launch; the barrier round r completes when the counter reaches
+// (r+1)*nblocks.  Each waiting CTA spins at most `limit_ns` nanoseconds; on
+// timeout it records CT_ERR_TIMEOUT and returns false, and a CTA that sees
+// another CTA's error also returns false, so every CTA leaves in bounded time.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsigned nblocks,
+                                             int* status, uint64_t limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    unsigned long long arrival = atomicAdd(counter, 1ull);
+    unsigned long long target = (arrival / nblocks + 1ull) * nblocks;
+    uint64_t t0 = globaltimer_ns();
+    while (ld_acquire_u64(counter) < target) {
+      if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > limit_ns) { set_status(status, CT_ERR_TIMEOUT); ok = 0; break; }
+      __nanosleep(20);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
+
+// ---------------------------------------------------------------------------
+// Device properties cached per process (device 0 of the current context).
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  int smem_optin = 0;
+};
+ct_status device_info(DeviceInfo* out);
+
+// ---------------------------------------------------------------------------
+// The factor.
+// ---------------------------------------------------------------------------
+}  // namespace ctqr
+
+struct ct_factor {
+  int64_t m = 0, n = 0, ld = 0;
+  int nb = 0;
+  ct_prec prec = CT_PREC_F64;
+  ct_dtype store = CT_F64;      // element type of F (FP64 for plain, FP32 otherwise)
+  void* F = nullptr;            // factored matrix (R above, V below the diagonal)
+  bool owns_F = true;
+  double* tau = nullptr;        // n reflector scalars
+  double* T = nullptr;          // npanels blocks of nb x nb (column-major, upper)
+  int* status = nullptr;        // device status word
+  unsigned long long* barrier = nullptr;  // grid-barrier counter
+  double* partials = nullptr;   // panel-kernel reduction scratch
+  size_t partials_elems = 0;
+  int device = 0;
+};
+
+namespace ctqr {
+
+int64_t npanels(const ct_factor* f);
+
+// ---- system matrix (siddon.cu) --------------------------------------------
+ct_status launch_build_system(const ct_geometry* g, ct_dtype dtype, double lambda, void* A,
+                              int64_t lda, int64_t m, int64_t n, cudaStream_t s);
+
+// ---- panel factorization (qr_panel.cu) ------------------------------------
+// Factor the panel F[j0:m, j0:j0+nbp] in FP64, write V/R back in the storage
+// type, tau[j0:j0+nbp] and the nbp x nbp upper T factor (ldt = nb).
+ct_status launch_panel(ct_factor* f, int64_t j0, int nbp, double* T, cudaStream_t s);
+size_t panel_partials_elems(int sms, int nb);
+
+// ---- block-reflector application (gemm_simt.cu) ---------------------------
+// C <- (I - V T V^T)^T C = C - V T^T V^T C for the mr x nc matrix C (leading
+// dimension ldc, type of C given by c_f64), V = unit lower trapezoid of the
+// panel at Fp (leading dimension ldf, storage type given by v_f64), nbp
+// reflectors, T upper nbp x nbp (leading dimension ldt).  Uses `work`
+// (at least reflector_work_elems(...) doubles).
+struct ReflectorArgs {
+  const void* V; bool v_f64; int64_t ldv;
+  const double* T; int ldt;
+  int nbp;
+  void* C; bool c_f64; int64_t ldc;
+  int64_t mr, nc;
+  bool fp32_math;  // accumulate in FP32 (mixed factor) instead of FP64
+};
+size_t reflector_work_elems(int sms, int nbp, int64_t nc);
+ct_status apply_block_reflector(const ReflectorArgs& a, double* work, size_t work_elems,
+                                int sms, cudaStream_t s);
+
+// ---- triangular solve (trsm.cu) -------------------------------------------
+ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k,
+                      cudaStream_t s);
+ct_status launch_dense_update(const void* V, bool v_f64, int64_t ldv, int K, const void* W,
+                              int64_t ldw, void* C, bool b_f64, int64_t ldc, int64_t mr, int64_t nc,
+                              cudaStream_t s);
+int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di);
+ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
+                             cudaStream_t s);
+ct_status launch_rank_check(ct_factor* f, cudaStream_t s);
+
+// ---- utilities (util.cu) ---------------------------------------------------
+ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,
+                             int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
+// Per-column reductions and updates used by the refinement (refine.cu).
+ct_status launch_col_norms2(const double* X, int64_t ldx, int64_t rows, int64_t k, double* out,
+                            cudaStream_t s);
+// X[0:rows, 0:k] += D; dnorm2[c] = ||D_c||^2, xnorm2[c] = ||X_c||^2 afterwards.
+ct_status launch_add_f32_to_f64(const float* D, int64_t ldd, double* X, int64_t ldx, int64_t rows,
+                                int64_t k, double* dnorm2, double* xnorm2, cudaStream_t s);
+ct_status launch_add_f64_to_f64(const double* D, int64_t ldd, double* X, int64_t ldx, int64_t rows,
+                                int64_t k, double* dnorm2, double* xnorm2, cudaStream_t s);
+
+}  // namespace ctqr

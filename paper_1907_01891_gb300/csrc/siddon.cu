@@ -1,0 +1,149 @@
+// siddon.cu -- dense system matrix A of Eq. (sistema): a_ij = length of ray i
+// inside pixel j (Sec. II-A; the paper does not say how A is built, so this
+// follows Siddon's ray traversal).  Compiled with -fmad=false so that every
+// crossing parameter is the plain rounded sequence (line - p)/d.
+//
+// Work split: the m x n block is first zero-filled by a bandwidth-bound kernel
+// (16-byte stores, grid a multiple of the SM count); then one thread per ray
+// walks the grid lines it crosses, in order of the ray parameter t, and
+// scatters the nonzero lengths (at most nx+ny per ray).  A ray only ever
+// touches its own row, so the scatter needs no atomics.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace ctqr {
+namespace {
+
+struct Geo {
+  int beam, nx, ny, n_views, n_bins;
+  double pixel, angle0, angle_span, src_iso, det_span, x0, y0;
+};
+
+__device__ __forceinline__ void ray_of(const Geo& g, int64_t ray, double& px, double& py,
+                                       double& dx, double& dy) {
+  const int v = (int)(ray / g.n_bins), b = (int)(ray % g.n_bins);
+  const double ang = g.angle0 + (double)v * g.angle_span / (double)g.n_views;
+  const double c = (double)b - 0.5 * (double)(g.n_bins - 1);
+  if (g.beam == 0) {
+    const double s = c * (g.det_span / (double)g.n_bins);
+    dx = cos(ang);
+    dy = sin(ang);
+    px = -s * dy;
+    py = s * dx;
+  } else {
+    const double gam = g.n_bins > 1 ? c * (g.det_span / (double)(g.n_bins - 1)) : 0.0;
+    px = g.src_iso * cos(ang);
+    py = g.src_iso * sin(ang);
+    dx = -cos(ang + gam);
+    dy = -sin(ang + gam);
+  }
+}
+
+// Grid line k along one axis: lo + k*pixel.
+__device__ __forceinline__ double line(double lo, int k, double pixel) { return lo + (double)k * pixel; }
+
+// Intersect [t0, t1] with {t : lo <= p + t d < hi} (half-open cell).
+__device__ __forceinline__ void clip(double p, double d, double lo, double hi, double& t0, double& t1) {
+  if (d == 0.0) {
+    if (!(p >= lo && p < hi)) { t0 = 1.0; t1 = 0.0; }
+    return;
+  }
+  const double ta = (lo - p) / d, tb = (hi - p) / d;
+  const double tmin = ta < tb ? ta : tb, tmax = ta < tb ? tb : ta;
+  if (tmin > t0) t0 = tmin;
+  if (tmax < t1) t1 = tmax;
+}
+
+// Cell index k with line(k) <= x < line(k+1), clamped to [0, cells-1].
+__device__ __forceinline__ int cell_of(double x, double lo, double pixel, int cells) {
+  int k = (int)floor((x - lo) / pixel);
+  k = k < 0 ? 0 : (k > cells - 1 ? cells - 1 : k);
+  if (k > 0 && x < line(lo, k, pixel)) --k;
+  if (k < cells - 1 && x >= line(lo, k + 1, pixel)) ++k;
+  return k;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_siddon(Geo g, S* __restrict__ A, int64_t lda) {
+  const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  if (ray >= rays) return;
+  double px, py, dx, dy;
+  ray_of(g, ray, px, py, dx, dy);
+  double t0 = -INFINITY, t1 = INFINITY;
+  clip(px, dx, g.x0, line(g.x0, g.nx, g.pixel), t0, t1);
+  clip(py, dy, g.y0, line(g.y0, g.ny, g.pixel), t0, t1);
+  if (!(t1 > t0)) return;  // the ray misses the image: its row stays zero
+
+  // Next grid line to cross along x (index ix, stepping sx) and y.
+  const int sx = dx > 0.0 ? 1 : -1, sy = dy > 0.0 ? 1 : -1;
+  int ix = -1, iy = -1;
+  if (dx != 0.0) {
+    ix = (int)floor((px + t0 * dx - g.x0) / g.pixel) + (sx > 0 ? 0 : 1);
+    ix = ix < 0 ? 0 : (ix > g.nx ? g.nx : ix);
+    while (ix >= 0 && ix <= g.nx && (line(g.x0, ix, g.pixel) - px) / dx <= t0) ix += sx;
+  }
+  if (dy != 0.0) {
+    iy = (int)floor((py + t0 * dy - g.y0) / g.pixel) + (sy > 0 ? 0 : 1);
+    iy = iy < 0 ? 0 : (iy > g.ny ? g.ny : iy);
+    while (iy >= 0 && iy <= g.ny && (line(g.y0, iy, g.pixel) - py) / dy <= t0) iy += sy;
+  }
+  double tcur = t0;
+  const int max_steps = g.nx + g.ny + 4;
+  for (int step = 0; step < max_steps && tcur < t1; ++step) {
+    const double tx = (dx != 0.0 && ix >= 0 && ix <= g.nx) ? (line(g.x0, ix, g.pixel) - px) / dx : INFINITY;
+    const double ty = (dy != 0.0 && iy >= 0 && iy <= g.ny) ? (line(g.y0, iy, g.pixel) - py) / dy : INFINITY;
+    double tn = tx < ty ? tx : ty;
+    if (t1 < tn) tn = t1;
+    if (tn > tcur) {
+      const double tm = 0.5 * (tcur + tn);
+      const int cx = cell_of(px + tm * dx, g.x0, g.pixel, g.nx);
+      const int cy = cell_of(py + tm * dy, g.y0, g.pixel, g.ny);
+      S* dst = A + ray + ((int64_t)cy * g.nx + cx) * lda;
+      *dst = (S)((double)*dst + (tn - tcur));
+    }
+    if (tx <= tn) ix += sx;
+    if (ty <= tn) iy += sy;
+    tcur = tn;
+  }
+}
+
+template <typename S>
+__global__ void k_lambda_rows(S* __restrict__ A, int64_t lda, int64_t row0, int64_t n, double lambda) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) A[row0 + j + j * lda] = (S)lambda;
+}
+
+}  // namespace
+
+ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
+                             cudaStream_t s);
+
+ct_status launch_build_system(const ct_geometry* gg, ct_dtype dtype, double lambda, void* A,
+                              int64_t lda, int64_t m, int64_t n, cudaStream_t s) {
+  Geo g;
+  g.beam = gg->beam; g.nx = gg->nx; g.ny = gg->ny; g.n_views = gg->n_views; g.n_bins = gg->n_bins;
+  g.pixel = gg->pixel; g.angle0 = gg->angle0; g.angle_span = gg->angle_span;
+  g.src_iso = gg->src_iso; g.det_span = gg->det_span;
+  g.x0 = -0.5 * (double)g.nx * g.pixel;
+  g.y0 = -0.5 * (double)g.ny * g.pixel;
+  const size_t elem = dtype == CT_F64 ? 8 : 4;
+  ct_status st = launch_zero_matrix(A, elem, lda, m, n, s);
+  if (st != CT_OK) return st;
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  const unsigned blocks = (unsigned)((rays + 127) / 128);
+  if (dtype == CT_F64) {
+    k_siddon<double><<<blocks, 128, 0, s>>>(g, (double*)A, lda);
+    if (lambda > 0.0)
+      k_lambda_rows<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double*)A, lda, rays, n, lambda);
+  } else {
+    k_siddon<float><<<blocks, 128, 0, s>>>(g, (float*)A, lda);
+    if (lambda > 0.0)
+      k_lambda_rows<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float*)A, lda, rays, n, lambda);
+  }
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+}  // namespace ctqr

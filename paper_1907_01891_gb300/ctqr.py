@@ -1,0 +1,287 @@
+"""Thin ctypes binding of ``libctqr.so`` (the C ABI in ``include/ctqr.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Matrices are torch CUDA tensors in column-major layout (use
+``colmajor()`` to make one); the current torch CUDA stream is passed to every
+call.  There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+CT_OK, CT_ERR_INVALID, CT_ERR_NOMEM, CT_ERR_CUDA, CT_ERR_RANK = 0, 1, 2, 3, 4
+CT_ERR_NONFINITE, CT_ERR_NOCONVERGE, CT_ERR_TIMEOUT, CT_ERR_UNSUPPORTED = 5, 6, 7, 8
+CT_F64, CT_F32 = 0, 1
+
+
+class Prec(enum.IntEnum):
+    F64 = 0
+    F32 = 1
+    TF32 = 2
+
+
+class CtError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_status_name(status)}")
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [
+        ("beam", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("pixel", ctypes.c_double), ("n_views", ctypes.c_int), ("n_bins", ctypes.c_int),
+        ("angle0", ctypes.c_double), ("angle_span", ctypes.c_double),
+        ("src_iso", ctypes.c_double), ("det_span", ctypes.c_double),
+    ]
+
+
+class QrOpts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("in_place", ctypes.c_int)]
+
+
+class RefineOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("last_update", ctypes.c_double),
+                ("residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+
+_lib = None
+
+# Every entry point of include/ctqr.h, with its ctypes signature.
+_VP, _I64, _D, _I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+_P64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "ct_status_str": ([_I], ctypes.c_char_p),
+    "ct_version": ([], ctypes.c_char_p),
+    "ct_system_size": ([ctypes.POINTER(Geometry), _D, _P64, _P64], _I),
+    "ct_build_system": ([ctypes.POINTER(Geometry), _I, _D, _VP, _I64, _VP], _I),
+    "ct_qr_factor": ([_VP, _I, _I64, _I64, _I64, _I, ctypes.POINTER(QrOpts),
+                      ctypes.POINTER(_VP), _VP], _I),
+    "ct_factor_info": ([_VP, _P64, _P64, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "ct_factor_data": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I), _P64, ctypes.POINTER(_VP)], _I),
+    "ct_factor_status": ([_VP, _VP], _I),
+    "ct_factor_copy": ([_VP, _VP, _I64, _VP, _VP], _I),
+    "ct_apply_qt": ([_VP, _VP, _I64, _I64, _VP], _I),
+    "ct_trsm_solve": ([_VP, _VP, _I64, _I64, _VP], _I),
+    "ct_reconstruct_batch": ([_VP, _VP, _I, _I64, _VP, _I64, _VP, _I64, _I64,
+                              ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
+    "ct_factor_destroy": ([_VP], None),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libctqr.so (building it first if needed) and bind every symbol."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libctqr.so not found at {path}; run build() first")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return load().ct_status_str(s).decode()
+    except Exception:  # library not loadable: still give a readable message
+        return f"status {s}"
+
+
+def _check(st: int, what: str) -> None:
+    if st != CT_OK:
+        raise CtError(st, what)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return CT_F64
+    if t.dtype == torch.float32:
+        return CT_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ld(t: torch.Tensor) -> int:
+    """Leading dimension of a column-major 2-D CUDA tensor."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    if t.stride(0) != 1 and t.shape[0] > 1:
+        raise ValueError("expected a column-major tensor (stride(0) == 1); use colmajor()")
+    return max(t.stride(1), t.shape[0], 1) if t.shape[1] > 1 else max(t.shape[0], 1)
+
+
+def colmajor(rows: int, cols: int, dtype=torch.float64, device="cuda", ld: int | None = None,
+             fill=None) -> torch.Tensor:
+    """A rows x cols column-major CUDA tensor (leading dimension ld >= rows)."""
+    ld = rows if ld is None else ld
+    storage = torch.empty((cols, ld), dtype=dtype, device=device)
+    if fill is not None:
+        storage.fill_(fill)  # padding rows included
+    return storage.t()[:rows]
+
+
+def to_colmajor(x, dtype=None, device="cuda") -> torch.Tensor:
+    """Copy a 2-D array (numpy or torch) into a new column-major CUDA tensor."""
+    x = torch.as_tensor(x)
+    if x.dim() == 1:
+        x = x[:, None]
+    t = colmajor(x.shape[0], x.shape[1], dtype=dtype or x.dtype, device=device)
+    t.copy_(x)
+    return t
+
+
+def geometry(g) -> Geometry:
+    """Geometry from an ``inputs.ScanGeometry`` (or anything with the fields)."""
+    return Geometry(g.beam, g.nx, g.ny, g.pixel, g.n_views, g.n_bins, g.angle0, g.angle_span,
+                    g.src_iso, g.det_span)
+
+
+def version() -> str:
+    return load().ct_version().decode()
+
+
+def system_size(geom, lam: float = 0.0) -> tuple[int, int]:
+    m, n = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ct_system_size(ctypes.byref(geometry(geom)), lam, ctypes.byref(m), ctypes.byref(n)),
+           "ct_system_size")
+    return m.value, n.value
+
+
+def build_system(geom, dtype=torch.float64, lam: float = 0.0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Dense system matrix A (m x n, column-major) built on the GPU."""
+    m, n = system_size(geom, lam)
+    A = colmajor(m, n, dtype=dtype) if out is None else out
+    _check(load().ct_build_system(ctypes.byref(geometry(geom)), _dt(A), lam, A.data_ptr(), _ld(A),
+                                  _stream()), "ct_build_system")
+    return A
+
+
+class Factor:
+    """Owning handle of a ``ct_factor``."""
+
+    def __init__(self, handle: int, keep=None):
+        self._h = ctypes.c_void_p(handle)
+        self._keep = keep  # borrowed matrix for in-place factors
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise RuntimeError("factor already destroyed")
+        return self._h
+
+    def info(self):
+        m, n, nb, prec = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(load().ct_factor_info(self.handle, ctypes.byref(m), ctypes.byref(n), ctypes.byref(nb),
+                                     ctypes.byref(prec)), "ct_factor_info")
+        return dict(m=m.value, n=n.value, nb=nb.value, prec=Prec(prec.value))
+
+    def data(self):
+        """(F, tau) as torch views of the factor's device memory (copies)."""
+        F, dt, ld, tau = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_void_p()
+        _check(load().ct_factor_data(self.handle, ctypes.byref(F), ctypes.byref(dt), ctypes.byref(ld),
+                                     ctypes.byref(tau)), "ct_factor_data")
+        inf = self.info()
+        return F.value, dt.value, ld.value, tau.value, inf
+
+    def status(self) -> int:
+        return load().ct_factor_status(self.handle, _stream())
+
+    def destroy(self) -> None:
+        if self._h:
+            load().ct_factor_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def qr_factor(A: torch.Tensor, prec: Prec = Prec.F64, nb: int = 0, in_place: bool = False) -> Factor:
+    m, n = A.shape
+    h = ctypes.c_void_p()
+    opts = QrOpts(nb, 1 if in_place else 0)
+    _check(load().ct_qr_factor(A.data_ptr(), _dt(A), m, n, _ld(A), int(prec), ctypes.byref(opts),
+                               ctypes.byref(h), _stream()), "ct_qr_factor")
+    return Factor(h.value, keep=A if in_place else None)
+
+
+def factor_matrix(f: Factor) -> tuple[torch.Tensor, torch.Tensor]:
+    """Copies of the factored matrix (R on/above, reflectors below the
+    diagonal; the factor's storage type) and of tau (FP64)."""
+    inf = f.info()
+    _, dt, _, _, _ = f.data()
+    dtype = torch.float64 if dt == CT_F64 else torch.float32
+    F = colmajor(inf["m"], inf["n"], dtype=dtype)
+    tau = torch.empty(inf["n"], dtype=torch.float64, device="cuda")
+    _check(load().ct_factor_copy(f.handle, F.data_ptr(), _ld(F), tau.data_ptr(), _stream()),
+           "ct_factor_copy")
+    return F, tau
+
+
+def apply_qt(f: Factor, B: torch.Tensor) -> torch.Tensor:
+    """B <- Q^T B in place (FP64, m x k column-major)."""
+    _check(load().ct_apply_qt(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()), "ct_apply_qt")
+    return B
+
+
+def trsm_solve(f: Factor, B: torch.Tensor) -> torch.Tensor:
+    """B[0:n] <- R^{-1} B[0:n] in place (FP64)."""
+    _check(load().ct_trsm_solve(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()), "ct_trsm_solve")
+    return B
+
+
+@dataclass
+class ReconReport:
+    status: int
+    iterations: int
+    last_update: float
+    residual: float
+    ms_total: float
+
+
+def reconstruct(f: Factor, B: torch.Tensor, A: torch.Tensor | None = None, X: torch.Tensor | None = None,
+                max_iter: int = 0, tol: float = 0.0, check: bool = True):
+    """X = R^{-1}(Q^T B)[0:n], refined with FP64 residuals against A when given.
+    Returns (X, ReconReport)."""
+    inf = f.info()
+    k = B.shape[1]
+    if X is None:
+        X = colmajor(inf["n"], k, dtype=torch.float64)
+    rep = Report()
+    ro = RefineOpts(max_iter, tol)
+    st = load().ct_reconstruct_batch(
+        f.handle, A.data_ptr() if A is not None else None, _dt(A) if A is not None else CT_F64,
+        _ld(A) if A is not None else 0, B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), k,
+        ctypes.byref(ro), ctypes.byref(rep), _stream())
+    if check:
+        _check(st, "ct_reconstruct_batch")
+    return X, ReconReport(st, rep.iterations, rep.last_update, rep.residual, rep.ms_total)

@@ -1,0 +1,229 @@
+"""GPU vs oracle parity through the C ABI (paper Eq. (sistema), (QR), (qr1)).
+
+Sizes span several 64-column panels and 64-row tiles with ragged tails; the
+oracle computes the same quantities from the same seeded inputs.
+Tolerances: the reconstructions X must match the oracle to a relative error of
+1e-10 (the accuracy target for the plain and refined paths); the factors
+R, V, tau and Q^T B, which a backward-stable QR perturbs by O(kappa * eps),
+are held to 1e-11 relative to the largest entry; the system matrix A, whose
+entries both sides compute with the same FP64 expressions (up to the last bit
+of sin/cos), to 1e-12 absolute.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1907_01891_gb300 import ctqr
+from paper_1907_01891_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _np(t: torch.Tensor) -> np.ndarray:
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _og(g):
+    return O.Geometry(*g.as_tuple())
+
+
+# ---------------------------------------------------------------- system matrix
+@pytest.mark.parametrize("geom", [I.CONFIG1["geom"], I.fan_geometry(24, 30, 37),
+                                  I.parallel_geometry(20, 13, 29, pixel=0.37),
+                                  I.ScanGeometry(0, 8, 8, 1.0, 2, 9, 0.0, np.pi, 0.0, 8.1)],
+                         ids=["config1", "fan24", "par20_pix037", "axis_aligned"])
+def test_system_matrix_matches_oracle(geom):
+    A = ctqr.build_system(geom, torch.float64)
+    ref = O.system_matrix(_og(geom))
+    got = _np(A)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= 1e-12 * geom.pixel
+    assert ((got != 0) == (ref != 0)).mean() > 0.9999
+
+
+def test_system_matrix_fp32_and_lambda_rows():
+    geom = I.fan_geometry(16, 20, 25)
+    lam = 1e-3
+    A32 = _np(ctqr.build_system(geom, torch.float32, lam=lam))
+    ref = O.system_matrix(_og(geom))
+    m = geom.m
+    assert A32.dtype == np.float32
+    assert np.abs(A32[:m] - ref.astype(np.float32)).max() <= 1e-6
+    assert np.array_equal(A32[m:], (lam * np.eye(geom.n)).astype(np.float32))
+
+
+def test_system_matrix_respects_leading_dimension():
+    geom = I.parallel_geometry(8, 5, 11)
+    A = ctqr.colmajor(geom.m, geom.n, torch.float64, ld=geom.m + 13, fill=7.0)
+    ctqr.build_system(geom, torch.float64, out=A)
+    assert np.abs(_np(A) - O.system_matrix(_og(geom))).max() <= 1e-12
+    storage = A.as_strided((geom.m + 13, geom.n), (1, geom.m + 13))
+    pad = _np(storage)[geom.m:]
+    assert (pad == 7.0).all(), "rows beyond m must not be touched"
+
+
+# ---------------------------------------------------------------- factorization
+SHAPES = [(1, 1), (7, 3), (64, 64), (130, 65), (517, 203), (1000, 129), (2700, 1024)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_qr_factor_matches_oracle(shape):
+    m, n = shape
+    A = I.random_matrix(m, n, seed=m + 7 * n)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A))
+    assert f.status() == ctqr.CT_OK
+    F, tau = ctqr.factor_matrix(f)
+    F, tau = _np(F), _np(tau)
+    Fo, tauo = O.qr(A)
+    scale = max(1.0, np.abs(Fo).max())
+    assert np.abs(np.triu(F[:n]) - np.triu(Fo[:n])).max() <= 1e-11 * scale
+    assert np.abs(np.tril(F, -1) - np.tril(Fo, -1)).max() <= 1e-11 * max(1.0, np.abs(np.tril(Fo, -1)).max())
+    assert np.abs(tau - tauo).max() <= 1e-11
+
+
+@pytest.mark.parametrize("nb", [8, 16, 33, 64])
+def test_qr_panel_widths_agree(nb):
+    A = I.random_matrix(300, 150, seed=5)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A), nb=nb)
+    assert f.info()["nb"] == nb
+    F, tau = ctqr.factor_matrix(f)
+    Fo, tauo = O.qr(A)
+    assert np.abs(np.triu(_np(F)[:150]) - np.triu(Fo[:150])).max() <= 1e-11 * np.abs(Fo).max()
+    assert np.abs(_np(tau) - tauo).max() <= 1e-11
+
+
+def test_qr_factor_ct_matrix_from_device_build():
+    g = I.CONFIG1["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    f = ctqr.qr_factor(A)
+    F, tau = ctqr.factor_matrix(f)
+    Fo, tauo = O.qr(_np(A))  # oracle on the GPU-built A isolates the QR error
+    n = g.n
+    assert np.abs(np.triu(_np(F)[:n]) - np.triu(Fo[:n])).max() <= 1e-11 * np.abs(Fo).max()
+    assert np.abs(_np(tau) - tauo).max() <= 1e-11
+
+
+def test_factorization_is_deterministic():
+    A = ctqr.to_colmajor(I.random_matrix(700, 300, seed=2))
+    F1, t1 = ctqr.factor_matrix(ctqr.qr_factor(A))
+    F2, t2 = ctqr.factor_matrix(ctqr.qr_factor(A))
+    assert torch.equal(F1, F2) and torch.equal(t1, t2)
+
+
+# ---------------------------------------------------------------- apply / solve
+@pytest.mark.parametrize("shape,k", [((517, 203), 1), ((517, 203), 5), ((1000, 129), 17), ((300, 300), 70)])
+def test_apply_qt_and_trsm_match_oracle(shape, k):
+    m, n = shape
+    A = I.random_matrix(m, n, seed=11)
+    B = I.random_matrix(m, k, seed=12)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A))
+    Fo, tauo = O.qr(A)
+    Bg = ctqr.to_colmajor(B)
+    ctqr.apply_qt(f, Bg)
+    QtB = O.apply_qt(Fo, tauo, B)
+    assert np.abs(_np(Bg) - QtB).max() <= 1e-11 * np.abs(QtB).max()
+    ctqr.trsm_solve(f, Bg)
+    X = O.backsolve(Fo, QtB)
+    got = _np(Bg)[:n]
+    assert np.linalg.norm(got - X) / np.linalg.norm(X) <= 1e-10
+
+
+def test_trsm_respects_leading_dimension_and_rows_below_n():
+    m, n, k = 400, 150, 3
+    A = I.random_matrix(m, n, seed=21)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A))
+    B = ctqr.colmajor(m, k, ld=m + 5)
+    B.copy_(torch.as_tensor(I.random_matrix(m, k, seed=22)))
+    before = _np(B)[n:].copy()
+    ctqr.trsm_solve(f, B)
+    assert np.array_equal(_np(B)[n:], before)
+
+
+# ---------------------------------------------------------------- reconstruction
+def test_reconstruct_config1_matches_oracle():
+    g = I.CONFIG1["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    x_true = I.phantoms(g, I.CONFIG1["seeds"])
+    Anp = _np(A)
+    b = Anp @ x_true
+    f = ctqr.qr_factor(A)
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b))
+    Xo = O.lstsq(Anp, b)
+    err = np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo)
+    assert err <= 1e-10
+    assert np.linalg.norm(_np(X) - x_true) / np.linalg.norm(x_true) <= 1e-10
+
+
+def test_reconstruct_multi_rhs_noisy_config4a_subset():
+    g = I.CONFIG4A["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    Anp = _np(A)
+    seeds = I.CONFIG4A["seeds"][:40]
+    b = I.poisson_noise(Anp @ I.phantoms(g, seeds), g.fov, I.CONFIG4A["noise_i0"], seed=1000)
+    f = ctqr.qr_factor(A)
+    X, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b))
+    Xo = O.lstsq(Anp, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10
+    # one RHS at a time gives the same columns
+    X1, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b[:, 7:8]))
+    assert np.linalg.norm(_np(X1)[:, 0] - _np(X)[:, 7]) <= 1e-13 * np.linalg.norm(_np(X)[:, 7])
+
+
+def test_mixed_fp32_factor_refined_to_fp64_accuracy():
+    g = I.CONFIG1["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    Anp = _np(A)
+    x_true = I.phantoms(g, [1, 2, 3])
+    b = Anp @ x_true
+    f = ctqr.qr_factor(A.to(torch.float32), prec=ctqr.Prec.F32)
+    assert f.info()["prec"] == ctqr.Prec.F32
+    X0, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b))  # unrefined: FP32-level accuracy
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A)
+    Xo = O.lstsq(Anp, b)
+    e0 = np.linalg.norm(_np(X0) - Xo) / np.linalg.norm(Xo)
+    e = np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo)
+    assert e <= 1e-10, (e, rep)
+    assert e0 > 1e-9  # the refinement did the work
+    assert 1 <= rep.iterations <= 10
+
+
+# ---------------------------------------------------------------- edge cases
+def test_rank_deficient_reported():
+    A = I.random_matrix(50, 20, seed=3)
+    A[:, 7] = 0.0
+    f = ctqr.qr_factor(ctqr.to_colmajor(A))
+    assert f.status() == ctqr.CT_ERR_RANK
+    A = I.random_matrix(50, 20, seed=3)
+    A[:, 9] = A[:, 2]
+    f = ctqr.qr_factor(ctqr.to_colmajor(A))
+    assert f.status() == ctqr.CT_ERR_RANK
+
+
+def test_nonfinite_reported():
+    A = I.random_matrix(80, 30, seed=4)
+    A[10, 5] = np.nan
+    f = ctqr.qr_factor(ctqr.to_colmajor(A))
+    assert f.status() == ctqr.CT_ERR_NONFINITE
+
+
+def test_invalid_arguments():
+    A = ctqr.to_colmajor(I.random_matrix(10, 20, seed=1))  # m < n
+    with pytest.raises(ctqr.CtError) as e:
+        ctqr.qr_factor(A)
+    assert e.value.status == ctqr.CT_ERR_INVALID
+    f = ctqr.qr_factor(ctqr.to_colmajor(I.random_matrix(30, 10, seed=1)))
+    short = ctqr.colmajor(20, 2)  # fewer rows than m
+    with pytest.raises(ctqr.CtError):
+        ctqr.apply_qt(f, short)
+    empty = ctqr.colmajor(30, 0)
+    assert ctqr.load().ct_apply_qt(f.handle, empty.data_ptr() or 16, 30, 0, None) == ctqr.CT_OK
+
+
+def test_in_place_factor_borrows_the_matrix():
+    A = I.random_matrix(200, 90, seed=8)
+    At = ctqr.to_colmajor(A)
+    f = ctqr.qr_factor(At, in_place=True)
+    Fo, _ = O.qr(A)
+    assert np.abs(np.triu(_np(At)[:90]) - np.triu(Fo[:90])).max() <= 1e-11 * np.abs(Fo).max()
