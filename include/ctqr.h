@@ -98,9 +98,12 @@ typedef struct ct_factor ct_factor;
 
 /* Options of ct_reconstruct_batch's FP64 refinement.  NULL = defaults. */
 typedef struct {
-  int max_iter;    /* iteration cap (default 30)                               */
+  int max_iter;    /* iteration cap, all phases together (default 60)          */
   double tol;      /* stop when every column has ||dx_c|| <= tol*||x_c||        */
                    /* (default 1e-12)                                          */
+  int method;      /* 0 auto: classical refinement while its updates shrink     */
+                   /*   at least twofold per step, then preconditioned CGLS;    */
+                   /* 1 classical only; 2 CGLS only (after the first solve)     */
 } ct_refine_opts;
 
 /* Optional report of ct_reconstruct_batch. */
@@ -109,7 +112,24 @@ typedef struct {
   double last_update;    /* max_c ||dx_c|| / ||x_c|| of the last correction      */
   double residual;       /* ||B - A X||_F / ||B||_F before the last correction   */
   double ms_total;       /* wall time of the call (host clock, synchronised)     */
+  double ms_build;       /* ct_reconstruct_scan only: device time of building A  */
+  double ms_factor;      /* ct_reconstruct_scan only: device time of A = QR      */
+  double ms_solve;       /* ct_reconstruct_scan only: device time of the solve   */
+                         /* (Q^T, R^-1 and refinement, copies excluded)          */
 } ct_report;
+
+/* Per-kernel-class launch statistics (ct_profile_kernels). */
+typedef struct {
+  const char* name;      /* kernel class (static storage)                        */
+  uint64_t launches;     /* launches since the last ct_profile_reset             */
+  uint64_t timed;        /* launches bracketed by CUDA events                    */
+  double ms;             /* summed device time of the timed launches             */
+  double flops;          /* summed algorithmic flops of all launches             */
+  double bytes;          /* summed algorithmic DRAM bytes of all launches        */
+} ct_kernel_stats;
+
+/* Where the caller's B and X live for ct_reconstruct_scan. */
+typedef enum { CT_DEVICE_BUFFERS = 0, CT_HOST_BUFFERS = 1 } ct_buffers;
 
 /* Human-readable name of a status code (static storage). */
 const char* ct_status_str(ct_status s);
@@ -186,13 +206,18 @@ ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k,
  * Without A (A == NULL) this is one Q^T application and one back-solve in
  * FP64 arithmetic with the factor as stored.
  * With A (the original m x n system matrix, type A_dtype, leading dimension
- * lda; FP64 for full accuracy) the result is improved by classical iterative
- * refinement: X_0 = R^{-1}(Q^T B)[0:n]; repeat  Res = B - A X  (FP64),
- * D = R^{-1}(Q^T Res)[0:n] (in FP32 arithmetic for an FP32-stored factor,
- * FP64 otherwise), X += D, until every column satisfies ||d_c|| <= tol ||x_c||.
- * This is how a CT_PREC_F32 / CT_PREC_TF32 factor reaches FP64 accuracy; it
- * converges to the least-squares solution when B is consistent (B = A X
- * exactly), otherwise to the solution of a nearby projected problem.
+ * lda; FP64 for full accuracy) the result is refined with FP64 residuals
+ * until every column satisfies ||dx_c|| <= tol ||x_c||.  This is how a
+ * CT_PREC_F32 / CT_PREC_TF32 factor reaches FP64 accuracy.
+ *  - classical refinement: X_0 = R^{-1}(Q^T B)[0:n]; repeat Res = B - A X
+ *    (FP64), D = R^{-1}(Q^T Res)[0:n] (FP32 arithmetic for an FP32-stored
+ *    factor, FP64 otherwise), X += D.  Cheap; exact for consistent B
+ *    (B = A X), but for noisy B the rounding of the correction solve, which is
+ *    proportional to the residual, stops it short of the least-squares
+ *    solution.
+ *  - CGLS on min ||A R^{-1} y - B||, X = R^{-1} y (the low-precision R as a
+ *    right preconditioner), every product with A, A^T, R^{-1}, R^{-T} in FP64:
+ *    converges to the least-squares solution for any B.
  * Synchronous: returns once X holds the result, with the factor's device
  * status, or CT_ERR_NOCONVERGE if the cap was reached (X then holds the last
  * iterate).  `report` (may be NULL) receives iteration counts and timings. */
@@ -202,9 +227,36 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A,
                                const ct_refine_opts* ropts, ct_report* report,
                                void* stream);
 
-/* Release a factor and its device memory (NULL is a no-op).  Synchronises
- * nothing: the caller must not destroy a factor whose work is still queued on
- * a stream it cannot order the free after. */
+/* Whole method for one scan: build A from `geom` on the device (Eq.
+ * (sistema), stacked over lambda*I when lambda > 0), factor it (Eq. (QR)) with
+ * trailing updates in `prec`, and reconstruct the k slices X = R^{-1}(Q^T B)
+ * (Eq. (qr1)), refined with FP64 residuals against the FP64 A when prec is not
+ * CT_PREC_F64.  B is m x k FP64 (ldb >= m), X is n x k FP64 (ldx >= n), both in
+ * host memory (CT_HOST_BUFFERS: copied in and out inside the call; page-locked
+ * memory gives full copy bandwidth) or in device memory (CT_DEVICE_BUFFERS).
+ * All other device memory (A in FP64, the factor, scratch) is allocated and
+ * released inside the call.  Synchronous; `report` (may be NULL) receives the
+ * phase timings. */
+ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec prec,
+                              const double* B, int64_t ldb, double* X, int64_t ldx,
+                              int64_t k, ct_buffers where, const ct_refine_opts* ropts,
+                              ct_report* report, void* stream);
+
+/* Launch accounting.  Every kernel launch is counted; with timing enabled
+ * each launch is also bracketed by CUDA events on its stream. */
+void ct_profile_enable(int on);
+/* Zero the counters (synchronises pending timing events first). */
+void ct_profile_reset(void);
+/* Fill up to max_entries stats (one per kernel class) and return how many
+ * were written; out == NULL returns the number of classes.  Synchronises the
+ * pending timing events. */
+int ct_profile_kernels(ct_kernel_stats* out, int max_entries);
+/* Total kernel launches since the last reset. */
+uint64_t ct_kernel_launches(void);
+
+/* Release a factor and its device memory (NULL is a no-op).  Waits for the
+ * device to finish all queued work first, so a factor may be destroyed while
+ * kernels that use it are still in flight. */
 void ct_factor_destroy(ct_factor* f);
 
 #ifdef __cplusplus

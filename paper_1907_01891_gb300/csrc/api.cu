@@ -107,6 +107,199 @@ ct_status read_status(const ct_factor* f, cudaStream_t s) {
   return (ct_status)h;
 }
 
+
+// FP64-residual refinement of X for a factor of A (see ct_reconstruct_batch).
+class Refiner {
+ public:
+  Refiner(const ct_factor* f, const void* A, ct_dtype adt, int64_t lda, const double* B, int64_t ldb,
+          double* X, int64_t ldx, int64_t k, cudaStream_t s, int sms)
+      : f_(f), A_(A), a64_(adt == CT_F64), lda_(lda), B_(B), ldb_(ldb), X_(X), ldx_(ldx), k_(k),
+        s_(s), sms_(sms), m_(f->m), n_(f->n), ldw_((f->m + 3) / 4 * 4) {}
+
+  ct_status run(const ct_refine_opts* o, ct_report* rep) {
+    const int max_iter = o && o->max_iter > 0 ? o->max_iter : 60;
+    tol_ = o && o->tol > 0.0 ? o->tol : 1e-12;
+    const int method = o ? o->method : 0;
+    ct_status st;
+    if ((st = alloc()) != CT_OK) return st;
+    if ((st = launch_col_norms2(B_, ldb_, m_, k_, bn2_, s_)) != CT_OK) return st;
+    // X_0 = R^{-1} (Q^T B)[0:n], then classical corrections.
+    if ((st = launch_zero_matrix(X_, 8, ldx_, n_, k_, s_)) != CT_OK) return st;
+    int it = 0;
+    double prev = INFINITY;
+    ct_status result = CT_ERR_NOCONVERGE;
+    bool go_cgls = method == 2;
+    for (; it <= max_iter; ++it) {
+      double worst = 0.0;
+      if ((st = classical_step(it > 0, &worst)) != CT_OK) return st;
+      if (it == 0) continue;
+      last_ = worst;
+      if (worst <= tol_) { result = CT_OK; break; }
+      if (!isfinite(worst)) return CT_ERR_NONFINITE;
+      if (method == 2 || (method == 0 && it >= 2 && worst > 0.5 * prev)) { go_cgls = true; break; }
+      prev = worst;
+    }
+    if (go_cgls && result != CT_OK) {
+      int used = 0;
+      result = cgls(max_iter - it, &used);
+      it += used;
+    }
+    if (rep) {
+      rep->iterations = it > max_iter ? max_iter : it;
+      rep->last_update = last_;
+      rep->residual = resid_;
+    }
+    return result;
+  }
+
+ private:
+  const ct_factor* f_;
+  const void* A_;
+  bool a64_;
+  int64_t lda_;
+  const double* B_;
+  int64_t ldb_;
+  double* X_;
+  int64_t ldx_, k_;
+  cudaStream_t s_;
+  int sms_;
+  int64_t m_, n_, ldw_;
+  double tol_ = 1e-12, last_ = INFINITY, resid_ = 0.0;
+  size_t work_elems_ = 0;
+  Scratch work_, Y_, D_, cg_, scal_;
+  double *Yd_ = nullptr, *bn2_ = nullptr, *n1_ = nullptr, *n2_ = nullptr, *n3_ = nullptr, *a_ = nullptr;
+  double *S_ = nullptr, *P_ = nullptr, *T_ = nullptr, *Q_ = nullptr;
+  std::vector<double> h_;
+
+  ct_status alloc() {
+    ct_status st;
+    work_elems_ = reflector_work_elems(sms_, f_->nb, k_);
+    if ((st = work_.alloc(work_elems_ * sizeof(double), s_)) != CT_OK) return st;
+    if ((st = Y_.alloc((size_t)ldw_ * k_ * sizeof(double), s_)) != CT_OK) return st;
+    if (f_->store == CT_F32 && (st = D_.alloc((size_t)ldw_ * k_ * sizeof(float), s_)) != CT_OK) return st;
+    if ((st = scal_.alloc((size_t)5 * k_ * sizeof(double), s_)) != CT_OK) return st;
+    Yd_ = (double*)Y_.p;
+    bn2_ = (double*)scal_.p;
+    n1_ = bn2_ + k_;
+    n2_ = n1_ + k_;
+    n3_ = n2_ + k_;
+    a_ = n3_ + k_;
+    h_.resize((size_t)4 * k_);
+    return CT_OK;
+  }
+
+  ct_status fetch(const double* d, int count) {
+    CT_CUDA_TRY(cudaMemcpyAsync(h_.data(), d, sizeof(double) * k_ * count, cudaMemcpyDeviceToHost, s_));
+    CT_CUDA_TRY(cudaStreamSynchronize(s_));
+    return CT_OK;
+  }
+
+  // Res = B - A X into Yd (m x k).
+  ct_status residual() {
+    ct_status st;
+    if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) return st;
+    return launch_dense_update(A_, a64_, lda_, (int)n_, X_, ldx_, Yd_, true, ldw_, m_, k_, s_);
+  }
+
+  // One classical step; with_residual = false is the first solve (X = 0).
+  ct_status classical_step(bool with_residual, double* worst) {
+    ct_status st;
+    if (with_residual) {
+      if ((st = residual()) != CT_OK) return st;
+      if ((st = launch_col_norms2(Yd_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;
+    } else if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) {
+      return st;
+    }
+    if (f_->store == CT_F32) {
+      float* D = (float*)D_.p;
+      if ((st = launch_copy_matrix(Yd_, CT_F64, ldw_, D, CT_F32, ldw_, m_, k_, s_)) != CT_OK) return st;
+      if ((st = apply_qt_all(f_, D, false, ldw_, k_, true, (double*)work_.p, work_elems_, sms_, s_)) != CT_OK) return st;
+      if ((st = launch_trsm(f_, D, false, ldw_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_add_f32_to_f64(D, ldw_, X_, ldx_, n_, k_, n2_, n3_, s_)) != CT_OK) return st;
+    } else {
+      if ((st = apply_qt_all(f_, Yd_, true, ldw_, k_, false, (double*)work_.p, work_elems_, sms_, s_)) != CT_OK) return st;
+      if ((st = launch_trsm(f_, Yd_, true, ldw_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_add_f64_to_f64(Yd_, ldw_, X_, ldx_, n_, k_, n2_, n3_, s_)) != CT_OK) return st;
+    }
+    // h = [bn2 | n1 = ||res||^2 | n2 = ||d||^2 | n3 = ||x||^2]
+    if ((st = fetch(bn2_, 4)) != CT_OK) return st;
+    double w = 0.0, rr = 0.0, bb = 0.0;
+    for (int64_t c = 0; c < k_; ++c) {
+      const double xc = sqrt(h_[3 * k_ + c]), dc = sqrt(h_[2 * k_ + c]);
+      const double rel = xc > 0.0 ? dc / xc : (dc > 0.0 ? INFINITY : 0.0);
+      if (!(rel <= w)) w = rel;
+      rr += h_[k_ + c];
+      bb += h_[c];
+    }
+    if (with_residual) resid_ = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    *worst = w;
+    return CT_OK;
+  }
+
+  // s = R^{-T} (A^T r)  with r in Yd.
+  ct_status precond_grad(double* S) {
+    ct_status st;
+    if ((st = launch_gemm_tn(A_, a64_, lda_, Yd_, ldw_, S, n_, m_, n_, k_, s_)) != CT_OK) return st;
+    return launch_trsm_t(f_, S, n_, k_, s_);
+  }
+
+  // CGLS on min ||A R^{-1} y - B|| from the current X, at most `budget` steps.
+  ct_status cgls(int budget, int* used) {
+    ct_status st;
+    *used = 0;
+    if ((st = cg_.alloc(((size_t)3 * n_ * k_ + (size_t)ldw_ * k_) * sizeof(double), s_)) != CT_OK) return st;
+    S_ = (double*)cg_.p;
+    P_ = S_ + n_ * k_;
+    T_ = P_ + n_ * k_;
+    Q_ = T_ + n_ * k_;
+    if ((st = residual()) != CT_OK) return st;              // r = B - A X
+    if ((st = precond_grad(S_)) != CT_OK) return st;        // s = R^-T A^T r
+    if ((st = launch_copy_matrix(S_, CT_F64, n_, P_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
+    if ((st = launch_col_norms2(S_, n_, n_, k_, n1_, s_)) != CT_OK) return st;
+    if ((st = fetch(n1_, 1)) != CT_OK) return st;
+    std::vector<double> gamma(h_.begin(), h_.begin() + k_), alpha(k_), beta(k_);
+    for (int it = 0; it < budget; ++it) {
+      *used = it + 1;
+      // t = R^{-1} p ; q = -A t
+      if ((st = launch_copy_matrix(P_, CT_F64, n_, T_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_trsm(f_, T_, true, n_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_zero_matrix(Q_, 8, ldw_, m_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, T_, n_, Q_, true, ldw_, m_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_col_norms2(Q_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;
+      if ((st = launch_col_norms2(T_, n_, n_, k_, n2_, s_)) != CT_OK) return st;
+      if ((st = launch_col_norms2(X_, ldx_, n_, k_, n3_, s_)) != CT_OK) return st;
+      if ((st = fetch(n1_, 3)) != CT_OK) return st;
+      double worst = 0.0;
+      for (int64_t c = 0; c < k_; ++c) {
+        const double qq = h_[c], tt = h_[k_ + c], xx = h_[2 * k_ + c];
+        alpha[c] = qq > 0.0 ? gamma[c] / qq : 0.0;
+        const double dx = alpha[c] * sqrt(tt), xn = sqrt(xx);
+        const double rel = xn > 0.0 ? dx / xn : (dx > 0.0 ? INFINITY : 0.0);
+        if (!(rel <= worst)) worst = rel;
+      }
+      CT_CUDA_TRY(cudaMemcpyAsync(a_, alpha.data(), sizeof(double) * k_, cudaMemcpyHostToDevice, s_));
+      if ((st = launch_colwise(0, 1.0, a_, T_, n_, X_, ldx_, n_, k_, s_)) != CT_OK) return st;   // x += a t
+      if ((st = launch_colwise(0, 1.0, a_, Q_, ldw_, Yd_, ldw_, m_, k_, s_)) != CT_OK) return st;  // r -= a A t
+      last_ = worst;
+      if (!isfinite(worst)) return CT_ERR_NONFINITE;
+      if (worst <= tol_) {
+        CT_CUDA_TRY(cudaStreamSynchronize(s_));
+        return CT_OK;
+      }
+      if ((st = precond_grad(S_)) != CT_OK) return st;
+      if ((st = launch_col_norms2(S_, n_, n_, k_, n1_, s_)) != CT_OK) return st;
+      if ((st = fetch(n1_, 1)) != CT_OK) return st;
+      for (int64_t c = 0; c < k_; ++c) {
+        beta[c] = gamma[c] > 0.0 ? h_[c] / gamma[c] : 0.0;
+        gamma[c] = h_[c];
+      }
+      CT_CUDA_TRY(cudaMemcpyAsync(a_, beta.data(), sizeof(double) * k_, cudaMemcpyHostToDevice, s_));
+      if ((st = launch_colwise(1, 1.0, a_, S_, n_, P_, n_, n_, k_, s_)) != CT_OK) return st;     // p = s + b p
+    }
+    return CT_ERR_NOCONVERGE;
+  }
+};
+
 }  // namespace
 
 namespace ctqr {
@@ -303,22 +496,19 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A, ct_dtype A_dty
   if (k == 0) return CT_OK;
   if (!B || !X || !aligned16(B) || !aligned16(X) || ldb < f->m || ldx < f->n) return CT_ERR_INVALID;
   if (A && (!aligned16(A) || lda < f->m || (A_dtype != CT_F64 && A_dtype != CT_F32))) return CT_ERR_INVALID;
-  const int max_iter = ropts && ropts->max_iter > 0 ? ropts->max_iter : 30;
-  const double tol = ropts && ropts->tol > 0.0 ? ropts->tol : 1e-12;
   cudaStream_t s = as_stream(stream);
   DeviceInfo di;
   ct_status st = device_info(&di);
   if (st != CT_OK) return st;
   const int64_t m = f->m, n = f->n;
-  const int64_t ldw = (m + 3) / 4 * 4;
-  const size_t work_elems = reflector_work_elems(di.sms, f->nb, k);
-
-  Scratch work, Y;
-  if ((st = work.alloc(work_elems * sizeof(double), s)) != CT_OK) return st;
-  if ((st = Y.alloc((size_t)ldw * k * sizeof(double), s)) != CT_OK) return st;
-  double* Yd = (double*)Y.p;
 
   if (!A) {
+    const int64_t ldw = (m + 3) / 4 * 4;
+    const size_t work_elems = reflector_work_elems(di.sms, f->nb, k);
+    Scratch work, Y;
+    if ((st = work.alloc(work_elems * sizeof(double), s)) != CT_OK) return st;
+    if ((st = Y.alloc((size_t)ldw * k * sizeof(double), s)) != CT_OK) return st;
+    double* Yd = (double*)Y.p;
     // Plain solve in FP64 arithmetic: Y = B; Y = Q^T Y; Y[0:n] = R^-1 Y[0:n]; X = Y[0:n].
     if ((st = launch_copy_matrix(B, CT_F64, ldb, Yd, CT_F64, ldw, m, k, s)) != CT_OK) return st;
     if ((st = apply_qt_all(f, Yd, true, ldw, k, false, (double*)work.p, work_elems, di.sms, s)) != CT_OK) return st;
@@ -329,65 +519,80 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A, ct_dtype A_dty
     return st;
   }
 
-  // Refinement.  Corrections are solved in the factor's storage precision.
-  const bool f32 = f->store == CT_F32;
-  Scratch Dbuf, norms;
-  if (f32 && (st = Dbuf.alloc((size_t)ldw * k * sizeof(float), s)) != CT_OK) return st;
-  if ((st = norms.alloc((size_t)3 * k * sizeof(double), s)) != CT_OK) return st;
-  double* dn2 = (double*)norms.p;
-  double* xn2 = dn2 + k;
-  double* bn2 = xn2 + k;
-  std::vector<double> h(3 * (size_t)k);
-  if ((st = launch_zero_matrix(X, 8, ldx, n, k, s)) != CT_OK) return st;
-  if ((st = launch_col_norms2(B, ldb, m, k, bn2, s)) != CT_OK) return st;
-  int it = 0;
-  double last = INFINITY, resid = 0.0;
-  ct_status result = CT_ERR_NOCONVERGE;
-  for (; it <= max_iter; ++it) {
-    // Res = B - A X (FP64); the first pass has X = 0, so Res = B.
-    if ((st = launch_copy_matrix(B, CT_F64, ldb, Yd, CT_F64, ldw, m, k, s)) != CT_OK) return st;
-    if (it > 0 && (st = launch_dense_update(A, A_dtype == CT_F64, lda, (int)n, X, ldx, Yd, true, ldw, m, k, s)) != CT_OK) return st;
-    if (it > 0) {
-      if ((st = launch_col_norms2(Yd, ldw, m, k, dn2, s)) != CT_OK) return st;
-      CT_CUDA_TRY(cudaMemcpyAsync(h.data(), dn2, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-      CT_CUDA_TRY(cudaMemcpyAsync(h.data() + 2 * k, bn2, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-      CT_CUDA_TRY(cudaStreamSynchronize(s));
-      double rr = 0.0, bb = 0.0;
-      for (int64_t c = 0; c < k; ++c) { rr += h[c]; bb += h[2 * k + c]; }
-      resid = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-    }
-    if (f32) {
-      float* D = (float*)Dbuf.p;
-      if ((st = launch_copy_matrix(Yd, CT_F64, ldw, D, CT_F32, ldw, m, k, s)) != CT_OK) return st;
-      if ((st = apply_qt_all(f, D, false, ldw, k, true, (double*)work.p, work_elems, di.sms, s)) != CT_OK) return st;
-      if ((st = launch_trsm(f, D, false, ldw, k, s)) != CT_OK) return st;
-      if ((st = launch_add_f32_to_f64(D, ldw, X, ldx, n, k, dn2, xn2, s)) != CT_OK) return st;
-    } else {
-      if ((st = apply_qt_all(f, Yd, true, ldw, k, false, (double*)work.p, work_elems, di.sms, s)) != CT_OK) return st;
-      if ((st = launch_trsm(f, Yd, true, ldw, k, s)) != CT_OK) return st;
-      if ((st = launch_add_f64_to_f64(Yd, ldw, X, ldx, n, k, dn2, xn2, s)) != CT_OK) return st;
-    }
-    CT_CUDA_TRY(cudaMemcpyAsync(h.data(), dn2, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
-    CT_CUDA_TRY(cudaStreamSynchronize(s));
-    double worst = 0.0;
-    for (int64_t c = 0; c < k; ++c) {
-      const double xc = sqrt(h[k + c]), dc = sqrt(h[c]);
-      const double rel = xc > 0.0 ? dc / xc : (dc > 0.0 ? INFINITY : 0.0);
-      if (!(rel <= worst)) worst = rel;
-    }
-    if (it > 0) last = worst;
-    if (it > 0 && worst <= tol) { result = CT_OK; break; }
-    if (!isfinite(worst)) { result = CT_ERR_NONFINITE; break; }
-  }
-  if (report) {
-    report->iterations = it > max_iter ? max_iter : it;
-    report->last_update = last;
-    report->residual = resid;
-  }
+  Refiner R(f, A, A_dtype, lda, B, ldb, X, ldx, k, s, di.sms);
+  st = R.run(ropts, report);
   ct_status dev = read_status(f, s);
   if (report) report->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   if (dev != CT_OK) return dev;
-  return result;
+  return st;
+}
+
+ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec prec,
+                              const double* B, int64_t ldb, double* X, int64_t ldx, int64_t k,
+                              ct_buffers where, const ct_refine_opts* ropts, ct_report* report,
+                              void* stream) {
+  const auto t_start = std::chrono::steady_clock::now();
+  if (report) memset(report, 0, sizeof(*report));
+  int64_t m = 0, n = 0;
+  ct_status st = ct_system_size(geom, lambda, &m, &n);
+  if (st != CT_OK) return st;
+  if (k < 0 || (k > 0 && (!B || !X || ldb < m || ldx < n))) return CT_ERR_INVALID;
+  if (where != CT_DEVICE_BUFFERS && where != CT_HOST_BUFFERS) return CT_ERR_INVALID;
+  if (prec != CT_PREC_F64 && prec != CT_PREC_F32 && prec != CT_PREC_TF32) return CT_ERR_INVALID;
+  if (m < n) return CT_ERR_INVALID;
+  if (k == 0) return CT_OK;
+  cudaStream_t s = as_stream(stream);
+  const bool host = where == CT_HOST_BUFFERS;
+  if (!host && (!aligned16(B) || !aligned16(X))) return CT_ERR_INVALID;
+  const int64_t lda = (m + 3) / 4 * 4;
+  Scratch Abuf, Bbuf, Xbuf;
+  if ((st = Abuf.alloc((size_t)lda * n * sizeof(double), s)) != CT_OK) return st;
+  const double* Bd = B;
+  double* Xd = X;
+  int64_t ldbd = ldb, ldxd = ldx;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto& e : ev) CT_CUDA_TRY(cudaEventCreate(&e));
+  struct EvFree {
+    cudaEvent_t* e;
+    ~EvFree() { for (int i = 0; i < 4; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+  } evfree{ev};
+  if (host) {
+    if ((st = Bbuf.alloc((size_t)lda * k * sizeof(double), s)) != CT_OK) return st;
+    if ((st = Xbuf.alloc((size_t)n * k * sizeof(double), s)) != CT_OK) return st;
+    CT_CUDA_TRY(cudaMemcpy2DAsync(Bbuf.p, lda * sizeof(double), B, ldb * sizeof(double),
+                                  m * sizeof(double), k, cudaMemcpyHostToDevice, s));
+    Bd = (const double*)Bbuf.p;
+    Xd = (double*)Xbuf.p;
+    ldbd = lda;
+    ldxd = n;
+  }
+  double* A = (double*)Abuf.p;
+  CT_CUDA_TRY(cudaEventRecord(ev[0], s));
+  if ((st = launch_build_system(geom, CT_F64, lambda, A, lda, m, n, s)) != CT_OK) return st;
+  CT_CUDA_TRY(cudaEventRecord(ev[1], s));
+  ct_factor* f = nullptr;
+  ct_qr_opts qo = {0, prec == CT_PREC_F64 ? 1 : 0};  // FP64: factor A in place
+  if ((st = ct_qr_factor(A, CT_F64, m, n, lda, prec, &qo, &f, stream)) != CT_OK) return st;
+  CT_CUDA_TRY(cudaEventRecord(ev[2], s));
+  ct_report rep;
+  ct_status rs = ct_reconstruct_batch(f, prec == CT_PREC_F64 ? nullptr : A, CT_F64, lda, Bd, ldbd, Xd,
+                                      ldxd, k, ropts, &rep, stream);
+  cudaError_t ce = cudaEventRecord(ev[3], s);
+  if (ce == cudaSuccess && host)
+    ce = cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, ldxd * sizeof(double), n * sizeof(double), k,
+                           cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  ct_factor_destroy(f);
+  if (ce != cudaSuccess) return CT_ERR_CUDA;
+  if (report) {
+    *report = rep;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev[0], ev[1]) == cudaSuccess) report->ms_build = t;
+    if (cudaEventElapsedTime(&t, ev[1], ev[2]) == cudaSuccess) report->ms_factor = t;
+    if (cudaEventElapsedTime(&t, ev[2], ev[3]) == cudaSuccess) report->ms_solve = t;
+    report->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return rs;
 }
 
 void ct_factor_destroy(ct_factor* f) {

@@ -181,6 +181,127 @@ __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_
   }
 }
 
+// C(r, c) -= sum_{a < K} V(a, r) W(a, c): the transposed-V update of the
+// forward substitution with R^T (V = a block row of R, read with a < K its
+// rows), 64 x BN tile per CTA.
+template <typename TV, int BN>
+__global__ void __launch_bounds__(kGT) k_update_t(const TV* __restrict__ V, int64_t ldv, int K,
+                                                   const double* __restrict__ W, int64_t ldw,
+                                                   double* __restrict__ C, int64_t ldc, int64_t mr,
+                                                   int64_t nc) {
+  constexpr int TN = BN / 16;
+  __shared__ double Vs[kBK][kBM + 1];
+  __shared__ double Ws[kBK][BN + 1];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int64_t r0 = (int64_t)blockIdx.x * kBM, c0 = (int64_t)blockIdx.y * BN;
+  double acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (int a0 = 0; a0 < K; a0 += kBK) {
+#pragma unroll
+    for (int i = 0; i < kBM * kBK / kGT; ++i) {
+      const int e = tid + kGT * i, aa = e % kBK, r = e / kBK;
+      const int64_t rg = r0 + r;
+      Vs[aa][r] = (rg < mr && a0 + aa < K) ? (double)V[a0 + aa + rg * ldv] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < (BN * kBK + kGT - 1) / kGT; ++i) {
+      const int e = tid + kGT * i;
+      if (e < BN * kBK) {
+        const int aa = e % kBK, c = e / kBK;
+        const int64_t cg = c0 + c;
+        Ws[aa][c] = (a0 + aa < K && cg < nc) ? W[a0 + aa + cg * ldw] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      double av[4], wv[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) wv[j] = Ws[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * wv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t cg = c0 + tx * TN + j;
+    if (cg >= nc) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + ty * 4 + i;
+      if (r < mr) C[r + cg * ldc] -= acc[i][j];
+    }
+  }
+}
+
+// Y(a, c) = sum_r A(r, a) R(r, c) for a < n, c < k (FP64 accumulation): A^T R
+// with the long contraction over the m rows; 64 x BN output tile per CTA.
+template <typename TA, int BN>
+__global__ void __launch_bounds__(kGT) k_gemm_tn(const TA* __restrict__ A, int64_t lda,
+                                                 const double* __restrict__ R, int64_t ldr,
+                                                 double* __restrict__ Y, int64_t ldy, int64_t m,
+                                                 int64_t n, int64_t k) {
+  constexpr int TN = BN / 16;
+  __shared__ double As[kBK][kBM + 1];
+  __shared__ double Rs[kBK][BN + 1];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int64_t a0 = (int64_t)blockIdx.x * kBM, c0 = (int64_t)blockIdx.y * BN;
+  double acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (int64_t r0 = 0; r0 < m; r0 += kBK) {
+#pragma unroll
+    for (int i = 0; i < kBM * kBK / kGT; ++i) {
+      const int e = tid + kGT * i, a = e / kBK, rr = e % kBK;
+      const int64_t r = r0 + rr, ag = a0 + a;
+      As[rr][a] = (r < m && ag < n) ? (double)A[r + ag * lda] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < (BN * kBK + kGT - 1) / kGT; ++i) {
+      const int e = tid + kGT * i;
+      if (e < BN * kBK) {
+        const int c = e / kBK, rr = e % kBK;
+        const int64_t r = r0 + rr, cg = c0 + c;
+        Rs[rr][c] = (r < m && cg < k) ? R[r + cg * ldr] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      double av[4], rv[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) rv[j] = Rs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * rv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t cg = c0 + tx * TN + j;
+    if (cg >= k) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t a = a0 + ty * 4 + i;
+      if (a < n) Y[a + cg * ldy] = acc[i][j];
+    }
+  }
+}
+
 size_t reflector_work_elems(int sms, int nbp, int64_t nc) {
   (void)nbp;
   return (size_t)kBM * ((size_t)128 * sms + 2 * (size_t)nc) + 64;
@@ -204,11 +325,23 @@ ct_status run_reflector(const ReflectorArgs& a, double* work, size_t work_elems,
   if (need > work_elems) return CT_ERR_INVALID;
   double* part = work;
   double* W = work + (size_t)splits * kBM * a.nc;
-  k_vtc<TV, TC, Acc, BN><<<dim3((unsigned)tiles_n, (unsigned)splits), kGT, 0, s>>>(
-      (const TV*)a.V, a.ldv, a.nbp, (const TC*)a.C, a.ldc, a.mr, a.nc, chunk, part);
-  k_tw<Acc><<<(unsigned)((a.nc + 31) / 32), kGT, 0, s>>>(part, (int)splits, a.nc, a.T, a.ldt, a.nbp, W);
-  k_update<TV, double, TC, Acc, BN><<<dim3((unsigned)((a.mr + kBM - 1) / kBM), (unsigned)tiles_n), kGT, 0, s>>>(
-      (const TV*)a.V, a.ldv, a.nbp, true, W, kBM, (TC*)a.C, a.ldc, a.mr, a.nc);
+  const double mnk = (double)a.mr * a.nbp * a.nc;
+  {
+    LaunchScope ls(K_VTC, s, 2.0 * mnk,
+                   (double)a.mr * a.nc * sizeof(TC) + (double)a.mr * a.nbp * sizeof(TV));
+    k_vtc<TV, TC, Acc, BN><<<dim3((unsigned)tiles_n, (unsigned)splits), kGT, 0, s>>>(
+        (const TV*)a.V, a.ldv, a.nbp, (const TC*)a.C, a.ldc, a.mr, a.nc, chunk, part);
+  }
+  {
+    LaunchScope ls(K_TW, s, (double)a.nbp * a.nbp * a.nc, (double)(splits + 1) * kBM * a.nc * 8);
+    k_tw<Acc><<<(unsigned)((a.nc + 31) / 32), kGT, 0, s>>>(part, (int)splits, a.nc, a.T, a.ldt, a.nbp, W);
+  }
+  {
+    LaunchScope ls(K_UPDATE, s, 2.0 * mnk,
+                   2.0 * a.mr * a.nc * sizeof(TC) + (double)a.mr * a.nbp * sizeof(TV));
+    k_update<TV, double, TC, Acc, BN><<<dim3((unsigned)((a.mr + kBM - 1) / kBM), (unsigned)tiles_n), kGT, 0, s>>>(
+        (const TV*)a.V, a.ldv, a.nbp, true, W, kBM, (TC*)a.C, a.ldc, a.mr, a.nc);
+  }
   CT_LAUNCH_CHECK();
   return CT_OK;
 }
@@ -241,6 +374,8 @@ namespace {
 template <typename TV, typename TB, typename Acc>
 void dense_update_t(const void* V, int64_t ldv, int K, const void* W, int64_t ldw, void* C,
                     int64_t ldc, int64_t mr, int64_t nc, cudaStream_t s) {
+  LaunchScope ls(K_UPDATE, s, 2.0 * mr * K * nc,
+                 2.0 * mr * nc * sizeof(TB) + (double)mr * K * sizeof(TV) + (double)K * nc * sizeof(TB));
   if (nc <= 16) {
     const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 15) / 16));
     k_update<TV, TB, TB, Acc, 16><<<grid, kGT, 0, s>>>((const TV*)V, ldv, K, false, (const TB*)W, ldw,
@@ -263,6 +398,41 @@ ct_status launch_dense_update(const void* V, bool v_f64, int64_t ldv, int K, con
   } else {
     if (v_f64) return CT_ERR_UNSUPPORTED;
     dense_update_t<float, float, float>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
+  }
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, const double* W,
+                                int64_t ldw, double* C, int64_t ldc, int64_t mr, int64_t nc,
+                                cudaStream_t s) {
+  if (mr <= 0 || nc <= 0 || K <= 0) return CT_OK;
+  LaunchScope ls(K_UPDATE, s, 2.0 * mr * K * nc, 16.0 * mr * nc + (double)mr * K * (v_f64 ? 8 : 4));
+  if (nc <= 16) {
+    const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 15) / 16));
+    if (v_f64) k_update_t<double, 16><<<grid, kGT, 0, s>>>((const double*)V, ldv, K, W, ldw, C, ldc, mr, nc);
+    else k_update_t<float, 16><<<grid, kGT, 0, s>>>((const float*)V, ldv, K, W, ldw, C, ldc, mr, nc);
+  } else {
+    const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 63) / 64));
+    if (v_f64) k_update_t<double, 64><<<grid, kGT, 0, s>>>((const double*)V, ldv, K, W, ldw, C, ldc, mr, nc);
+    else k_update_t<float, 64><<<grid, kGT, 0, s>>>((const float*)V, ldv, K, W, ldw, C, ldc, mr, nc);
+  }
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+ct_status launch_gemm_tn(const void* A, bool a_f64, int64_t lda, const double* R, int64_t ldr,
+                         double* Y, int64_t ldy, int64_t m, int64_t n, int64_t k, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return CT_OK;
+  LaunchScope ls(K_GEMM_TN, s, 2.0 * m * n * k, (double)m * n * (a_f64 ? 8 : 4) + 8.0 * (m + n) * k);
+  if (k <= 16) {
+    const dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((k + 15) / 16));
+    if (a_f64) k_gemm_tn<double, 16><<<grid, kGT, 0, s>>>((const double*)A, lda, R, ldr, Y, ldy, m, n, k);
+    else k_gemm_tn<float, 16><<<grid, kGT, 0, s>>>((const float*)A, lda, R, ldr, Y, ldy, m, n, k);
+  } else {
+    const dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((k + 63) / 64));
+    if (a_f64) k_gemm_tn<double, 64><<<grid, kGT, 0, s>>>((const double*)A, lda, R, ldr, Y, ldy, m, n, k);
+    else k_gemm_tn<float, 64><<<grid, kGT, 0, s>>>((const float*)A, lda, R, ldr, Y, ldy, m, n, k);
   }
   CT_LAUNCH_CHECK();
   return CT_OK;

@@ -77,6 +77,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 
 // ---------------------------------------------------------------------------
+// Launch accounting (profile.cu).  Construct a LaunchScope right before a
+// kernel launch and let it go out of scope right after: it counts the launch,
+// adds its algorithmic flops and bytes, and (when timing is enabled through
+// ct_profile_enable) brackets it with CUDA events on the launching stream.
+// ---------------------------------------------------------------------------
+enum KernelClass {
+  K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
+  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_COUNT
+};
+
+class LaunchScope {
+ public:
+  LaunchScope(int cls, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
+  ~LaunchScope();
+  LaunchScope(const LaunchScope&) = delete;
+  LaunchScope& operator=(const LaunchScope&) = delete;
+
+ private:
+  int cls_;
+  cudaStream_t s_;
+  void* start_;
+};
+
+// ---------------------------------------------------------------------------
 // Device properties cached per process (device 0 of the current context).
 // ---------------------------------------------------------------------------
 struct DeviceInfo {
@@ -149,6 +173,19 @@ int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di);
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
                              cudaStream_t s);
 ct_status launch_rank_check(ct_factor* f, cudaStream_t s);
+// B[0:n] <- R^{-T} B[0:n] (FP64).
+ct_status launch_trsm_t(const ct_factor* f, double* B, int64_t ldb, int64_t k, cudaStream_t s);
+// C(r, c) -= sum_{a<K} V(a, r) W(a, c) (V read transposed), FP64 C and W.
+ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, const double* W,
+                                int64_t ldw, double* C, int64_t ldc, int64_t mr, int64_t nc,
+                                cudaStream_t s);
+// Y = A^T R: A m x n (FP64 or FP32), R m x k FP64, Y n x k FP64.
+ct_status launch_gemm_tn(const void* A, bool a_f64, int64_t lda, const double* R, int64_t ldr,
+                         double* Y, int64_t ldy, int64_t m, int64_t n, int64_t k, cudaStream_t s);
+// Column-wise updates with per-column device scalars a[c]:
+//   mode 0: Y[:, c] += sign * a[c] * X[:, c];   mode 1: Y[:, c] = X[:, c] + a[c] * Y[:, c].
+ct_status launch_colwise(int mode, double sign, const double* a, const double* X, int64_t ldx,
+                         double* Y, int64_t ldy, int64_t rows, int64_t k, cudaStream_t s);
 
 // ---- utilities (util.cu) ---------------------------------------------------
 ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,

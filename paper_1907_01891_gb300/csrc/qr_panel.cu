@@ -242,6 +242,7 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   a.status = f->status;
   CT_CUDA_TRY(cudaMemsetAsync(f->barrier, 0, 2 * sizeof(unsigned long long), s));
   void* args[] = {&a};
+  LaunchScope ls(K_PANEL, s, 3.0 * (double)mr * nbp * nbp, 2.0 * (double)mr * nbp * sizeof(S));
   CT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel<S>, dim3(grid), dim3(kPT), args, smem, s));
   return CT_OK;
 }

@@ -52,11 +52,34 @@ __global__ void __launch_bounds__(256) k_add(const TD* __restrict__ D, int64_t l
   if (threadIdx.x == 0) xn2[c] = sx;
 }
 
+__global__ void __launch_bounds__(256) k_colwise(int mode, double sign, const double* __restrict__ a,
+                                                 const double* __restrict__ X, int64_t ldx,
+                                                 double* __restrict__ Y, int64_t ldy, int64_t rows) {
+  const int64_t c = blockIdx.y;
+  const double ac = a[c];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (mode == 0) Y[r + c * ldy] += sign * ac * X[r + c * ldx];
+    else Y[r + c * ldy] = X[r + c * ldx] + ac * Y[r + c * ldy];
+  }
+}
+
 }  // namespace
+
+ct_status launch_colwise(int mode, double sign, const double* a, const double* X, int64_t ldx,
+                         double* Y, int64_t ldy, int64_t rows, int64_t k, cudaStream_t s) {
+  if (rows <= 0 || k <= 0) return CT_OK;
+  LaunchScope ls(K_AXPY, s, 2.0 * rows * k, 24.0 * rows * k);
+  const unsigned gx = (unsigned)((rows + 255) / 256 < 128 ? (rows + 255) / 256 : 128);
+  k_colwise<<<dim3(gx, (unsigned)k), 256, 0, s>>>(mode, sign, a, X, ldx, Y, ldy, rows);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
 
 ct_status launch_col_norms2(const double* X, int64_t ldx, int64_t rows, int64_t k, double* out,
                             cudaStream_t s) {
   if (k <= 0) return CT_OK;
+  LaunchScope ls(K_NORMS, s, 2.0 * rows * k, 8.0 * rows * k);
   k_col_norms2<<<(unsigned)k, 256, 0, s>>>(X, ldx, rows, out);
   CT_LAUNCH_CHECK();
   return CT_OK;
@@ -65,6 +88,7 @@ ct_status launch_col_norms2(const double* X, int64_t ldx, int64_t rows, int64_t 
 ct_status launch_add_f32_to_f64(const float* D, int64_t ldd, double* X, int64_t ldx, int64_t rows,
                                 int64_t k, double* dnorm2, double* xnorm2, cudaStream_t s) {
   if (k <= 0) return CT_OK;
+  LaunchScope ls(K_ADD, s, 4.0 * rows * k, 20.0 * rows * k);
   k_add<float><<<(unsigned)k, 256, 0, s>>>(D, ldd, X, ldx, rows, dnorm2, xnorm2);
   CT_LAUNCH_CHECK();
   return CT_OK;
@@ -73,6 +97,7 @@ ct_status launch_add_f32_to_f64(const float* D, int64_t ldd, double* X, int64_t 
 ct_status launch_add_f64_to_f64(const double* D, int64_t ldd, double* X, int64_t ldx, int64_t rows,
                                 int64_t k, double* dnorm2, double* xnorm2, cudaStream_t s) {
   if (k <= 0) return CT_OK;
+  LaunchScope ls(K_ADD, s, 4.0 * rows * k, 24.0 * rows * k);
   k_add<double><<<(unsigned)k, 256, 0, s>>>(D, ldd, X, ldx, rows, dnorm2, xnorm2);
   CT_LAUNCH_CHECK();
   return CT_OK;

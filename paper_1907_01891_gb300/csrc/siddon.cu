@@ -133,16 +133,20 @@ ct_status launch_build_system(const ct_geometry* gg, ct_dtype dtype, double lamb
   if (st != CT_OK) return st;
   const int64_t rays = (int64_t)g.n_views * g.n_bins;
   const unsigned blocks = (unsigned)((rays + 127) / 128);
-  if (dtype == CT_F64) {
-    k_siddon<double><<<blocks, 128, 0, s>>>(g, (double*)A, lda);
-    if (lambda > 0.0)
-      k_lambda_rows<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double*)A, lda, rays, n, lambda);
-  } else {
-    k_siddon<float><<<blocks, 128, 0, s>>>(g, (float*)A, lda);
-    if (lambda > 0.0)
-      k_lambda_rows<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float*)A, lda, rays, n, lambda);
+  {
+    LaunchScope ls(K_SIDDON, s, 0.0, (double)rays * (g.nx + g.ny) * elem);
+    if (dtype == CT_F64) k_siddon<double><<<blocks, 128, 0, s>>>(g, (double*)A, lda);
+    else k_siddon<float><<<blocks, 128, 0, s>>>(g, (float*)A, lda);
   }
   CT_LAUNCH_CHECK();
+  if (lambda > 0.0) {
+    LaunchScope ls(K_SIDDON, s, 0.0, (double)n * elem);
+    if (dtype == CT_F64)
+      k_lambda_rows<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double*)A, lda, rays, n, lambda);
+    else
+      k_lambda_rows<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float*)A, lda, rays, n, lambda);
+    CT_LAUNCH_CHECK();
+  }
   return CT_OK;
 }
 

@@ -69,10 +69,12 @@ ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, in
     const size_t bytes = (size_t)rows * (size_t)cols * elem;
     const size_t n16 = bytes / 16;
     const unsigned grid = (unsigned)di.sms * 4;
+    LaunchScope ls(K_ZERO, s, 0.0, (double)bytes);
     k_zero_flat<<<grid, 512, 0, s>>>((uint4*)A, n16, (unsigned char*)A + n16 * 16, bytes - n16 * 16);
   } else {
     dim3 grid((unsigned)((rows + 255) / 256 < 64 ? (rows + 255) / 256 : 64),
               (unsigned)(cols < 65535 ? cols : 65535));
+    LaunchScope ls(K_ZERO, s, 0.0, (double)rows * cols * elem);
     if (elem == 8) k_zero_cols<double><<<grid, 256, 0, s>>>((double*)A, lda, rows, cols);
     else k_zero_cols<float><<<grid, 256, 0, s>>>((float*)A, lda, rows, cols);
   }
@@ -85,6 +87,8 @@ ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* ds
   if (rows <= 0 || cols <= 0) return CT_OK;
   dim3 grid((unsigned)((rows + 255) / 256 < 64 ? (rows + 255) / 256 : 64),
             (unsigned)(cols < 65535 ? cols : 65535));
+  LaunchScope ls(K_COPY, s, 0.0,
+                 (double)rows * cols * ((st == CT_F64 ? 8 : 4) + (dt == CT_F64 ? 8 : 4)));
   if (st == CT_F64 && dt == CT_F64)
     k_copy<double, double><<<grid, 256, 0, s>>>((const double*)src, lds, (double*)dst, ldd, rows, cols);
   else if (st == CT_F64 && dt == CT_F32)

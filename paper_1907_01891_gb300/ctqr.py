@@ -48,12 +48,25 @@ class QrOpts(ctypes.Structure):
 
 
 class RefineOpts(ctypes.Structure):
-    _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double)]
+    _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("method", ctypes.c_int)]
+
+
+REFINE_AUTO, REFINE_CLASSICAL, REFINE_CGLS = 0, 1, 2
 
 
 class Report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("last_update", ctypes.c_double),
-                ("residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("residual", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_build", ctypes.c_double), ("ms_factor", ctypes.c_double),
+                ("ms_solve", ctypes.c_double)]
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("timed", ctypes.c_uint64),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+CT_DEVICE_BUFFERS, CT_HOST_BUFFERS = 0, 1
 
 
 _lib = None
@@ -77,6 +90,12 @@ SIGNATURES = {
     "ct_reconstruct_batch": ([_VP, _VP, _I, _I64, _VP, _I64, _VP, _I64, _I64,
                               ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
     "ct_factor_destroy": ([_VP], None),
+    "ct_reconstruct_scan": ([ctypes.POINTER(Geometry), _D, _I, _VP, _I64, _VP, _I64, _I64, _I,
+                             ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
+    "ct_profile_enable": ([_I], None),
+    "ct_profile_reset": ([], None),
+    "ct_profile_kernels": ([ctypes.POINTER(KernelStats), _I], _I),
+    "ct_kernel_launches": ([], ctypes.c_uint64),
 }
 
 
@@ -266,10 +285,13 @@ class ReconReport:
     last_update: float
     residual: float
     ms_total: float
+    ms_build: float = 0.0
+    ms_factor: float = 0.0
+    ms_solve: float = 0.0
 
 
 def reconstruct(f: Factor, B: torch.Tensor, A: torch.Tensor | None = None, X: torch.Tensor | None = None,
-                max_iter: int = 0, tol: float = 0.0, check: bool = True):
+                max_iter: int = 0, tol: float = 0.0, method: int = REFINE_AUTO, check: bool = True):
     """X = R^{-1}(Q^T B)[0:n], refined with FP64 residuals against A when given.
     Returns (X, ReconReport)."""
     inf = f.info()
@@ -277,7 +299,7 @@ def reconstruct(f: Factor, B: torch.Tensor, A: torch.Tensor | None = None, X: to
     if X is None:
         X = colmajor(inf["n"], k, dtype=torch.float64)
     rep = Report()
-    ro = RefineOpts(max_iter, tol)
+    ro = RefineOpts(max_iter, tol, method)
     st = load().ct_reconstruct_batch(
         f.handle, A.data_ptr() if A is not None else None, _dt(A) if A is not None else CT_F64,
         _ld(A) if A is not None else 0, B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), k,
@@ -285,3 +307,59 @@ def reconstruct(f: Factor, B: torch.Tensor, A: torch.Tensor | None = None, X: to
     if check:
         _check(st, "ct_reconstruct_batch")
     return X, ReconReport(st, rep.iterations, rep.last_update, rep.residual, rep.ms_total)
+
+
+def reconstruct_scan(geom, B, X=None, prec: Prec = Prec.F64, lam: float = 0.0, max_iter: int = 0,
+                     tol: float = 0.0, method: int = REFINE_AUTO, check: bool = True):
+    """Whole method for one scan (build A, factor, reconstruct).  B and X are
+    either CUDA tensors (device buffers) or numpy arrays / CPU tensors (host
+    buffers, copied inside the call).  Returns (X, ReconReport)."""
+    m, n = system_size(geom, lam)
+    rep = Report()
+    ro = RefineOpts(max_iter, tol, method)
+    on_device = isinstance(B, torch.Tensor) and B.is_cuda
+    if on_device:
+        k = B.shape[1]
+        if X is None:
+            X = colmajor(n, k)
+        args = (B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), k, CT_DEVICE_BUFFERS)
+    else:
+        Bt = torch.as_tensor(B)
+        if Bt.dim() == 1:
+            Bt = Bt[:, None]
+        k = Bt.shape[1]
+        if not (Bt.dtype == torch.float64 and Bt.stride(0) == 1):
+            Bt = Bt.t().contiguous().t().to(torch.float64) if Bt.dtype != torch.float64 else Bt.t().contiguous().t()
+        if X is None:
+            X = torch.empty((k, n), dtype=torch.float64).t()
+        ldb = Bt.stride(1) if k > 1 else m
+        ldx = X.stride(1) if k > 1 else n
+        args = (Bt.data_ptr(), ldb, X.data_ptr(), ldx, k, CT_HOST_BUFFERS)
+        B = Bt
+    st = load().ct_reconstruct_scan(ctypes.byref(geometry(geom)), lam, int(prec), *args,
+                                    ctypes.byref(ro), ctypes.byref(rep), _stream())
+    if check:
+        _check(st, "ct_reconstruct_scan")
+    return X, ReconReport(st, rep.iterations, rep.last_update, rep.residual, rep.ms_total,
+                          rep.ms_build, rep.ms_factor, rep.ms_solve)
+
+
+def profile_enable(on: bool = True) -> None:
+    load().ct_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    load().ct_profile_reset()
+
+
+def profile_kernels() -> list[dict]:
+    lib = load()
+    n = lib.ct_profile_kernels(None, 0)
+    arr = (KernelStats * n)()
+    n = lib.ct_profile_kernels(arr, n)
+    return [dict(name=a.name.decode(), launches=a.launches, timed=a.timed, ms=a.ms, flops=a.flops,
+                 bytes=a.bytes) for a in arr[:n]]
+
+
+def kernel_launches() -> int:
+    return int(load().ct_kernel_launches())

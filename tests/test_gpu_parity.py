@@ -227,3 +227,53 @@ def test_in_place_factor_borrows_the_matrix():
     f = ctqr.qr_factor(At, in_place=True)
     Fo, _ = O.qr(A)
     assert np.abs(np.triu(_np(At)[:90]) - np.triu(Fo[:90])).max() <= 1e-11 * np.abs(Fo).max()
+
+
+def test_mixed_factor_cgls_reaches_least_squares_on_noisy_data():
+    """Noisy sinograms make A x = b inconsistent; the FP64 CGLS phase (R from
+    the FP32 factor as right preconditioner) must still land on the oracle's
+    least-squares solution."""
+    g = I.CONFIG4A["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    Anp = _np(A)
+    seeds = I.CONFIG4A["seeds"][:12]
+    b = I.poisson_noise(Anp @ I.phantoms(g, seeds), g.fov, I.CONFIG4A["noise_i0"], seed=77)
+    Xo = O.lstsq(Anp, b)
+    f = ctqr.qr_factor(A.to(torch.float32), prec=ctqr.Prec.F32)
+    for method in (ctqr.REFINE_AUTO, ctqr.REFINE_CGLS):
+        X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A, method=method)
+        err = np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo)
+        assert err <= 1e-10, (method, err, rep)
+    # classical refinement alone stalls above the target on inconsistent data
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A, method=ctqr.REFINE_CLASSICAL, max_iter=8,
+                              check=False)
+    assert rep.status in (ctqr.CT_OK, ctqr.CT_ERR_NOCONVERGE)
+
+
+def test_cgls_on_fp64_factor_and_fp32_system_matrix():
+    g = I.parallel_geometry(24, 40, 35)
+    A = ctqr.build_system(g, torch.float64)
+    Anp = _np(A)
+    b = I.poisson_noise(Anp @ I.phantoms(g, [4, 5]), g.fov, 1e4, seed=3)
+    Xo = O.lstsq(Anp, b)
+    f = ctqr.qr_factor(A)
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A, method=ctqr.REFINE_CGLS)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10
+    # residuals against an FP32 copy of A converge to the FP32 system's solution
+    A32 = A.to(torch.float32)
+    X32, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A32, method=ctqr.REFINE_CGLS, check=False)
+    A32np = _np(A32).astype(np.float64)
+    Xo32 = O.lstsq(A32np, b)
+    assert np.linalg.norm(_np(X32) - Xo32) / np.linalg.norm(Xo32) <= 1e-9
+
+
+def test_reconstruct_scan_host_and_device_buffers_agree():
+    g = I.CONFIG1["geom"]
+    Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+    b = Ao @ I.phantoms(g, [9, 10, 11])
+    Xh, rep = ctqr.reconstruct_scan(g, b, prec=ctqr.Prec.F32)
+    Xd, _ = ctqr.reconstruct_scan(g, ctqr.to_colmajor(b), prec=ctqr.Prec.F32)
+    Xo = O.lstsq(Ao, b)
+    assert np.linalg.norm(Xh.numpy() - Xo) / np.linalg.norm(Xo) <= 1e-10
+    assert np.linalg.norm(_np(Xd) - Xo) / np.linalg.norm(Xo) <= 1e-10
+    assert rep.ms_factor > 0 and rep.ms_build > 0 and rep.ms_solve > 0
