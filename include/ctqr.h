@@ -52,8 +52,9 @@ typedef enum { CT_F64 = 0, CT_F32 = 1 } ct_dtype;
  * C <- C - V T^T V^T C).  Panels, reflector norms and T factors are always
  * computed in FP64.  CT_PREC_F64: plain FP64 everywhere, factor stored in FP64.
  * CT_PREC_F32: factor stored in FP32, updates in FP32 (CUDA cores).
- * CT_PREC_TF32: factor stored in FP32, updates on the tensor cores in TF32
- * with FP32 accumulation. */
+ * CT_PREC_TF32: factor stored in FP32; 128-column outer blocks of 32-column
+ * panels, the outer trailing updates on the tensor cores (tcgen05) in TF32 with
+ * FP32 accumulation (error-compensated by default, see ct_qr_opts). */
 typedef enum { CT_PREC_F64 = 0, CT_PREC_F32 = 1, CT_PREC_TF32 = 2 } ct_prec;
 
 /* Scanner geometry (Sec. II-A and Table (scanner) describe the paper's fan-beam
@@ -85,10 +86,15 @@ typedef struct {
 
 /* Options of ct_qr_factor.  NULL selects the defaults. */
 typedef struct {
-  int nb;        /* panel width, 1..64 (0 = choose)                             */
-  int in_place;  /* 1: overwrite the caller's A with the factor and borrow it  */
-                 /*    (A must then have the factor's storage type and stay    */
-                 /*    alive until ct_factor_destroy); 0: copy A               */
+  int nb;          /* panel width, 1..64 (0 = choose; CT_PREC_TF32 needs a     */
+                   /* power of two <= 32)                                      */
+  int in_place;    /* 1: overwrite the caller's A with the factor and borrow  */
+                   /*    it (A must then have the factor's storage type and   */
+                   /*    stay alive until ct_factor_destroy); 0: copy A       */
+  int tf32_passes; /* CT_PREC_TF32 only: 3 (default, 0 = default) splits each  */
+                   /* operand into a TF32 high part and a low remainder and   */
+                   /* sums three tensor-core products (close to FP32          */
+                   /* accuracy); 1 uses plain TF32 (about 3 decimal digits)   */
 } ct_qr_opts;
 
 /* Opaque factorization: reflectors V and R (in the factored matrix), tau, and
@@ -99,6 +105,9 @@ typedef struct ct_factor ct_factor;
 /* Options of ct_reconstruct_batch's FP64 refinement.  NULL = defaults. */
 typedef struct {
   int max_iter;    /* iteration cap, all phases together (default 60)          */
+  double lambda;   /* > 0: the factored system is [A_rays; lambda*I] and the A */
+                   /* passed to ct_reconstruct_batch holds only its first     */
+                   /* m - n rows (the lambda*I rows are applied implicitly)   */
   double tol;      /* stop when every column has ||dx_c|| <= tol*||x_c||        */
                    /* (default 1e-12)                                          */
   int method;      /* 0 auto: classical refinement while its updates shrink     */
@@ -226,6 +235,24 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A,
                                int64_t ldb, double* X, int64_t ldx, int64_t k,
                                const ct_refine_opts* ropts, ct_report* report,
                                void* stream);
+
+/* Tensor-core contraction used by the trailing update (the paper's
+ * Apply_left_Qt_of_dense_QR task, Sec. II-C-3, applies a block reflector
+ * C - V T^T V^T C through two such products): C = A^T B (accumulate == 0) or
+ * C -= A^T B (accumulate == 1), with A K x M, B K x N and C M x N, all FP32
+ * column-major device matrices (lda >= K and ldb >= K multiples of 4, A and B
+ * 16-byte aligned, ldc >= M).  tcgen05 TF32 MMAs with FP32 accumulation;
+ * split3 = 1 splits each operand into a TF32 high part and a low remainder
+ * and sums hi*hi + hi*lo + lo*hi, recovering close to FP32 accuracy at three
+ * times the tensor work.  Asynchronous on `stream`; a timed-out device wait
+ * is reported as CT_ERR_TIMEOUT by the next ct_gemm_status call. */
+ct_status ct_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                          const float* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
+                          int split3, void* stream);
+
+/* Synchronise `stream` and return (and clear) the device status recorded by
+ * ct_gemm_tf32_tn calls. */
+ct_status ct_gemm_status(void* stream);
 
 /* Whole method for one scan: build A from `geom` on the device (Eq.
  * (sistema), stacked over lambda*I when lambda > 0), factor it (Eq. (QR)) with

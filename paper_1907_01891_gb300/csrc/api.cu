@@ -119,6 +119,9 @@ class Refiner {
   ct_status run(const ct_refine_opts* o, ct_report* rep) {
     const int max_iter = o && o->max_iter > 0 ? o->max_iter : 60;
     tol_ = o && o->tol > 0.0 ? o->tol : 1e-12;
+    lam_ = o && o->lambda > 0.0 ? o->lambda : 0.0;
+    ma_ = lam_ > 0.0 ? m_ - n_ : m_;
+    if (ma_ < 0) return CT_ERR_INVALID;
     const int method = o ? o->method : 0;
     ct_status st;
     if ((st = alloc()) != CT_OK) return st;
@@ -164,7 +167,8 @@ class Refiner {
   cudaStream_t s_;
   int sms_;
   int64_t m_, n_, ldw_;
-  double tol_ = 1e-12, last_ = INFINITY, resid_ = 0.0;
+  double tol_ = 1e-12, last_ = INFINITY, resid_ = 0.0, lam_ = 0.0;
+  int64_t ma_ = 0;  // rows of A (the lambda*I rows below it are implicit)
   size_t work_elems_ = 0;
   Scratch work_, Y_, D_, cg_, scal_;
   double *Yd_ = nullptr, *bn2_ = nullptr, *n1_ = nullptr, *n2_ = nullptr, *n3_ = nullptr, *a_ = nullptr;
@@ -194,11 +198,13 @@ class Refiner {
     return CT_OK;
   }
 
-  // Res = B - A X into Yd (m x k).
+  // Res = B - [A; lambda I] X into Yd (m x k).
   ct_status residual() {
     ct_status st;
     if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) return st;
-    return launch_dense_update(A_, a64_, lda_, (int)n_, X_, ldx_, Yd_, true, ldw_, m_, k_, s_);
+    if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, X_, ldx_, Yd_, true, ldw_, ma_, k_, s_)) != CT_OK) return st;
+    if (lam_ > 0.0) return launch_colwise(0, -lam_, nullptr, X_, ldx_, Yd_ + ma_, ldw_, n_, k_, s_);
+    return CT_OK;
   }
 
   // One classical step; with_residual = false is the first solve (X = 0).
@@ -236,10 +242,11 @@ class Refiner {
     return CT_OK;
   }
 
-  // s = R^{-T} (A^T r)  with r in Yd.
+  // s = R^{-T} ([A; lambda I]^T r)  with r in Yd.
   ct_status precond_grad(double* S) {
     ct_status st;
-    if ((st = launch_gemm_tn(A_, a64_, lda_, Yd_, ldw_, S, n_, m_, n_, k_, s_)) != CT_OK) return st;
+    if ((st = launch_gemm_tn(A_, a64_, lda_, Yd_, ldw_, S, n_, ma_, n_, k_, s_)) != CT_OK) return st;
+    if (lam_ > 0.0 && (st = launch_colwise(0, lam_, nullptr, Yd_ + ma_, ldw_, S, n_, n_, k_, s_)) != CT_OK) return st;
     return launch_trsm_t(f_, S, n_, k_, s_);
   }
 
@@ -264,7 +271,8 @@ class Refiner {
       if ((st = launch_copy_matrix(P_, CT_F64, n_, T_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
       if ((st = launch_trsm(f_, T_, true, n_, k_, s_)) != CT_OK) return st;
       if ((st = launch_zero_matrix(Q_, 8, ldw_, m_, k_, s_)) != CT_OK) return st;
-      if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, T_, n_, Q_, true, ldw_, m_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, T_, n_, Q_, true, ldw_, ma_, k_, s_)) != CT_OK) return st;
+      if (lam_ > 0.0 && (st = launch_colwise(0, -lam_, nullptr, T_, n_, Q_ + ma_, ldw_, n_, k_, s_)) != CT_OK) return st;
       if ((st = launch_col_norms2(Q_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;
       if ((st = launch_col_norms2(T_, n_, n_, k_, n2_, s_)) != CT_OK) return st;
       if ((st = launch_col_norms2(X_, ldx_, n_, k_, n3_, s_)) != CT_OK) return st;
@@ -350,7 +358,6 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   if (!A || !aligned16(A) || n < 1 || m < n || lda < m) return CT_ERR_INVALID;
   if (dtype != CT_F64 && dtype != CT_F32) return CT_ERR_INVALID;
   if (prec != CT_PREC_F64 && prec != CT_PREC_F32 && prec != CT_PREC_TF32) return CT_ERR_INVALID;
-  if (prec == CT_PREC_TF32) return CT_ERR_UNSUPPORTED;
   const ct_dtype store = prec == CT_PREC_F64 ? CT_F64 : CT_F32;
   const bool in_place = opts && opts->in_place;
   if (in_place && dtype != store) return CT_ERR_INVALID;
@@ -366,8 +373,12 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   f->prec = prec;
   f->store = store;
   f->device = di.device;
+  const bool tc = prec == CT_PREC_TF32;
+  const int passes = opts && opts->tf32_passes ? opts->tf32_passes : 3;
+  if (tc && passes != 1 && passes != 3) { delete f; return CT_ERR_INVALID; }
   int want = (opts && opts->nb) ? opts->nb : (prec == CT_PREC_F64 ? 64 : 32);
-  f->nb = panel_width_that_fits(m, want, di);
+  if (tc && (want > 32 || (want & (want - 1)))) { delete f; return CT_ERR_INVALID; }
+  f->nb = panel_width_that_fits(m, want, di, store == CT_F64 ? 8 : 4, tc);
   const size_t es = elem_size(store);
   if (in_place) {
     f->F = (void*)A;
@@ -398,28 +409,47 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   const size_t work_elems = reflector_work_elems(di.sms, f->nb, n);
   Scratch work;
   if ((st = work.alloc(work_elems * sizeof(double), s)) != CT_OK) { free_factor(f); return st; }
-
-  for (int64_t j0 = 0, p = 0; j0 < n; j0 += f->nb, ++p) {
-    const int nbp = (int)(n - j0 < f->nb ? n - j0 : f->nb);
-    double* Tp = f->T + (size_t)p * f->nb * f->nb;
-    st = launch_panel(f, j0, nbp, Tp, s);
-    if (st != CT_OK) { free_factor(f); return st; }
-    if (j0 + nbp < n) {
-      ReflectorArgs a;
-      a.V = (const char*)f->F + (size_t)(j0 + j0 * f->ld) * es;
-      a.v_f64 = store == CT_F64;
-      a.ldv = f->ld;
-      a.T = Tp;
-      a.ldt = f->nb;
-      a.nbp = nbp;
-      a.C = (char*)f->F + (size_t)(j0 + (j0 + nbp) * f->ld) * es;
-      a.c_f64 = store == CT_F64;
-      a.ldc = f->ld;
-      a.mr = m - j0;
-      a.nc = n - j0 - nbp;
-      a.fp32_math = store == CT_F32;
-      st = apply_block_reflector(a, (double*)work.p, work_elems, di.sms, s);
-      if (st != CT_OK) { free_factor(f); return st; }
+  // One panel (factor + update of the columns [j0+nbp, cend) to its right).
+  auto panel_step = [&](int64_t j0, int nbp, int64_t cend) -> ct_status {
+    double* Tp = f->T + (size_t)(j0 / f->nb) * f->nb * f->nb;
+    ct_status r = launch_panel(f, j0, nbp, Tp, s);
+    if (r != CT_OK || j0 + nbp >= cend) return r;
+    ReflectorArgs a;
+    a.V = (const char*)f->F + (size_t)(j0 + j0 * f->ld) * es;
+    a.v_f64 = store == CT_F64;
+    a.ldv = f->ld;
+    a.T = Tp;
+    a.ldt = f->nb;
+    a.nbp = nbp;
+    a.C = (char*)f->F + (size_t)(j0 + (j0 + nbp) * f->ld) * es;
+    a.c_f64 = store == CT_F64;
+    a.ldc = f->ld;
+    a.mr = m - j0;
+    a.nc = cend - j0 - nbp;
+    a.fp32_math = store == CT_F32;
+    return apply_block_reflector(a, (double*)work.p, work_elems, di.sms, s);
+  };
+  if (!tc) {
+    for (int64_t j0 = 0; j0 < n; j0 += f->nb) {
+      const int nbp = (int)(n - j0 < f->nb ? n - j0 : f->nb);
+      if ((st = panel_step(j0, nbp, n)) != CT_OK) { free_factor(f); return st; }
+    }
+  } else {
+    // 128-column outer blocks: inner panels update only their own block, the
+    // rest of the matrix gets one tensor-core update per outer block.
+    const size_t owf = outer_work_floats(di.sms, m, n);
+    Scratch owork;
+    if ((st = owork.alloc(owf * sizeof(float), s)) != CT_OK) { free_factor(f); return st; }
+    for (int64_t J = 0; J < n; J += 128) {
+      const int nbo = (int)(n - J < 128 ? n - J : 128);
+      for (int64_t j0 = J; j0 < J + nbo; j0 += f->nb) {
+        const int nbp = (int)(J + nbo - j0 < f->nb ? J + nbo - j0 : f->nb);
+        if ((st = panel_step(j0, nbp, J + nbo)) != CT_OK) { free_factor(f); return st; }
+      }
+      if ((st = outer_block_update(f, J, nbo, (float*)owork.p, owf, di.sms, passes == 3, s)) != CT_OK) {
+        free_factor(f);
+        return st;
+      }
     }
   }
   st = launch_rank_check(f, s);
@@ -495,7 +525,8 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A, ct_dtype A_dty
   if (!f || k < 0) return CT_ERR_INVALID;
   if (k == 0) return CT_OK;
   if (!B || !X || !aligned16(B) || !aligned16(X) || ldb < f->m || ldx < f->n) return CT_ERR_INVALID;
-  if (A && (!aligned16(A) || lda < f->m || (A_dtype != CT_F64 && A_dtype != CT_F32))) return CT_ERR_INVALID;
+  const int64_t a_rows = (ropts && ropts->lambda > 0.0) ? f->m - f->n : f->m;
+  if (A && (!aligned16(A) || lda < a_rows || (A_dtype != CT_F64 && A_dtype != CT_F32))) return CT_ERR_INVALID;
   cudaStream_t s = as_stream(stream);
   DeviceInfo di;
   ct_status st = device_info(&di);
@@ -567,16 +598,31 @@ ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec pr
     ldxd = n;
   }
   double* A = (double*)Abuf.p;
+  const bool mixed = prec != CT_PREC_F64;
+  const int64_t ma = lambda > 0.0 ? m - n : m;
+  Scratch F32buf;
+  if (mixed && (st = F32buf.alloc((size_t)lda * n * sizeof(float), s)) != CT_OK) return st;
   CT_CUDA_TRY(cudaEventRecord(ev[0], s));
-  if ((st = launch_build_system(geom, CT_F64, lambda, A, lda, m, n, s)) != CT_OK) return st;
+  if (!mixed) {
+    // FP64: build [A; lambda I] and factor it in place.
+    if ((st = launch_build_system(geom, CT_F64, lambda, A, lda, m, n, s)) != CT_OK) return st;
+  } else {
+    // Mixed: FP64 rays-only A for the residuals, FP32 [A; lambda I] to factor.
+    if ((st = launch_build_system(geom, CT_F64, 0.0, A, lda, ma, n, s)) != CT_OK) return st;
+    if ((st = launch_build_system(geom, CT_F32, lambda, F32buf.p, lda, m, n, s)) != CT_OK) return st;
+  }
   CT_CUDA_TRY(cudaEventRecord(ev[1], s));
   ct_factor* f = nullptr;
-  ct_qr_opts qo = {0, prec == CT_PREC_F64 ? 1 : 0};  // FP64: factor A in place
-  if ((st = ct_qr_factor(A, CT_F64, m, n, lda, prec, &qo, &f, stream)) != CT_OK) return st;
+  ct_qr_opts qo = {0, 1, 0};  // factor in place
+  if ((st = ct_qr_factor(mixed ? F32buf.p : (void*)A, mixed ? CT_F32 : CT_F64, m, n, lda, prec, &qo, &f,
+                         stream)) != CT_OK)
+    return st;
   CT_CUDA_TRY(cudaEventRecord(ev[2], s));
+  ct_refine_opts ro = ropts ? *ropts : ct_refine_opts{0, 0.0, 0.0, 0};
+  ro.lambda = lambda;
   ct_report rep;
-  ct_status rs = ct_reconstruct_batch(f, prec == CT_PREC_F64 ? nullptr : A, CT_F64, lda, Bd, ldbd, Xd,
-                                      ldxd, k, ropts, &rep, stream);
+  ct_status rs = ct_reconstruct_batch(f, mixed ? A : nullptr, CT_F64, lda, Bd, ldbd, Xd, ldxd, k, &ro, &rep,
+                                      stream);
   cudaError_t ce = cudaEventRecord(ev[3], s);
   if (ce == cudaSuccess && host)
     ce = cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, ldxd * sizeof(double), n * sizeof(double), k,
@@ -593,6 +639,41 @@ ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec pr
     report->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   }
   return rs;
+}
+
+static int* gemm_status_word(ct_status* err) {
+  static int* word = nullptr;
+  if (!word) {
+    if (cudaMalloc((void**)&word, sizeof(int)) != cudaSuccess || cudaMemset(word, 0, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      word = nullptr;
+      *err = CT_ERR_NOMEM;
+    }
+  }
+  return word;
+}
+
+ct_status ct_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                          int64_t ldb, float* C, int64_t ldc, int accumulate, int split3, void* stream) {
+  if (M < 0 || N < 0 || K < 0) return CT_ERR_INVALID;
+  if (M == 0 || N == 0) return CT_OK;
+  ct_status err = CT_OK;
+  int* status = gemm_status_word(&err);
+  if (!status) return err;
+  return tc_gemm_tn(A, lda, B, ldb, M, N, K, C, ldc, 0, accumulate ? 1 : 0, 1, split3 != 0, status,
+                    as_stream(stream));
+}
+
+ct_status ct_gemm_status(void* stream) {
+  ct_status err = CT_OK;
+  int* status = gemm_status_word(&err);
+  if (!status) return err;
+  int h = 0;
+  cudaStream_t s = as_stream(stream);
+  CT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CT_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h != 0) CT_CUDA_TRY(cudaMemset(status, 0, sizeof(int)));
+  return (ct_status)h;
 }
 
 void ct_factor_destroy(ct_factor* f) {

@@ -169,7 +169,13 @@ ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int6
 ct_status launch_dense_update(const void* V, bool v_f64, int64_t ldv, int K, const void* W,
                               int64_t ldw, void* C, bool b_f64, int64_t ldc, int64_t mr, int64_t nc,
                               cudaStream_t s);
-int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di);
+int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth, bool pow2);
+// Tensor-core update of C = F[J:m, J+nbo:n] with the 128-column block
+// reflector of F[J:m, J:J+nbo] (outer_update.cu); work holds
+// outer_work_floats(...) floats.
+size_t outer_work_floats(int sms, int64_t m, int64_t n);
+ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
+                             bool split3, cudaStream_t s);
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
                              cudaStream_t s);
 ct_status launch_rank_check(ct_factor* f, cudaStream_t s);
@@ -182,10 +188,19 @@ ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, c
 // Y = A^T R: A m x n (FP64 or FP32), R m x k FP64, Y n x k FP64.
 ct_status launch_gemm_tn(const void* A, bool a_f64, int64_t lda, const double* R, int64_t ldr,
                          double* Y, int64_t ldy, int64_t m, int64_t n, int64_t k, cudaStream_t s);
-// Column-wise updates with per-column device scalars a[c]:
+// Column-wise updates with per-column device scalars a[c] (a == NULL: 1):
 //   mode 0: Y[:, c] += sign * a[c] * X[:, c];   mode 1: Y[:, c] = X[:, c] + a[c] * Y[:, c].
 ct_status launch_colwise(int mode, double sign, const double* a, const double* X, int64_t ldx,
                          double* Y, int64_t ldy, int64_t rows, int64_t k, cudaStream_t s);
+
+// ---- tensor-core GEMM (tc_gemm.cu) ---------------------------------------
+// C (M x N) = A^T B (mode 0; split z of `splits` writes C + z*split_stride) or
+// C -= A^T B (mode 1, splits must be 1); A is K x M, B is K x N, all FP32
+// column-major, lda/ldb multiples of 4, A/B 16-byte aligned.  split3 selects
+// error-compensated TF32 (hi*hi + hi*lo + lo*hi).
+ct_status tc_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,
+                     int64_t K, float* C, int64_t ldc, int64_t split_stride, int mode, int splits,
+                     bool split3, int* status, cudaStream_t s);
 
 // ---- utilities (util.cu) ---------------------------------------------------
 ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,

@@ -56,13 +56,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <typename S>
+// S: storage type of the matrix; Mth: arithmetic of the panel's dot products
+// and rank-1 updates (double for the FP64 factorization; float for the
+// mixed-precision one, where sigma, alpha, beta, tau and T stay FP64).
+template <typename S, typename Mth>
 __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   extern __shared__ double smem[];
-  double* slab = smem;                              // [nbp][rp], column-major
-  double* red = slab + (size_t)a.nbp * a.rp;        // [2*kMaxNb] reduced values
-  double* wv = red + 2 * kMaxNb;                    // [kMaxNb]  w_c
-  double* scratch = wv + kMaxNb;                    // [kNW][2*kMaxNb]
+  double* red = smem;                               // [2*kMaxNb] reduced values
+  double* wvd = red + 2 * kMaxNb;                   // [kMaxNb]  w_c
+  double* scratch = wvd + kMaxNb;                   // [kNW][2*kMaxNb]
+  Mth* slab = (Mth*)(scratch + kNW * 2 * kMaxNb);   // [nbp][rp], column-major
   __shared__ int s_last;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   S* P = (S*)a.P;
 
   for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < nr; r += kPT) slab[(size_t)c * rp + r] = (double)P[rb + r + c * a.ld];
+    for (int r = tid; r < nr; r += kPT) slab[(size_t)c * rp + r] = (Mth)P[rb + r + c * a.ld];
   __syncthreads();
 
   for (int k = 0; k < nbp; ++k) {
@@ -82,16 +85,23 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
     const int kl = (int)(k - rb);                    // its local index when owner
     const int first = (int)(k + 1 - rb > 0 ? (k + 1 - rb < nr ? k + 1 - rb : nr) : 0);
     double* part = a.col_part + ((size_t)(k & 1) * a.grid + blockIdx.x) * (2 * kMaxNb);
-    const double* colk = slab + (size_t)k * rp;
-    // Partial vector: [q] = d_{k+q} (q = 0 is sigma), [ne + q] = a_{k, k+q}.
+    const Mth* colk = slab + (size_t)k * rp;
+    // Partial vector: [q] = d_{k+q} (q = 0 is sigma, always accumulated in
+    // FP64), [ne + q] = a_{k, k+q}.
     for (int q = warp; q < ne; q += kNW) {
-      const double* colc = slab + (size_t)(k + q) * rp;
+      const Mth* colc = slab + (size_t)(k + q) * rp;
       double s = 0.0;
-      for (int r = first + lane; r < nr; r += 32) s += colk[r] * colc[r];
+      if (q == 0) {
+        for (int r = first + lane; r < nr; r += 32) s += (double)colk[r] * (double)colk[r];
+      } else {
+        Mth sm = (Mth)0;
+        for (int r = first + lane; r < nr; r += 32) sm += colk[r] * colc[r];
+        s = (double)sm;
+      }
       s = warp_sum(s);
       if (lane == 0) {
         part[q] = s;
-        part[ne + q] = owner ? colc[kl] : 0.0;
+        part[ne + q] = owner ? (double)colc[kl] : 0.0;
       }
     }
     if (!grid_barrier(&a.bar[0], a.grid, a.status, kBarrierLimitNs)) return;
@@ -129,18 +139,19 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
       tau = (beta - alpha) / beta;
       scale = 1.0 / (alpha - beta);
     }
-    if (tid > 0 && tid < ne) wv[tid] = tau * (red[ne + tid] + scale * red[tid]);
+    if (tid > 0 && tid < ne) wvd[tid] = tau * (red[ne + tid] + scale * red[tid]);
     __syncthreads();
     if (tau != 0.0) {
+      const Mth sc = (Mth)scale;
       for (int r = first + tid; r < nr; r += kPT) {
-        double* colr = slab + r;
-        const double v = colr[(size_t)k * rp] * scale;
+        Mth* colr = slab + r;
+        const Mth v = colr[(size_t)k * rp] * sc;
         colr[(size_t)k * rp] = v;
-        for (int q = 1; q < ne; ++q) colr[(size_t)(k + q) * rp] -= wv[q] * v;
+        for (int q = 1; q < ne; ++q) colr[(size_t)(k + q) * rp] -= (Mth)wvd[q] * v;
       }
-      if (owner && tid > 0 && tid < ne) slab[(size_t)(k + tid) * rp + kl] -= wv[tid];
+      if (owner && tid > 0 && tid < ne) slab[(size_t)(k + tid) * rp + kl] -= (Mth)wvd[tid];
     }
-    if (owner && tid == 0) slab[(size_t)k * rp + kl] = beta;
+    if (owner && tid == 0) slab[(size_t)k * rp + kl] = (Mth)beta;
     if (blockIdx.x == 0 && tid == 0) a.tau[k] = tau;
     __syncthreads();
   }
@@ -159,8 +170,8 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
       for (int r = lane; r < nr; r += 32) {
         const int64_t gr = rb + r;
         if (gr < j) continue;  // v_j vanishes above its diagonal
-        const double vj = gr == j ? 1.0 : slab[(size_t)j * rp + r];
-        const double vi = gr == i ? 1.0 : (gr > i ? slab[(size_t)i * rp + r] : 0.0);
+        const double vj = gr == j ? 1.0 : (double)slab[(size_t)j * rp + r];
+        const double vi = gr == i ? 1.0 : (gr > i ? (double)slab[(size_t)i * rp + r] : 0.0);
         s += vi * vj;
       }
       s = warp_sum(s);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   if (!s_last) return;
   __threadfence();
 
-  // Last CTA: total Gram (fixed CTA order) and T.
+  // Last CTA: total Gram (fixed CTA order) and T (FP64 either way).
   double* G = smem;                  // [npairs]
   double* Tm = G + npairs;           // [nbp][nbp] column-major
   double* tcol = Tm + nbp * nbp;     // [nbp]
@@ -206,7 +217,14 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   }
 }
 
-template <typename S>
+size_t panel_smem_bytes(int nbp, int rp, size_t mth) {
+  const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb) * sizeof(double);
+  size_t bytes = small + (size_t)nbp * rp * mth;
+  const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
+  return bytes < t_need ? t_need : bytes;
+}
+
+template <typename S, typename Mth>
 ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStream_t s,
                          const DeviceInfo& di) {
   const int64_t mr = f->m - j0;
@@ -214,15 +232,11 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   if (grid > di.sms) grid = di.sms;
   if (grid < 1) grid = 1;
   int rp = (int)((mr + grid - 1) / grid);
-  const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb);
-  size_t smem_d = (size_t)nbp * rp + small;
-  const size_t t_need = (size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp;
-  if (smem_d < t_need) smem_d = t_need;
-  const size_t smem = smem_d * sizeof(double);
+  const size_t smem = panel_smem_bytes(nbp, rp, sizeof(Mth));
   if (smem > (size_t)di.smem_optin) return CT_ERR_UNSUPPORTED;
-  CT_CUDA_TRY(cudaFuncSetAttribute(k_panel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CT_CUDA_TRY(cudaFuncSetAttribute(k_panel<S, Mth>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel<S>, kPT, smem));
+  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel<S, Mth>, kPT, smem));
   if (per_sm < 1) return CT_ERR_UNSUPPORTED;
   if (grid > per_sm * di.sms) return CT_ERR_UNSUPPORTED;
 
@@ -243,7 +257,7 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   CT_CUDA_TRY(cudaMemsetAsync(f->barrier, 0, 2 * sizeof(unsigned long long), s));
   void* args[] = {&a};
   LaunchScope ls(K_PANEL, s, 3.0 * (double)mr * nbp * nbp, 2.0 * (double)mr * nbp * sizeof(S));
-  CT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel<S>, dim3(grid), dim3(kPT), args, smem, s));
+  CT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel<S, Mth>, dim3(grid), dim3(kPT), args, smem, s));
   return CT_OK;
 }
 
@@ -254,15 +268,15 @@ size_t panel_partials_elems(int sms, int nb) {
   return (size_t)2 * sms * 2 * kMaxNb + (size_t)sms * (kMaxNb * (kMaxNb - 1) / 2);
 }
 
-// Largest panel width <= want whose shared-memory slab fits for mr rows.
-int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di) {
+// Largest panel width <= want (halving when pow2) whose shared-memory slab
+// fits for mr rows; mth = bytes of the panel arithmetic type.
+int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth, bool pow2) {
   int grid = (int)((mr + 63) / 64);
   if (grid > di.sms) grid = di.sms;
   if (grid < 1) grid = 1;
-  const int64_t rp = (mr + grid - 1) / grid;
-  const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb);
+  const int rp = (int)((mr + grid - 1) / grid);
   int nb = want > kMaxNb ? kMaxNb : want;
-  while (nb > 8 && ((size_t)nb * rp + small) * sizeof(double) > (size_t)di.smem_optin) nb -= 8;
+  while (nb > 8 && panel_smem_bytes(nb, rp, mth) > (size_t)di.smem_optin) nb = pow2 ? nb / 2 : nb - 8;
   return nb;
 }
 
@@ -271,8 +285,8 @@ ct_status launch_panel(ct_factor* f, int64_t j0, int nbp, double* T, cudaStream_
   DeviceInfo di;
   ct_status st = device_info(&di);
   if (st != CT_OK) return st;
-  return f->store == CT_F64 ? launch_panel_t<double>(f, j0, nbp, T, s, di)
-                            : launch_panel_t<float>(f, j0, nbp, T, s, di);
+  return f->store == CT_F64 ? launch_panel_t<double, double>(f, j0, nbp, T, s, di)
+                            : launch_panel_t<float, float>(f, j0, nbp, T, s, di);
 }
 
 }  // namespace ctqr

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_colwise(int mode, double sign, const do
                                                  const double* __restrict__ X, int64_t ldx,
                                                  double* __restrict__ Y, int64_t ldy, int64_t rows) {
   const int64_t c = blockIdx.y;
-  const double ac = a[c];
+  const double ac = a ? a[c] : 1.0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
        r += (int64_t)gridDim.x * blockDim.x) {
     if (mode == 0) Y[r + c * ldy] += sign * ac * X[r + c * ldx];

@@ -1,0 +1,399 @@
+// tc_gemm.cu -- tensor-core (tcgen05, TF32) GEMM for the trailing update.
+//
+//   C (M x N)  =  A^T B        (mode 0: store; split z writes C + z*split_stride)
+//   C (M x N) -=  A^T B        (mode 1)
+// with A stored K x M and B stored K x N, both column-major FP32 (so both
+// operands are K-major, the canonical tcgen05 layout), C column-major FP32.
+// This one "TN" form covers both contractions of the block-reflector update
+// C <- C - V (T^T (V^T C)) (the paper's Apply_left_Qt_of_dense_QR task):
+// V^T C uses A = V (column-major) and B = C; the update V W uses A = V stored
+// row-major (K = reflectors contiguous) and B = W.
+//
+// Structure (one 128 x BN output tile per CTA, optional split-K over z):
+//   warp 0 (one lane)  TMA producer: 128B-swizzled 32-float K slices of A and
+//                      B into a STAGES-deep shared-memory ring, mbarrier
+//                      expect_tx completion;
+//   warp 1 (one lane)  allocates TMEM and issues tcgen05.mma.kind::tf32
+//                      (M = 128, N = BN, K = 8 each, 4 per slice), committing
+//                      each stage back to the producer;
+//   warps 2-5          split3: turn each landed slice x into a TF32-exact high
+//                      part hi = trunc_tf32(x) (in place) and a low part
+//                      lo = x - hi, so the three products hi*hi + hi*lo + lo*hi
+//                      recover FP32-level accuracy (error-compensated TF32);
+//                      afterwards they drain the FP32 accumulator from TMEM
+//                      with tcgen05.ld and apply the epilogue (coalesced
+//                      column-major stores, one row per thread).
+// Every wait is bounded (CT_ERR_TIMEOUT in the status word, then an orderly
+// exit that still waits for issued copies and MMAs and frees TMEM).
+#include <cuda.h>
+
+#include "internal.cuh"
+
+namespace ctqr {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 32;  // floats per K slice = one 128-byte swizzle row
+constexpr int kThreads = 192;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+struct TcArgs {
+  int64_t M, N, K;
+  int64_t k_chunk;
+  float* C;
+  int64_t ldc;
+  int64_t split_stride;
+  int mode;
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity.  With
+// bail = true it also gives up as soon as another thread recorded an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, bool bail = true) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u) {
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      if (bail && ld_volatile_i32(status) != 0) return false;
+      if (now - t0 > kWaitLimitNs) {
+        set_status(status, CT_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), fixed field 0b001 at bit 46.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
+  const uint64_t a = smem_u32(p);
+  uint64_t d = (a >> 4) & 0x3FFFull;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_trunc(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+template <int BN, int STAGES, bool SPLIT3>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs args) {
+  constexpr uint32_t A_BYTES = kBM * kBK * 4;
+  constexpr uint32_t B_BYTES = BN * kBK * 4;
+  constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT3 ? 2 : 1);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* conv = full + STAGES;
+  uint64_t* empty = conv + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kBM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * args.k_chunk;
+  int64_t kend = kbeg + args.k_chunk;
+  if (kend > args.K) kend = args.K;
+  const int nk = kend > kbeg ? (int)((kend - kbeg + kBK - 1) / kBK) : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 4);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int kt = 0; kt < nk && ok; ++kt) {
+        const int s = kt % STAGES, u = kt / STAGES;
+        if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), args.status)) { ok = false; break; }
+        unsigned char* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        const int x = (int)(kbeg + (int64_t)kt * kBK);
+        tma_load_2d(st, &tmA, x, (int)m0, &full[s]);
+        tma_load_2d(st + A_BYTES, &tmB, x, (int)n0, &full[s]);
+        ++issued;
+      }
+      if (!ok) {
+        // Error exit: let the copies already issued land before the CTA ends.
+        for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+          mbar_wait(&full[kt % STAGES], (uint32_t)((kt / STAGES) & 1), args.status, false);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(kBM >> 4) << 24);
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES, u = kt / STAGES;
+        if (!mbar_wait(SPLIT3 ? &conv[s] : &full[s], (uint32_t)(u & 1), args.status)) break;
+        tc_fence_after();
+        unsigned char* st = smem + s * STAGE_BYTES;
+        const uint64_t da = sdesc_sw128(st), db = sdesc_sw128(st + A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 8; ++kk) {
+          const uint64_t adv = (uint64_t)(kk * 2);  // 8 floats = 32 bytes = 2 x 16 B
+          mma_tf32(tmem, da + adv, db + adv, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          if (SPLIT3) {
+            const uint64_t dal = sdesc_sw128(st + A_BYTES + B_BYTES);
+            const uint64_t dbl = sdesc_sw128(st + 2 * A_BYTES + B_BYTES);
+            mma_tf32(tmem, dal + adv, db + adv, idesc, 1u);
+            mma_tf32(tmem, da + adv, dbl + adv, idesc, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(done);
+    }
+  } else {
+    // warps 2..5
+    const int cw = warp - 2;  // 0..3
+    if (SPLIT3) {
+      const int t = cw * 32 + lane;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES, u = kt / STAGES;
+        if (!mbar_wait(&full[s], (uint32_t)(u & 1), args.status)) break;
+        unsigned char* st = smem + s * STAGE_BYTES;
+        float4* a = (float4*)st;
+        float4* b = (float4*)(st + A_BYTES);
+        float4* alo = (float4*)(st + A_BYTES + B_BYTES);
+        float4* blo = (float4*)(st + 2 * A_BYTES + B_BYTES);
+        for (int i = t; i < (int)(A_BYTES / 16); i += 128) {
+          const float4 x = a[i];
+          const float4 h = make_float4(tf32_trunc(x.x), tf32_trunc(x.y), tf32_trunc(x.z), tf32_trunc(x.w));
+          a[i] = h;
+          alo[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        for (int i = t; i < (int)(B_BYTES / 16); i += 128) {
+          const float4 x = b[i];
+          const float4 h = make_float4(tf32_trunc(x.x), tf32_trunc(x.y), tf32_trunc(x.z), tf32_trunc(x.w));
+          b[i] = h;
+          blo[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[s]);
+      }
+    }
+    // Epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 = tile rows.
+    if (mbar_wait(done, 0u, args.status)) {
+      tc_fence_after();
+      const int lg = warp & 3;
+      const int64_t row = m0 + lg * 32 + lane;
+      float* C = args.C + (args.mode == 0 ? (int64_t)blockIdx.z * args.split_stride : 0);
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c, v);
+        if (nk == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (row < args.M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t col = n0 + c + j;
+            if (col < args.N) {
+              float* p = C + row + col * args.ldc;
+              if (args.mode == 0) *p = v[j];
+              else *p -= v[j];
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor: d0 contiguous elements per column, d1 columns, column
+// stride ld elements; boxes of box0 x box1 with 128-byte swizzle.
+bool make_map(CUtensorMap* m, const float* base, uint64_t d0, uint64_t d1, uint64_t ld, uint32_t box0,
+              uint32_t box1) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {d0, d1};
+  cuuint64_t strides[1] = {ld * 4};
+  cuuint32_t box[2] = {box0, box1};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES, bool SPLIT3>
+ct_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int splits, cudaStream_t s) {
+  constexpr size_t STAGE_BYTES = (size_t)(kBM + BN) * kBK * 4 * (SPLIT3 ? 2 : 1);
+  const size_t smem = STAGES * STAGE_BYTES + 1024 + 256;
+  static bool attr_done = false;
+  if (!attr_done) {
+    CT_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm_tn<BN, STAGES, SPLIT3>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_done = true;
+  }
+  const dim3 grid((unsigned)((a.M + kBM - 1) / kBM), (unsigned)((a.N + BN - 1) / BN), (unsigned)splits);
+  k_tc_gemm_tn<BN, STAGES, SPLIT3><<<grid, kThreads, smem, s>>>(ma, mb, a);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+}  // namespace
+
+// C (M x N) = / -= A^T B on the tensor cores; see the file comment.
+ct_status tc_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,
+                     int64_t K, float* C, int64_t ldc, int64_t split_stride, int mode, int splits,
+                     bool split3, int* status, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return CT_OK;
+  if (!A || !B || !C || K < 0 || lda < K || ldb < K || ldc < M) return CT_ERR_INVALID;
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || (lda & 3) || (ldb & 3)) return CT_ERR_INVALID;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return CT_ERR_INVALID;
+  if (splits < 1) splits = 1;
+  int64_t chunk = (K + splits - 1) / splits;
+  chunk = (chunk + kBK - 1) / kBK * kBK;
+  if (chunk < kBK) chunk = kBK;
+  splits = (int)((K + chunk - 1) / chunk);
+  if (splits < 1) splits = 1;
+  if (mode == 0 && splits > 1 && split_stride < ldc * N) return CT_ERR_INVALID;
+  if (mode != 0 && splits > 1) return CT_ERR_INVALID;  // in-place subtraction must not be split
+  CUtensorMap ma, mb;
+  const uint64_t kd = K > 0 ? (uint64_t)K : 1;
+  constexpr int BN = 128;
+  if (!make_map(&ma, A, kd, (uint64_t)M, (uint64_t)lda, kBK, kBM)) return CT_ERR_CUDA;
+  if (!make_map(&mb, B, kd, (uint64_t)N, (uint64_t)ldb, kBK, BN)) return CT_ERR_CUDA;
+  TcArgs a;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.k_chunk = chunk;
+  a.C = C;
+  a.ldc = ldc;
+  a.split_stride = split_stride;
+  a.mode = mode;
+  a.status = status;
+  LaunchScope ls(K_TC_GEMM, s, 2.0 * M * N * K,
+                 4.0 * ((double)K * (M + N) + (mode == 0 ? 1.0 : 2.0) * M * N));
+  if (split3) return launch_tc<BN, 3, true>(ma, mb, a, splits, s);
+  return launch_tc<BN, 6, false>(ma, mb, a, splits, s);
+}
+
+}  // namespace ctqr

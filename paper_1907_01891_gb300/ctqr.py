@@ -44,11 +44,12 @@ class Geometry(ctypes.Structure):
 
 
 class QrOpts(ctypes.Structure):
-    _fields_ = [("nb", ctypes.c_int), ("in_place", ctypes.c_int)]
+    _fields_ = [("nb", ctypes.c_int), ("in_place", ctypes.c_int), ("tf32_passes", ctypes.c_int)]
 
 
 class RefineOpts(ctypes.Structure):
-    _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("method", ctypes.c_int)]
+    _fields_ = [("max_iter", ctypes.c_int), ("lambda_", ctypes.c_double), ("tol", ctypes.c_double),
+                ("method", ctypes.c_int)]
 
 
 REFINE_AUTO, REFINE_CLASSICAL, REFINE_CGLS = 0, 1, 2
@@ -92,6 +93,8 @@ SIGNATURES = {
     "ct_factor_destroy": ([_VP], None),
     "ct_reconstruct_scan": ([ctypes.POINTER(Geometry), _D, _I, _VP, _I64, _VP, _I64, _I64, _I,
                              ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
+    "ct_gemm_tf32_tn": ([_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _I, _I, _VP], _I),
+    "ct_gemm_status": ([_VP], _I),
     "ct_profile_enable": ([_I], None),
     "ct_profile_reset": ([], None),
     "ct_profile_kernels": ([ctypes.POINTER(KernelStats), _I], _I),
@@ -152,7 +155,7 @@ def _ld(t: torch.Tensor) -> int:
         raise ValueError("expected a 2-D tensor")
     if t.stride(0) != 1 and t.shape[0] > 1:
         raise ValueError("expected a column-major tensor (stride(0) == 1); use colmajor()")
-    return max(t.stride(1), t.shape[0], 1) if t.shape[1] > 1 else max(t.shape[0], 1)
+    return max(t.stride(1), t.shape[0], 1)
 
 
 def colmajor(rows: int, cols: int, dtype=torch.float64, device="cuda", ld: int | None = None,
@@ -244,10 +247,11 @@ class Factor:
             pass
 
 
-def qr_factor(A: torch.Tensor, prec: Prec = Prec.F64, nb: int = 0, in_place: bool = False) -> Factor:
+def qr_factor(A: torch.Tensor, prec: Prec = Prec.F64, nb: int = 0, in_place: bool = False,
+              tf32_passes: int = 0) -> Factor:
     m, n = A.shape
     h = ctypes.c_void_p()
-    opts = QrOpts(nb, 1 if in_place else 0)
+    opts = QrOpts(nb, 1 if in_place else 0, tf32_passes)
     _check(load().ct_qr_factor(A.data_ptr(), _dt(A), m, n, _ld(A), int(prec), ctypes.byref(opts),
                                ctypes.byref(h), _stream()), "ct_qr_factor")
     return Factor(h.value, keep=A if in_place else None)
@@ -291,7 +295,8 @@ class ReconReport:
 
 
 def reconstruct(f: Factor, B: torch.Tensor, A: torch.Tensor | None = None, X: torch.Tensor | None = None,
-                max_iter: int = 0, tol: float = 0.0, method: int = REFINE_AUTO, check: bool = True):
+                max_iter: int = 0, tol: float = 0.0, method: int = REFINE_AUTO, lam: float = 0.0,
+                check: bool = True):
     """X = R^{-1}(Q^T B)[0:n], refined with FP64 residuals against A when given.
     Returns (X, ReconReport)."""
     inf = f.info()
@@ -299,7 +304,7 @@ def reconstruct(f: Factor, B: torch.Tensor, A: torch.Tensor | None = None, X: to
     if X is None:
         X = colmajor(inf["n"], k, dtype=torch.float64)
     rep = Report()
-    ro = RefineOpts(max_iter, tol, method)
+    ro = RefineOpts(max_iter, lam, tol, method)
     st = load().ct_reconstruct_batch(
         f.handle, A.data_ptr() if A is not None else None, _dt(A) if A is not None else CT_F64,
         _ld(A) if A is not None else 0, B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), k,
@@ -316,7 +321,7 @@ def reconstruct_scan(geom, B, X=None, prec: Prec = Prec.F64, lam: float = 0.0, m
     buffers, copied inside the call).  Returns (X, ReconReport)."""
     m, n = system_size(geom, lam)
     rep = Report()
-    ro = RefineOpts(max_iter, tol, method)
+    ro = RefineOpts(max_iter, 0.0, tol, method)
     on_device = isinstance(B, torch.Tensor) and B.is_cuda
     if on_device:
         k = B.shape[1]
@@ -342,6 +347,23 @@ def reconstruct_scan(geom, B, X=None, prec: Prec = Prec.F64, lam: float = 0.0, m
         _check(st, "ct_reconstruct_scan")
     return X, ReconReport(st, rep.iterations, rep.last_update, rep.residual, rep.ms_total,
                           rep.ms_build, rep.ms_factor, rep.ms_solve)
+
+
+def gemm_tf32_tn(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, accumulate: bool = False,
+                 split3: bool = True) -> torch.Tensor:
+    """C = A^T B (or C -= A^T B) on the tensor cores; A is K x M, B is K x N,
+    FP32 column-major."""
+    K, M = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = colmajor(M, N, dtype=torch.float32)
+    _check(load().ct_gemm_tf32_tn(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                                  1 if accumulate else 0, 1 if split3 else 0, _stream()), "ct_gemm_tf32_tn")
+    return C
+
+
+def gemm_status() -> int:
+    return load().ct_gemm_status(_stream())
 
 
 def profile_enable(on: bool = True) -> None:

@@ -277,3 +277,68 @@ def test_reconstruct_scan_host_and_device_buffers_agree():
     assert np.linalg.norm(Xh.numpy() - Xo) / np.linalg.norm(Xo) <= 1e-10
     assert np.linalg.norm(_np(Xd) - Xo) / np.linalg.norm(Xo) <= 1e-10
     assert rep.ms_factor > 0 and rep.ms_build > 0 and rep.ms_solve > 0
+
+
+# ---------------------------------------------------------------- tensor-core factor
+@pytest.mark.parametrize("shape", [(300, 200), (700, 300), (1000, 513)])
+def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape):
+    """3xTF32 outer updates give an FP32-quality factor (R within ~1e-4 of the
+    oracle's, relative to max |R|); refinement then reaches the 1e-10 target."""
+    m, n = shape
+    A = I.random_matrix(m, n, seed=31 + m)
+    At = ctqr.to_colmajor(A)
+    f = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32)
+    assert f.status() == ctqr.CT_OK
+    F, tau = ctqr.factor_matrix(f)
+    Fo, tauo = O.qr(A)
+    R, Ro = np.triu(_np(F).astype(np.float64)[:n]), np.triu(Fo[:n])
+    assert np.abs(R - Ro).max() <= 1e-4 * np.abs(Ro).max()
+    b = A @ I.random_matrix(n, 2, seed=1)
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=At)
+    Xo = O.lstsq(A, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
+
+
+def test_tf32_single_pass_option_is_less_accurate_but_refines():
+    m, n = 600, 260
+    A = I.random_matrix(m, n, seed=41)
+    At = ctqr.to_colmajor(A)
+    f1 = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32, tf32_passes=1)
+    f3 = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32, tf32_passes=3)
+    Fo, _ = O.qr(A)
+    Ro = np.triu(Fo[:n])
+    e1 = np.abs(np.triu(_np(ctqr.factor_matrix(f1)[0]).astype(np.float64)[:n]) - Ro).max()
+    e3 = np.abs(np.triu(_np(ctqr.factor_matrix(f3)[0]).astype(np.float64)[:n]) - Ro).max()
+    assert e3 < e1 / 20
+    b = A @ I.random_matrix(n, 1, seed=2)
+    X, rep = ctqr.reconstruct(f1, ctqr.to_colmajor(b), A=At)
+    Xo = O.lstsq(A, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
+
+
+def test_tf32_ct_reconstruction_config1_and_noisy_subset():
+    g = I.CONFIG1["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    Anp = _np(A)
+    b = np.hstack([Anp @ I.phantoms(g, [1]),
+                   I.poisson_noise(Anp @ I.phantoms(g, [1001, 1002]), g.fov, 1e4, seed=9)])
+    f = ctqr.qr_factor(A.to(torch.float32), prec=ctqr.Prec.TF32)
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A)
+    Xo = O.lstsq(Anp, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
+
+
+@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.F32, ctqr.Prec.TF32])
+def test_lambda_stacked_scan_matches_oracle(prec):
+    """[A; lambda I] x = [b; 0] with a rank-deficient A (fan beam with 1.06
+    rays per pixel): the stacked system is full rank and every precision path
+    lands on the oracle's regularized least-squares solution."""
+    g = I.fan_geometry(24, 18, 34)
+    lam = 1e-3
+    Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+    b = Ao @ I.phantoms(g, [5, 6])
+    As = np.vstack([Ao, lam * np.eye(g.n)])
+    bs = np.vstack([b, np.zeros((g.n, 2))])
+    Xo = O.lstsq(As, bs)
+    X, rep = ctqr.reconstruct_scan(g, bs, prec=prec, lam=lam)
+    assert np.linalg.norm(X.numpy() - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
