@@ -109,40 +109,50 @@ ct_status read_status(const ct_factor* f, cudaStream_t s) {
 
 
 // FP64-residual refinement of X for a factor of A (see ct_reconstruct_batch).
+// A is the dense matrix the caller passed, or the sparse form of the system
+// built from a geometry (ct_reconstruct_scan); either way every product with
+// A or A^T is exact FP64.
 class Refiner {
  public:
-  Refiner(const ct_factor* f, const void* A, ct_dtype adt, int64_t lda, const double* B, int64_t ldb,
-          double* X, int64_t ldx, int64_t k, cudaStream_t s, int sms)
-      : f_(f), A_(A), a64_(adt == CT_F64), lda_(lda), B_(B), ldb_(ldb), X_(X), ldx_(ldx), k_(k),
+  Refiner(const ct_factor* f, const void* A, ct_dtype adt, int64_t lda, const SparseSystem* sp, const double* B,
+          int64_t ldb, double* X, int64_t ldx, int64_t k, cudaStream_t s, int sms)
+      : f_(f), A_(A), a64_(adt == CT_F64), lda_(lda), sp_(sp), B_(B), ldb_(ldb), X_(X), ldx_(ldx), k_(k),
         s_(s), sms_(sms), m_(f->m), n_(f->n), ldw_((f->m + 3) / 4 * 4) {}
 
   ct_status run(const ct_refine_opts* o, ct_report* rep) {
-    const int max_iter = o && o->max_iter > 0 ? o->max_iter : 60;
+    const int max_iter = o && o->max_iter > 0 ? o->max_iter : 200;
     tol_ = o && o->tol > 0.0 ? o->tol : 1e-12;
     lam_ = o && o->lambda > 0.0 ? o->lambda : 0.0;
     ma_ = lam_ > 0.0 ? m_ - n_ : m_;
     if (ma_ < 0) return CT_ERR_INVALID;
+    if (sp_ && (sp_->m != ma_ || sp_->n != n_)) return CT_ERR_INVALID;
     const int method = o ? o->method : 0;
     ct_status st;
     if ((st = alloc()) != CT_OK) return st;
     if ((st = launch_col_norms2(B_, ldb_, m_, k_, bn2_, s_)) != CT_OK) return st;
-    // X_0 = R^{-1} (Q^T B)[0:n], then classical corrections.
+    // X_0 = R^{-1} (Q^T B)[0:n], then classical corrections while they pay.
     if ((st = launch_zero_matrix(X_, 8, ldx_, n_, k_, s_)) != CT_OK) return st;
     int it = 0;
     double prev = INFINITY;
     ct_status result = CT_ERR_NOCONVERGE;
-    bool go_cgls = method == 2;
+    // lambda*I rows make the system inconsistent: go to CGLS after X_0.
+    const bool classical_only = method == 1;
+    const bool cgls_now = method == 2 || (method == 0 && lam_ > 0.0);
+    bool go_cgls = false;
     for (; it <= max_iter; ++it) {
       double worst = 0.0;
       if ((st = classical_step(it > 0, &worst)) != CT_OK) return st;
-      if (it == 0) continue;
+      if (it == 0) {
+        if (cgls_now) { go_cgls = true; break; }
+        continue;
+      }
       last_ = worst;
       if (worst <= tol_) { result = CT_OK; break; }
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
-      if (method == 2 || (method == 0 && it >= 2 && worst > 0.5 * prev)) { go_cgls = true; break; }
+      if (!classical_only && it >= 2 && worst > 0.25 * prev) { go_cgls = true; break; }
       prev = worst;
     }
-    if (go_cgls && result != CT_OK) {
+    if (go_cgls) {
       int used = 0;
       result = cgls(max_iter - it, &used);
       it += used;
@@ -160,6 +170,7 @@ class Refiner {
   const void* A_;
   bool a64_;
   int64_t lda_;
+  const SparseSystem* sp_;
   const double* B_;
   int64_t ldb_;
   double* X_;
@@ -172,15 +183,17 @@ class Refiner {
   size_t work_elems_ = 0;
   Scratch work_, Y_, D_, cg_, scal_;
   double *Yd_ = nullptr, *bn2_ = nullptr, *n1_ = nullptr, *n2_ = nullptr, *n3_ = nullptr, *a_ = nullptr;
-  double *S_ = nullptr, *P_ = nullptr, *T_ = nullptr, *Q_ = nullptr;
+  double *S_ = nullptr, *P_ = nullptr, *T_ = nullptr, *Q_ = nullptr, *S0_ = nullptr;
   std::vector<double> h_;
+
+  bool f32() const { return f_->store == CT_F32; }
 
   ct_status alloc() {
     ct_status st;
     work_elems_ = reflector_work_elems(sms_, f_->nb, k_);
     if ((st = work_.alloc(work_elems_ * sizeof(double), s_)) != CT_OK) return st;
     if ((st = Y_.alloc((size_t)ldw_ * k_ * sizeof(double), s_)) != CT_OK) return st;
-    if (f_->store == CT_F32 && (st = D_.alloc((size_t)ldw_ * k_ * sizeof(float), s_)) != CT_OK) return st;
+    if (f32() && (st = D_.alloc((size_t)ldw_ * k_ * sizeof(float), s_)) != CT_OK) return st;
     if ((st = scal_.alloc((size_t)5 * k_ * sizeof(double), s_)) != CT_OK) return st;
     Yd_ = (double*)Y_.p;
     bn2_ = (double*)scal_.p;
@@ -198,11 +211,39 @@ class Refiner {
     return CT_OK;
   }
 
+  // Yd[0:ma] -= A X.
+  ct_status sub_AX(const double* X, int64_t ldx) {
+    if (sp_) return sp_->apply(X, ldx, k_, Yd_, ldw_, 1, s_);
+    return launch_dense_update(A_, a64_, lda_, (int)n_, X, ldx, Yd_, true, ldw_, ma_, k_, s_);
+  }
+
+  // Q = [A; lambda I] T.
+  ct_status mul_A(const double* T, int64_t ldt, double* Q) {
+    ct_status st;
+    if (sp_) {
+      if ((st = sp_->apply(T, ldt, k_, Q, ldw_, 0, s_)) != CT_OK) return st;
+    } else {
+      if ((st = launch_zero_matrix(Q, 8, ldw_, ma_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, T, ldt, Q, true, ldw_, ma_, k_, s_)) != CT_OK) return st;
+      if ((st = scale_neg(Q, ma_)) != CT_OK) return st;  // the update left -A T in Q
+    }
+    if (lam_ > 0.0) {
+      if ((st = launch_zero_matrix(Q + ma_, 8, ldw_, n_, k_, s_)) != CT_OK) return st;
+      if ((st = launch_colwise(0, lam_, nullptr, T, ldt, Q + ma_, ldw_, n_, k_, s_)) != CT_OK) return st;
+    }
+    return CT_OK;
+  }
+
+  ct_status scale_neg(double* Q, int64_t rows) {
+    // Q = -Q via Q += (-2) Q.
+    return launch_colwise(0, -2.0, nullptr, Q, ldw_, Q, ldw_, rows, k_, s_);
+  }
+
   // Res = B - [A; lambda I] X into Yd (m x k).
   ct_status residual() {
     ct_status st;
     if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) return st;
-    if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, X_, ldx_, Yd_, true, ldw_, ma_, k_, s_)) != CT_OK) return st;
+    if ((st = sub_AX(X_, ldx_)) != CT_OK) return st;
     if (lam_ > 0.0) return launch_colwise(0, -lam_, nullptr, X_, ldx_, Yd_ + ma_, ldw_, n_, k_, s_);
     return CT_OK;
   }
@@ -216,7 +257,7 @@ class Refiner {
     } else if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) {
       return st;
     }
-    if (f_->store == CT_F32) {
+    if (f32()) {
       float* D = (float*)D_.p;
       if ((st = launch_copy_matrix(Yd_, CT_F64, ldw_, D, CT_F32, ldw_, m_, k_, s_)) != CT_OK) return st;
       if ((st = apply_qt_all(f_, D, false, ldw_, k_, true, (double*)work_.p, work_elems_, sms_, s_)) != CT_OK) return st;
@@ -242,23 +283,48 @@ class Refiner {
     return CT_OK;
   }
 
-  // s = R^{-T} ([A; lambda I]^T r)  with r in Yd.
-  ct_status precond_grad(double* S) {
+  // In-place preconditioner solves on an n x k FP64 block (ld n): R^{-1}
+  // (transpose = false) or R^{-T}; FP32 arithmetic for an FP32-stored R.
+  ct_status precond(double* Z, bool transpose) {
     ct_status st;
-    if ((st = launch_gemm_tn(A_, a64_, lda_, Yd_, ldw_, S, n_, ma_, n_, k_, s_)) != CT_OK) return st;
-    if (lam_ > 0.0 && (st = launch_colwise(0, lam_, nullptr, Yd_ + ma_, ldw_, S, n_, n_, k_, s_)) != CT_OK) return st;
-    return launch_trsm_t(f_, S, n_, k_, s_);
+    if (!f32()) return transpose ? launch_trsm_t(f_, Z, true, n_, k_, s_) : launch_trsm(f_, Z, true, n_, k_, s_);
+    float* D = (float*)D_.p;
+    if ((st = launch_copy_matrix(Z, CT_F64, n_, D, CT_F32, n_, n_, k_, s_)) != CT_OK) return st;
+    if ((st = transpose ? launch_trsm_t(f_, D, false, n_, k_, s_) : launch_trsm(f_, D, false, n_, k_, s_)) != CT_OK)
+      return st;
+    return launch_copy_matrix(D, CT_F32, n_, Z, CT_F64, n_, n_, k_, s_);
   }
 
-  // CGLS on min ||A R^{-1} y - B|| from the current X, at most `budget` steps.
+  // S = R^{-T} ([A; lambda I]^T r)  with r in Yd.
+  ct_status precond_grad(double* S) {
+    ct_status st;
+    if (sp_) {
+      if ((st = sp_->apply_t(Yd_, ldw_, k_, S, n_, s_)) != CT_OK) return st;
+    } else if ((st = launch_gemm_tn(A_, a64_, lda_, Yd_, ldw_, S, n_, ma_, n_, k_, s_)) != CT_OK) {
+      return st;
+    }
+    if (lam_ > 0.0 && (st = launch_colwise(0, lam_, nullptr, Yd_ + ma_, ldw_, S, n_, n_, k_, s_)) != CT_OK) return st;
+    return precond(S, true);
+  }
+
+  // Flexible preconditioned CGLS on min ||[A; lambda I] x - B|| from the
+  // current X, the low-precision R as right preconditioner.  x and the
+  // residual r are kept consistent in FP64 (r -= alpha A t with the exact
+  // product of the very t added to x); alpha is the exact line search
+  // <r, A t> / ||A t||^2 and beta the Polak-Ribiere ratio, so rounding in the
+  // preconditioner solves slows the iteration but cannot move its fixed
+  // point, A^T r = 0.
   ct_status cgls(int budget, int* used) {
     ct_status st;
     *used = 0;
-    if ((st = cg_.alloc(((size_t)3 * n_ * k_ + (size_t)ldw_ * k_) * sizeof(double), s_)) != CT_OK) return st;
+    if ((st = cg_.alloc(((size_t)5 * n_ * k_ + (size_t)ldw_ * k_) * sizeof(double), s_)) != CT_OK) return st;
     S_ = (double*)cg_.p;
-    P_ = S_ + n_ * k_;
+    S0_ = S_ + n_ * k_;
+    P_ = S0_ + n_ * k_;
     T_ = P_ + n_ * k_;
-    Q_ = T_ + n_ * k_;
+    double* G = T_ + n_ * k_;  // scratch n x k
+    Q_ = G + n_ * k_;
+    (void)G;
     if ((st = residual()) != CT_OK) return st;              // r = B - A X
     if ((st = precond_grad(S_)) != CT_OK) return st;        // s = R^-T A^T r
     if ((st = launch_copy_matrix(S_, CT_F64, n_, P_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
@@ -267,39 +333,43 @@ class Refiner {
     std::vector<double> gamma(h_.begin(), h_.begin() + k_), alpha(k_), beta(k_);
     for (int it = 0; it < budget; ++it) {
       *used = it + 1;
-      // t = R^{-1} p ; q = -A t
+      // t = R^{-1} p ; q = [A; lambda I] t
       if ((st = launch_copy_matrix(P_, CT_F64, n_, T_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
-      if ((st = launch_trsm(f_, T_, true, n_, k_, s_)) != CT_OK) return st;
-      if ((st = launch_zero_matrix(Q_, 8, ldw_, m_, k_, s_)) != CT_OK) return st;
-      if ((st = launch_dense_update(A_, a64_, lda_, (int)n_, T_, n_, Q_, true, ldw_, ma_, k_, s_)) != CT_OK) return st;
-      if (lam_ > 0.0 && (st = launch_colwise(0, -lam_, nullptr, T_, n_, Q_ + ma_, ldw_, n_, k_, s_)) != CT_OK) return st;
-      if ((st = launch_col_norms2(Q_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;
-      if ((st = launch_col_norms2(T_, n_, n_, k_, n2_, s_)) != CT_OK) return st;
-      if ((st = launch_col_norms2(X_, ldx_, n_, k_, n3_, s_)) != CT_OK) return st;
-      if ((st = fetch(n1_, 3)) != CT_OK) return st;
+      if ((st = precond(T_, false)) != CT_OK) return st;
+      if ((st = mul_A(T_, n_, Q_)) != CT_OK) return st;
+      if ((st = launch_col_dots(Yd_, ldw_, Q_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;   // <r, q>
+      if ((st = launch_col_norms2(Q_, ldw_, m_, k_, n2_, s_)) != CT_OK) return st;           // ||q||^2
+      if ((st = launch_col_norms2(T_, n_, n_, k_, n3_, s_)) != CT_OK) return st;             // ||t||^2
+      if ((st = launch_col_norms2(X_, ldx_, n_, k_, a_, s_)) != CT_OK) return st;            // ||x||^2
+      if ((st = fetch(n1_, 4)) != CT_OK) return st;
       double worst = 0.0;
       for (int64_t c = 0; c < k_; ++c) {
-        const double qq = h_[c], tt = h_[k_ + c], xx = h_[2 * k_ + c];
-        alpha[c] = qq > 0.0 ? gamma[c] / qq : 0.0;
-        const double dx = alpha[c] * sqrt(tt), xn = sqrt(xx);
+        const double rq = h_[c], qq = h_[k_ + c], tt = h_[2 * k_ + c], xx = h_[3 * k_ + c];
+        alpha[c] = qq > 0.0 ? rq / qq : 0.0;
+        const double dx = fabs(alpha[c]) * sqrt(tt), xn = sqrt(xx + alpha[c] * alpha[c] * tt);
         const double rel = xn > 0.0 ? dx / xn : (dx > 0.0 ? INFINITY : 0.0);
         if (!(rel <= worst)) worst = rel;
       }
       CT_CUDA_TRY(cudaMemcpyAsync(a_, alpha.data(), sizeof(double) * k_, cudaMemcpyHostToDevice, s_));
-      if ((st = launch_colwise(0, 1.0, a_, T_, n_, X_, ldx_, n_, k_, s_)) != CT_OK) return st;   // x += a t
-      if ((st = launch_colwise(0, 1.0, a_, Q_, ldw_, Yd_, ldw_, m_, k_, s_)) != CT_OK) return st;  // r -= a A t
+      if ((st = launch_colwise(0, 1.0, a_, T_, n_, X_, ldx_, n_, k_, s_)) != CT_OK) return st;    // x += a t
+      if ((st = launch_colwise(0, -1.0, a_, Q_, ldw_, Yd_, ldw_, m_, k_, s_)) != CT_OK) return st;  // r -= a q
       last_ = worst;
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
       if (worst <= tol_) {
         CT_CUDA_TRY(cudaStreamSynchronize(s_));
         return CT_OK;
       }
+      // s_new = R^-T A^T r ; beta = <s_new, s_new - s_old> / gamma (Polak-Ribiere, >= 0)
+      if ((st = launch_copy_matrix(S_, CT_F64, n_, S0_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
       if ((st = precond_grad(S_)) != CT_OK) return st;
       if ((st = launch_col_norms2(S_, n_, n_, k_, n1_, s_)) != CT_OK) return st;
-      if ((st = fetch(n1_, 1)) != CT_OK) return st;
+      if ((st = launch_col_dots(S_, n_, S0_, n_, n_, k_, n2_, s_)) != CT_OK) return st;
+      if ((st = fetch(n1_, 2)) != CT_OK) return st;
       for (int64_t c = 0; c < k_; ++c) {
-        beta[c] = gamma[c] > 0.0 ? h_[c] / gamma[c] : 0.0;
-        gamma[c] = h_[c];
+        const double ss = h_[c], s0 = h_[k_ + c];
+        double b = gamma[c] > 0.0 ? (ss - s0) / gamma[c] : 0.0;
+        beta[c] = b > 0.0 ? b : 0.0;
+        gamma[c] = ss;
       }
       CT_CUDA_TRY(cudaMemcpyAsync(a_, beta.data(), sizeof(double) * k_, cudaMemcpyHostToDevice, s_));
       if ((st = launch_colwise(1, 1.0, a_, S_, n_, P_, n_, n_, k_, s_)) != CT_OK) return st;     // p = s + b p
@@ -517,9 +587,19 @@ ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k, v
   return launch_trsm(f, B, true, ldb, k, as_stream(stream));
 }
 
+static ct_status reconstruct_impl(const ct_factor* f, const void* A, ct_dtype A_dtype, int64_t lda,
+                                  const SparseSystem* sp, const double* B, int64_t ldb, double* X, int64_t ldx,
+                                  int64_t k, const ct_refine_opts* ropts, ct_report* report, void* stream);
+
 ct_status ct_reconstruct_batch(const ct_factor* f, const void* A, ct_dtype A_dtype, int64_t lda,
                                const double* B, int64_t ldb, double* X, int64_t ldx, int64_t k,
                                const ct_refine_opts* ropts, ct_report* report, void* stream) {
+  return reconstruct_impl(f, A, A_dtype, lda, nullptr, B, ldb, X, ldx, k, ropts, report, stream);
+}
+
+static ct_status reconstruct_impl(const ct_factor* f, const void* A, ct_dtype A_dtype, int64_t lda,
+                                  const SparseSystem* sp, const double* B, int64_t ldb, double* X, int64_t ldx,
+                                  int64_t k, const ct_refine_opts* ropts, ct_report* report, void* stream) {
   const auto t_start = std::chrono::steady_clock::now();
   if (report) memset(report, 0, sizeof(*report));
   if (!f || k < 0) return CT_ERR_INVALID;
@@ -533,7 +613,7 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A, ct_dtype A_dty
   if (st != CT_OK) return st;
   const int64_t m = f->m, n = f->n;
 
-  if (!A) {
+  if (!A && !sp) {
     const int64_t ldw = (m + 3) / 4 * 4;
     const size_t work_elems = reflector_work_elems(di.sms, f->nb, k);
     Scratch work, Y;
@@ -550,7 +630,7 @@ ct_status ct_reconstruct_batch(const ct_factor* f, const void* A, ct_dtype A_dty
     return st;
   }
 
-  Refiner R(f, A, A_dtype, lda, B, ldb, X, ldx, k, s, di.sms);
+  Refiner R(f, A, A_dtype, lda, sp, B, ldb, X, ldx, k, s, di.sms);
   st = R.run(ropts, report);
   ct_status dev = read_status(f, s);
   if (report) report->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
@@ -576,8 +656,11 @@ ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec pr
   const bool host = where == CT_HOST_BUFFERS;
   if (!host && (!aligned16(B) || !aligned16(X))) return CT_ERR_INVALID;
   const int64_t lda = (m + 3) / 4 * 4;
+  const bool mixed = prec != CT_PREC_F64;
   Scratch Abuf, Bbuf, Xbuf;
-  if ((st = Abuf.alloc((size_t)lda * n * sizeof(double), s)) != CT_OK) return st;
+  // FP64: [A; lambda I] in FP64, factored in place.  Mixed: [A; lambda I] in
+  // FP32, factored in place, plus the exact sparse FP64 A for the residuals.
+  if ((st = Abuf.alloc((size_t)lda * n * (mixed ? sizeof(float) : sizeof(double)), s)) != CT_OK) return st;
   const double* Bd = B;
   double* Xd = X;
   int64_t ldbd = ldb, ldxd = ldx;
@@ -597,32 +680,30 @@ ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec pr
     ldbd = lda;
     ldxd = n;
   }
-  double* A = (double*)Abuf.p;
-  const bool mixed = prec != CT_PREC_F64;
-  const int64_t ma = lambda > 0.0 ? m - n : m;
-  Scratch F32buf;
-  if (mixed && (st = F32buf.alloc((size_t)lda * n * sizeof(float), s)) != CT_OK) return st;
+  int* sp_status = nullptr;
+  CT_CUDA_TRY(cudaMallocAsync((void**)&sp_status, sizeof(int), s));
+  struct SFree { int* p; cudaStream_t s; ~SFree() { cudaFreeAsync(p, s); } } sfree{sp_status, s};
+  CT_CUDA_TRY(cudaMemsetAsync(sp_status, 0, sizeof(int), s));
+  SparseSystem sp;
   CT_CUDA_TRY(cudaEventRecord(ev[0], s));
-  if (!mixed) {
-    // FP64: build [A; lambda I] and factor it in place.
-    if ((st = launch_build_system(geom, CT_F64, lambda, A, lda, m, n, s)) != CT_OK) return st;
-  } else {
-    // Mixed: FP64 rays-only A for the residuals, FP32 [A; lambda I] to factor.
-    if ((st = launch_build_system(geom, CT_F64, 0.0, A, lda, ma, n, s)) != CT_OK) return st;
-    if ((st = launch_build_system(geom, CT_F32, lambda, F32buf.p, lda, m, n, s)) != CT_OK) return st;
-  }
+  if ((st = launch_build_system(geom, mixed ? CT_F32 : CT_F64, lambda, Abuf.p, lda, m, n, s)) != CT_OK) return st;
+  if (mixed && (st = sp.build(geom, k, sp_status, s)) != CT_OK) return st;
   CT_CUDA_TRY(cudaEventRecord(ev[1], s));
   ct_factor* f = nullptr;
   ct_qr_opts qo = {0, 1, 0};  // factor in place
-  if ((st = ct_qr_factor(mixed ? F32buf.p : (void*)A, mixed ? CT_F32 : CT_F64, m, n, lda, prec, &qo, &f,
-                         stream)) != CT_OK)
-    return st;
+  if ((st = ct_qr_factor(Abuf.p, mixed ? CT_F32 : CT_F64, m, n, lda, prec, &qo, &f, stream)) != CT_OK) return st;
   CT_CUDA_TRY(cudaEventRecord(ev[2], s));
   ct_refine_opts ro = ropts ? *ropts : ct_refine_opts{0, 0.0, 0.0, 0};
   ro.lambda = lambda;
   ct_report rep;
-  ct_status rs = ct_reconstruct_batch(f, mixed ? A : nullptr, CT_F64, lda, Bd, ldbd, Xd, ldxd, k, &ro, &rep,
-                                      stream);
+  ct_status rs = reconstruct_impl(f, nullptr, CT_F64, 0, mixed ? &sp : nullptr, Bd, ldbd, Xd, ldxd, k, &ro, &rep,
+                                  stream);
+  if (rs == CT_OK && mixed) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, sp_status, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess && h != 0)
+      rs = (ct_status)h;
+  }
   cudaError_t ce = cudaEventRecord(ev[3], s);
   if (ce == cudaSuccess && host)
     ce = cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, ldxd * sizeof(double), n * sizeof(double), k,

@@ -184,27 +184,27 @@ __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_
 // C(r, c) -= sum_{a < K} V(a, r) W(a, c): the transposed-V update of the
 // forward substitution with R^T (V = a block row of R, read with a < K its
 // rows), 64 x BN tile per CTA.
-template <typename TV, int BN>
+template <typename TV, typename TB, typename Acc, int BN>
 __global__ void __launch_bounds__(kGT) k_update_t(const TV* __restrict__ V, int64_t ldv, int K,
-                                                   const double* __restrict__ W, int64_t ldw,
-                                                   double* __restrict__ C, int64_t ldc, int64_t mr,
+                                                   const TB* __restrict__ W, int64_t ldw,
+                                                   TB* __restrict__ C, int64_t ldc, int64_t mr,
                                                    int64_t nc) {
   constexpr int TN = BN / 16;
-  __shared__ double Vs[kBK][kBM + 1];
-  __shared__ double Ws[kBK][BN + 1];
+  __shared__ Acc Vs[kBK][kBM + 1];
+  __shared__ Acc Ws[kBK][BN + 1];
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   const int64_t r0 = (int64_t)blockIdx.x * kBM, c0 = (int64_t)blockIdx.y * BN;
-  double acc[4][TN];
+  Acc acc[4][TN];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = (Acc)0;
   for (int a0 = 0; a0 < K; a0 += kBK) {
 #pragma unroll
     for (int i = 0; i < kBM * kBK / kGT; ++i) {
       const int e = tid + kGT * i, aa = e % kBK, r = e / kBK;
       const int64_t rg = r0 + r;
-      Vs[aa][r] = (rg < mr && a0 + aa < K) ? (double)V[a0 + aa + rg * ldv] : 0.0;
+      Vs[aa][r] = (rg < mr && a0 + aa < K) ? (Acc)V[a0 + aa + rg * ldv] : (Acc)0;
     }
 #pragma unroll
     for (int i = 0; i < (BN * kBK + kGT - 1) / kGT; ++i) {
@@ -212,13 +212,13 @@ __global__ void __launch_bounds__(kGT) k_update_t(const TV* __restrict__ V, int6
       if (e < BN * kBK) {
         const int aa = e % kBK, c = e / kBK;
         const int64_t cg = c0 + c;
-        Ws[aa][c] = (a0 + aa < K && cg < nc) ? W[a0 + aa + cg * ldw] : 0.0;
+        Ws[aa][c] = (a0 + aa < K && cg < nc) ? (Acc)W[a0 + aa + cg * ldw] : (Acc)0;
       }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      double av[4], wv[TN];
+      Acc av[4], wv[TN];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty * 4 + i];
 #pragma unroll
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kGT) k_update_t(const TV* __restrict__ V, int6
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int64_t r = r0 + ty * 4 + i;
-      if (r < mr) C[r + cg * ldc] -= acc[i][j];
+      if (r < mr) C[r + cg * ldc] = (TB)((Acc)C[r + cg * ldc] - acc[i][j]);
     }
   }
 }
@@ -403,19 +403,31 @@ ct_status launch_dense_update(const void* V, bool v_f64, int64_t ldv, int K, con
   return CT_OK;
 }
 
-ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, const double* W,
-                                int64_t ldw, double* C, int64_t ldc, int64_t mr, int64_t nc,
-                                cudaStream_t s) {
-  if (mr <= 0 || nc <= 0 || K <= 0) return CT_OK;
-  LaunchScope ls(K_UPDATE, s, 2.0 * mr * K * nc, 16.0 * mr * nc + (double)mr * K * (v_f64 ? 8 : 4));
+namespace {
+template <typename TV, typename TB, typename Acc>
+void dense_update_t_t(const void* V, int64_t ldv, int K, const void* W, int64_t ldw, void* C, int64_t ldc,
+                      int64_t mr, int64_t nc, cudaStream_t s) {
   if (nc <= 16) {
     const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 15) / 16));
-    if (v_f64) k_update_t<double, 16><<<grid, kGT, 0, s>>>((const double*)V, ldv, K, W, ldw, C, ldc, mr, nc);
-    else k_update_t<float, 16><<<grid, kGT, 0, s>>>((const float*)V, ldv, K, W, ldw, C, ldc, mr, nc);
+    k_update_t<TV, TB, Acc, 16><<<grid, kGT, 0, s>>>((const TV*)V, ldv, K, (const TB*)W, ldw, (TB*)C, ldc, mr, nc);
   } else {
     const dim3 grid((unsigned)((mr + kBM - 1) / kBM), (unsigned)((nc + 63) / 64));
-    if (v_f64) k_update_t<double, 64><<<grid, kGT, 0, s>>>((const double*)V, ldv, K, W, ldw, C, ldc, mr, nc);
-    else k_update_t<float, 64><<<grid, kGT, 0, s>>>((const float*)V, ldv, K, W, ldw, C, ldc, mr, nc);
+    k_update_t<TV, TB, Acc, 64><<<grid, kGT, 0, s>>>((const TV*)V, ldv, K, (const TB*)W, ldw, (TB*)C, ldc, mr, nc);
+  }
+}
+}  // namespace
+
+ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, const void* W, int64_t ldw,
+                                void* C, bool b_f64, int64_t ldc, int64_t mr, int64_t nc, cudaStream_t s) {
+  if (mr <= 0 || nc <= 0 || K <= 0) return CT_OK;
+  LaunchScope ls(K_UPDATE, s, 2.0 * mr * K * nc,
+                 (b_f64 ? 16.0 : 8.0) * mr * nc + (double)mr * K * (v_f64 ? 8 : 4));
+  if (b_f64) {
+    if (v_f64) dense_update_t_t<double, double, double>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
+    else dense_update_t_t<float, double, double>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
+  } else {
+    if (v_f64) return CT_ERR_UNSUPPORTED;
+    dense_update_t_t<float, float, float>(V, ldv, K, W, ldw, C, ldc, mr, nc, s);
   }
   CT_LAUNCH_CHECK();
   return CT_OK;

@@ -84,7 +84,7 @@ constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 // ---------------------------------------------------------------------------
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
-  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_COUNT
+  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_COUNT
 };
 
 class LaunchScope {
@@ -179,12 +179,14 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
                              cudaStream_t s);
 ct_status launch_rank_check(ct_factor* f, cudaStream_t s);
-// B[0:n] <- R^{-T} B[0:n] (FP64).
-ct_status launch_trsm_t(const ct_factor* f, double* B, int64_t ldb, int64_t k, cudaStream_t s);
-// C(r, c) -= sum_{a<K} V(a, r) W(a, c) (V read transposed), FP64 C and W.
-ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, const double* W,
-                                int64_t ldw, double* C, int64_t ldc, int64_t mr, int64_t nc,
-                                cudaStream_t s);
+// B[0:n] <- R^{-T} B[0:n] (FP64 B, or FP32 B with an FP32-stored R).
+ct_status launch_trsm_t(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s);
+// C(r, c) -= sum_{a<K} V(a, r) W(a, c) (V read transposed); W and C FP64 or FP32.
+ct_status launch_dense_update_t(const void* V, bool v_f64, int64_t ldv, int K, const void* W, int64_t ldw,
+                                void* C, bool b_f64, int64_t ldc, int64_t mr, int64_t nc, cudaStream_t s);
+// Column-wise dot products out[c] = sum_r X[r, c] Y[r, c] (FP64).
+ct_status launch_col_dots(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t rows,
+                          int64_t k, double* out, cudaStream_t s);
 // Y = A^T R: A m x n (FP64 or FP32), R m x k FP64, Y n x k FP64.
 ct_status launch_gemm_tn(const void* A, bool a_f64, int64_t lda, const double* R, int64_t ldr,
                          double* Y, int64_t ldy, int64_t m, int64_t n, int64_t k, cudaStream_t s);
@@ -201,6 +203,28 @@ ct_status launch_colwise(int mode, double sign, const double* a, const double* X
 ct_status tc_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,
                      int64_t K, float* C, int64_t ldc, int64_t split_stride, int mode, int splits,
                      bool split3, int* status, cudaStream_t s);
+
+// ---- sparse system matrix (sparse.cu) -------------------------------------
+// CSR + CSC of the rays-only A of a geometry (same entries as the dense build),
+// with staging buffers for products with up to kmax right-hand sides.
+struct SparseSystem {
+  int64_t m = 0, n = 0, nnz = 0, kmax = 0;
+  int64_t* row_ptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  int64_t* col_ptr = nullptr;
+  int* crow = nullptr;
+  double* cval = nullptr;
+  double* stage = nullptr;
+  ~SparseSystem();
+  void release();
+  ct_status build(const ct_geometry* g, int64_t k_max, int* status, cudaStream_t s);
+  // Y op= A X (mode 0 store, 1 subtract, 2 store negated); X n x k, Y m x k.
+  ct_status apply(const double* X, int64_t ldx, int64_t k, double* Y, int64_t ldy, int mode,
+                  cudaStream_t s) const;
+  // S = A^T R; R m x k, S n x k.
+  ct_status apply_t(const double* R, int64_t ldr, int64_t k, double* S, int64_t lds, cudaStream_t s) const;
+};
 
 // ---- utilities (util.cu) ---------------------------------------------------
 ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   double* red = smem;                               // [2*kMaxNb] reduced values
   double* wvd = red + 2 * kMaxNb;                   // [kMaxNb]  w_c
   double* scratch = wvd + kMaxNb;                   // [kNW][2*kMaxNb]
-  Mth* slab = (Mth*)(scratch + kNW * 2 * kMaxNb);   // [nbp][rp], column-major
+  Mth* wvm = (Mth*)(scratch + kNW * 2 * kMaxNb);    // [kMaxNb] w_c in the panel arithmetic
+  Mth* slab = wvm + kMaxNb;                         // [nbp][rp], column-major
   __shared__ int s_last;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -106,25 +107,34 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
     }
     if (!grid_barrier(&a.bar[0], a.grid, a.status, kBarrierLimitNs)) return;
 
-    // Deterministic reduction: warp w sums CTAs b = w, w+kNW, ...; lanes take
-    // consecutive entries (coalesced); then the kNW warp sums are added in order.
+    // Deterministic reduction: thread t owns entry q = t % L of the partial
+    // vectors (L = 2*ne) and sums the CTAs b = g, g+G, g+2G, ... of its group
+    // g = t / L (G groups); the loads are independent and issued eight at a
+    // time, then the G group sums are added in order.  Every CTA does the
+    // same sums in the same order, so all hold identical totals.
     {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      const int L = 2 * ne;
+      int groups = kPT / L;
+      if (groups > kNW) groups = kNW;
+      const int q = tid % L, grp = tid / L;
       const double* base = a.col_part + (size_t)(k & 1) * a.grid * (2 * kMaxNb);
-      for (int b = warp; b < a.grid; b += kNW) {
-        const double* pb = base + (size_t)b * (2 * kMaxNb);
+      if (grp < groups) {
+        double acc = 0.0;
+        int b = grp;
+        for (; b + 7 * groups < a.grid; b += 8 * groups) {
+          double v[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int q = lane + 32 * i;
-          if (q < 2 * ne) acc[i] += __ldcg(pb + q);
+          for (int u = 0; u < 8; ++u) v[u] = __ldcg(base + (size_t)(b + u * groups) * (2 * kMaxNb) + q);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc += v[u];
         }
+        for (; b < a.grid; b += groups) acc += __ldcg(base + (size_t)b * (2 * kMaxNb) + q);
+        scratch[grp * (2 * kMaxNb) + q] = acc;
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) scratch[warp * (2 * kMaxNb) + lane + 32 * i] = acc[i];
       __syncthreads();
-      if (tid < 2 * ne) {
+      if (tid < L) {
         double s = 0.0;
-        for (int w = 0; w < kNW; ++w) s += scratch[w * (2 * kMaxNb) + tid];
+        for (int w = 0; w < groups; ++w) s += scratch[w * (2 * kMaxNb) + tid];
         red[tid] = s;
       }
       __syncthreads();
@@ -139,7 +149,10 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
       tau = (beta - alpha) / beta;
       scale = 1.0 / (alpha - beta);
     }
-    if (tid > 0 && tid < ne) wvd[tid] = tau * (red[ne + tid] + scale * red[tid]);
+    if (tid > 0 && tid < ne) {
+      wvd[tid] = tau * (red[ne + tid] + scale * red[tid]);
+      wvm[tid] = (Mth)wvd[tid];  // converted once, not per row
+    }
     __syncthreads();
     if (tau != 0.0) {
       const Mth sc = (Mth)scale;
@@ -147,9 +160,9 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
         Mth* colr = slab + r;
         const Mth v = colr[(size_t)k * rp] * sc;
         colr[(size_t)k * rp] = v;
-        for (int q = 1; q < ne; ++q) colr[(size_t)(k + q) * rp] -= (Mth)wvd[q] * v;
+        for (int q = 1; q < ne; ++q) colr[(size_t)(k + q) * rp] -= wvm[q] * v;
       }
-      if (owner && tid > 0 && tid < ne) slab[(size_t)(k + tid) * rp + kl] -= (Mth)wvd[tid];
+      if (owner && tid > 0 && tid < ne) slab[(size_t)(k + tid) * rp + kl] -= wvm[tid];
     }
     if (owner && tid == 0) slab[(size_t)k * rp + kl] = (Mth)beta;
     if (blockIdx.x == 0 && tid == 0) a.tau[k] = tau;
@@ -161,20 +174,21 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
     for (int r = tid; r < nr; r += kPT) P[rb + r + c * a.ld] = (S)slab[(size_t)c * rp + r];
 
   // This CTA's share of the strictly upper Gram matrix G = V^T V, packed as
-  // p(i, j) = j(j-1)/2 + i for i < j.  v_i is 0 above row i and 1 on it.
+  // p(i, j) = j(j-1)/2 + i for i < j (accumulated in the panel arithmetic).
+  // v_i is 0 above row i and 1 on it.
   const int npairs = nbp * (nbp - 1) / 2;
   double* gp = a.gram_part + (size_t)blockIdx.x * (kMaxNb * (kMaxNb - 1) / 2);
   for (int j = 1 + warp; j < nbp; j += kNW) {
     for (int i = 0; i < j; ++i) {
-      double s = 0.0;
+      Mth sm = (Mth)0;
       for (int r = lane; r < nr; r += 32) {
         const int64_t gr = rb + r;
         if (gr < j) continue;  // v_j vanishes above its diagonal
-        const double vj = gr == j ? 1.0 : (double)slab[(size_t)j * rp + r];
-        const double vi = gr == i ? 1.0 : (gr > i ? (double)slab[(size_t)i * rp + r] : 0.0);
-        s += vi * vj;
+        const Mth vj = gr == j ? (Mth)1 : slab[(size_t)j * rp + r];
+        const Mth vi = gr == i ? (Mth)1 : (gr > i ? slab[(size_t)i * rp + r] : (Mth)0);
+        sm += vi * vj;
       }
-      s = warp_sum(s);
+      const double s = warp_sum((double)sm);
       if (lane == 0) gp[j * (j - 1) / 2 + i] = s;
     }
   }
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
 }
 
 size_t panel_smem_bytes(int nbp, int rp, size_t mth) {
-  const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb) * sizeof(double);
+  const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb) * sizeof(double) + kMaxNb * mth;
   size_t bytes = small + (size_t)nbp * rp * mth;
   const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
   return bytes < t_need ? t_need : bytes;

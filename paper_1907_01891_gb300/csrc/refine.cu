@@ -19,6 +19,17 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
+__global__ void __launch_bounds__(256) k_col_dots(const double* __restrict__ X, int64_t ldx,
+                                                  const double* __restrict__ Y, int64_t ldy, int64_t rows,
+                                                  double* __restrict__ out) {
+  __shared__ double sh[8];
+  const int64_t c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += X[r + c * ldx] * Y[r + c * ldy];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[c] = s;
+}
+
 __global__ void __launch_bounds__(256) k_col_norms2(const double* __restrict__ X, int64_t ldx,
                                                     int64_t rows, double* __restrict__ out) {
   __shared__ double sh[8];
@@ -72,6 +83,15 @@ ct_status launch_colwise(int mode, double sign, const double* a, const double* X
   LaunchScope ls(K_AXPY, s, 2.0 * rows * k, 24.0 * rows * k);
   const unsigned gx = (unsigned)((rows + 255) / 256 < 128 ? (rows + 255) / 256 : 128);
   k_colwise<<<dim3(gx, (unsigned)k), 256, 0, s>>>(mode, sign, a, X, ldx, Y, ldy, rows);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+ct_status launch_col_dots(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t rows,
+                          int64_t k, double* out, cudaStream_t s) {
+  if (k <= 0) return CT_OK;
+  LaunchScope ls(K_NORMS, s, 2.0 * rows * k, 16.0 * rows * k);
+  k_col_dots<<<(unsigned)k, 256, 0, s>>>(X, ldx, Y, ldy, rows, out);
   CT_LAUNCH_CHECK();
   return CT_OK;
 }

@@ -64,17 +64,16 @@ __device__ __forceinline__ int cell_of(double x, double lo, double pixel, int ce
   return k;
 }
 
-template <typename S>
-__global__ void __launch_bounds__(128) k_siddon(Geo g, S* __restrict__ A, int64_t lda) {
-  const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t rays = (int64_t)g.n_views * g.n_bins;
-  if (ray >= rays) return;
+// Walk ray `ray` through the grid; emit(pixel, length) for every segment of
+// positive length, in order of the ray parameter.  Returns the segment count.
+template <typename Emit>
+__device__ __forceinline__ int traverse(const Geo& g, int64_t ray, Emit emit) {
   double px, py, dx, dy;
   ray_of(g, ray, px, py, dx, dy);
   double t0 = -INFINITY, t1 = INFINITY;
   clip(px, dx, g.x0, line(g.x0, g.nx, g.pixel), t0, t1);
   clip(py, dy, g.y0, line(g.y0, g.ny, g.pixel), t0, t1);
-  if (!(t1 > t0)) return;  // the ray misses the image: its row stays zero
+  if (!(t1 > t0)) return 0;  // the ray misses the image
 
   // Next grid line to cross along x (index ix, stepping sx) and y.
   const int sx = dx > 0.0 ? 1 : -1, sy = dy > 0.0 ? 1 : -1;
@@ -90,6 +89,7 @@ __global__ void __launch_bounds__(128) k_siddon(Geo g, S* __restrict__ A, int64_
     while (iy >= 0 && iy <= g.ny && (line(g.y0, iy, g.pixel) - py) / dy <= t0) iy += sy;
   }
   double tcur = t0;
+  int count = 0;
   const int max_steps = g.nx + g.ny + 4;
   for (int step = 0; step < max_steps && tcur < t1; ++step) {
     const double tx = (dx != 0.0 && ix >= 0 && ix <= g.nx) ? (line(g.x0, ix, g.pixel) - px) / dx : INFINITY;
@@ -100,13 +100,50 @@ __global__ void __launch_bounds__(128) k_siddon(Geo g, S* __restrict__ A, int64_
       const double tm = 0.5 * (tcur + tn);
       const int cx = cell_of(px + tm * dx, g.x0, g.pixel, g.nx);
       const int cy = cell_of(py + tm * dy, g.y0, g.pixel, g.ny);
-      S* dst = A + ray + ((int64_t)cy * g.nx + cx) * lda;
-      *dst = (S)((double)*dst + (tn - tcur));
+      emit(cy * g.nx + cx, tn - tcur);
+      ++count;
     }
     if (tx <= tn) ix += sx;
     if (ty <= tn) iy += sy;
     tcur = tn;
   }
+  return count;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_siddon(Geo g, S* __restrict__ A, int64_t lda) {
+  const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  if (ray >= rays) return;
+  traverse(g, ray, [&](int j, double len) {
+    S* dst = A + ray + (int64_t)j * lda;
+    *dst = (S)((double)*dst + len);
+  });
+}
+
+// Sparse form, pass 1: segments per ray.
+__global__ void __launch_bounds__(128) k_ray_nnz(Geo g, int* __restrict__ nnz) {
+  const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  if (ray >= rays) return;
+  nnz[ray] = traverse(g, ray, [](int, double) {});
+}
+
+// Sparse form, pass 2: CSR entries of every ray (same segments as k_siddon).
+__global__ void __launch_bounds__(128) k_ray_fill(Geo g, const int64_t* __restrict__ row_ptr,
+                                                  int* __restrict__ col, double* __restrict__ val) {
+  const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  if (ray >= rays) return;
+  int64_t pos = row_ptr[ray];
+  const int64_t end = row_ptr[ray + 1];
+  traverse(g, ray, [&](int j, double len) {
+    if (pos < end) {
+      col[pos] = j;
+      val[pos] = len;
+      ++pos;
+    }
+  });
 }
 
 template <typename S>
@@ -115,19 +152,42 @@ __global__ void k_lambda_rows(S* __restrict__ A, int64_t lda, int64_t row0, int6
   if (j < n) A[row0 + j + j * lda] = (S)lambda;
 }
 
-}  // namespace
-
-ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
-                             cudaStream_t s);
-
-ct_status launch_build_system(const ct_geometry* gg, ct_dtype dtype, double lambda, void* A,
-                              int64_t lda, int64_t m, int64_t n, cudaStream_t s) {
+Geo make_geo(const ct_geometry* gg) {
   Geo g;
   g.beam = gg->beam; g.nx = gg->nx; g.ny = gg->ny; g.n_views = gg->n_views; g.n_bins = gg->n_bins;
   g.pixel = gg->pixel; g.angle0 = gg->angle0; g.angle_span = gg->angle_span;
   g.src_iso = gg->src_iso; g.det_span = gg->det_span;
   g.x0 = -0.5 * (double)g.nx * g.pixel;
   g.y0 = -0.5 * (double)g.ny * g.pixel;
+  return g;
+}
+
+}  // namespace
+
+ct_status launch_ray_nnz(const ct_geometry* gg, int* nnz, cudaStream_t s) {
+  const Geo g = make_geo(gg);
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  LaunchScope ls(K_SIDDON, s, 0.0, 4.0 * rays);
+  k_ray_nnz<<<(unsigned)((rays + 127) / 128), 128, 0, s>>>(g, nnz);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+ct_status launch_ray_fill(const ct_geometry* gg, const int64_t* row_ptr, int* col, double* val, cudaStream_t s) {
+  const Geo g = make_geo(gg);
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  LaunchScope ls(K_SIDDON, s, 0.0, 12.0 * rays * (g.nx + g.ny));
+  k_ray_fill<<<(unsigned)((rays + 127) / 128), 128, 0, s>>>(g, row_ptr, col, val);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
+                             cudaStream_t s);
+
+ct_status launch_build_system(const ct_geometry* gg, ct_dtype dtype, double lambda, void* A,
+                              int64_t lda, int64_t m, int64_t n, cudaStream_t s) {
+  const Geo g = make_geo(gg);
   const size_t elem = dtype == CT_F64 ? 8 : 4;
   ct_status st = launch_zero_matrix(A, elem, lda, m, n, s);
   if (st != CT_OK) return st;

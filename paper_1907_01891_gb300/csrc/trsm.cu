@@ -58,25 +58,25 @@ __global__ void __launch_bounds__(256) k_trsm_diag(const S* __restrict__ F, int6
 
 // Z[i0:i0+nbt, c] = R[i0:i0+nbt, i0:i0+nbt]^{-T} Y[i0:i0+nbt, c] (forward
 // substitution with the lower triangular R^T), FP64 arithmetic.
-template <typename S>
+template <typename S, typename TB, typename Acc>
 __global__ void __launch_bounds__(256) k_trsm_diag_t(const S* __restrict__ F, int64_t ld, int64_t i0,
-                                                     int nbt, double* __restrict__ B, int64_t ldb,
+                                                     int nbt, TB* __restrict__ B, int64_t ldb,
                                                      int64_t k) {
-  __shared__ double Rs[kTB][kTB + 1];
+  __shared__ Acc Rs[kTB][kTB + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < kTB * kTB; e += 256) {
     const int r = e % kTB, c = e / kTB;
-    Rs[r][c] = (r < nbt && c < nbt && r <= c) ? (double)F[i0 + r + (i0 + c) * ld] : 0.0;
+    Rs[r][c] = (r < nbt && c < nbt && r <= c) ? (Acc)F[i0 + r + (i0 + c) * ld] : (Acc)0;
   }
   __syncthreads();
   const int64_t col = (int64_t)blockIdx.x * 8 + warp;
   if (col >= k) return;
-  double* y = B + i0 + col * ldb;
-  double y0 = lane < nbt ? y[lane] : 0.0;
-  double y1 = lane + 32 < nbt ? y[lane + 32] : 0.0;
+  TB* y = B + i0 + col * ldb;
+  Acc y0 = lane < nbt ? (Acc)y[lane] : (Acc)0;
+  Acc y1 = lane + 32 < nbt ? (Acc)y[lane + 32] : (Acc)0;
   for (int i = 0; i < nbt; ++i) {
-    const double yi = __shfl_sync(0xffffffffu, i < 32 ? y0 : y1, i & 31);
-    const double zi = yi / Rs[i][i];
+    const Acc yi = __shfl_sync(0xffffffffu, i < 32 ? y0 : y1, i & 31);
+    const Acc zi = yi / Rs[i][i];
     if (i < 32) {
       if (lane == i) y0 = zi;
     } else if (lane == i - 32) {
@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(256) k_trsm_diag_t(const S* __restrict__ F, in
     if (lane > i && lane < nbt) y0 -= Rs[i][lane] * zi;
     if (lane + 32 > i && lane + 32 < nbt) y1 -= Rs[i][lane + 32] * zi;
   }
-  if (lane < nbt) y[lane] = y0;
-  if (lane + 32 < nbt) y[lane + 32] = y1;
+  if (lane < nbt) y[lane] = (TB)y0;
+  if (lane + 32 < nbt) y[lane + 32] = (TB)y1;
 }
 
 // Rank / finiteness test on diag(R): CT_ERR_RANK when some
@@ -165,26 +165,34 @@ ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int6
   return CT_OK;
 }
 
-// B[0:n, 0:k] <- R^{-T} B[0:n, 0:k] (FP64 B, FP64 arithmetic): blocks top-down,
-// diagonal forward solve, then the rows below get B[i1:n] -= R[i0:i1, i1:n]^T Z.
-ct_status launch_trsm_t(const ct_factor* f, double* B, int64_t ldb, int64_t k, cudaStream_t s) {
+// B[0:n, 0:k] <- R^{-T} B[0:n, 0:k]: blocks top-down, diagonal forward solve,
+// then the rows below get B[i1:n] -= R[i0:i1, i1:n]^T Z.  FP64 B in FP64
+// arithmetic; FP32 B (FP32-stored R only) in FP32.
+ct_status launch_trsm_t(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
   const int64_t n = f->n;
   const bool f64 = f->store == CT_F64;
+  if (!b_f64 && f64) return CT_ERR_UNSUPPORTED;
+  const size_t esz = b_f64 ? 8 : 4;
   for (int64_t i0 = 0; i0 < n; i0 += kTB) {
     const int nbt = (int)(n - i0 < kTB ? n - i0 : kTB);
     const unsigned grid = (unsigned)((k + 7) / 8);
     {
-      LaunchScope ls(K_TRSM_DIAG, s, (double)nbt * nbt * k, (double)nbt * nbt * (f64 ? 8 : 4) + 16.0 * nbt * k);
-      if (f64) k_trsm_diag_t<double><<<grid, 256, 0, s>>>((const double*)f->F, f->ld, i0, nbt, B, ldb, k);
-      else k_trsm_diag_t<float><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, B, ldb, k);
+      LaunchScope ls(K_TRSM_DIAG, s, (double)nbt * nbt * k, (double)nbt * nbt * (f64 ? 8 : 4) + 2.0 * esz * nbt * k);
+      if (f64)
+        k_trsm_diag_t<double, double, double><<<grid, 256, 0, s>>>((const double*)f->F, f->ld, i0, nbt, (double*)B, ldb, k);
+      else if (b_f64)
+        k_trsm_diag_t<float, double, double><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, (double*)B, ldb, k);
+      else
+        k_trsm_diag_t<float, float, float><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, (float*)B, ldb, k);
     }
     CT_LAUNCH_CHECK();
     const int64_t i1 = i0 + nbt;
     if (i1 < n) {
       const void* Rrow = f64 ? (const void*)((const double*)f->F + i0 + i1 * f->ld)
                              : (const void*)((const float*)f->F + i0 + i1 * f->ld);
-      ct_status st = launch_dense_update_t(Rrow, f64, f->ld, nbt, B + i0, ldb, B + i1, ldb, n - i1, k, s);
+      ct_status st = launch_dense_update_t(Rrow, f64, f->ld, nbt, (const char*)B + i0 * esz, ldb,
+                                           (char*)B + i1 * esz, b_f64, ldb, n - i1, k, s);
       if (st != CT_OK) return st;
     }
   }

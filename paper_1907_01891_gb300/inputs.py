@@ -78,14 +78,18 @@ def fan_geometry(npix: int, n_views: int, n_bins: int, pixel: float = 1.0,
 
 
 # The five workloads (sizes, seeds, noise) the tests and the benchmark use.
+# lam > 0 stacks lam*I under the ray rows.  The 256x256 fan geometry has
+# only 1.06 rays per pixel and its A is numerically rank deficient (scaled
+# analogues have condition numbers near 1e17), so that workload is solved as
+# the Tikhonov-stacked system [A; 1e-3 I] x = [b; 0].
 CONFIG1 = dict(name="parallel32_60x45_k1", geom=parallel_geometry(32, 60, 45),
-               seeds=[1], n_ellipses=5, noise_i0=None)
+               seeds=[1], n_ellipses=5, noise_i0=None, lam=0.0)
 CONFIG2 = dict(name="fan128_128x181_k16", geom=fan_geometry(128, 128, 181),
-               seeds=list(range(100, 116)), n_ellipses=5, noise_i0=1e5)
-CONFIG3 = dict(name="fan256_192x363_k64", geom=fan_geometry(256, 192, 363),
-               seeds=list(range(200, 264)), n_ellipses=5, noise_i0=None)
+               seeds=list(range(100, 116)), n_ellipses=5, noise_i0=1e5, lam=0.0)
+CONFIG3 = dict(name="fan256_192x363_k64_lam1e-3", geom=fan_geometry(256, 192, 363),
+               seeds=list(range(200, 264)), n_ellipses=5, noise_i0=None, lam=1e-3)
 CONFIG4A = dict(name="parallel32_60x45_k512", geom=parallel_geometry(32, 60, 45),
-                seeds=list(range(1000, 1512)), n_ellipses=5, noise_i0=1e4)
+                seeds=list(range(1000, 1512)), n_ellipses=5, noise_i0=1e4, lam=0.0)
 
 
 def ellipse_phantom(nx: int, ny: int, pixel: float, seed: int, n_ellipses: int = 5) -> np.ndarray:
