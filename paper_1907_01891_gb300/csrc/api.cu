@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/ctqr.h: argument checks, the factor's
 // lifetime, and the host-side sequencing of the kernels on the caller's stream.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -120,6 +121,18 @@ class Refiner {
         s_(s), sms_(sms), m_(f->m), n_(f->n), ldw_((f->m + 3) / 4 * 4) {}
 
   ct_status run(const ct_refine_opts* o, ct_report* rep) {
+    // Work on a private stream ordered after the caller's (graph capture is
+    // not allowed on the legacy default stream); the caller's stream waits
+    // for it at the end.
+    ct_status st0 = own_.attach(s_);
+    if (st0 != CT_OK) return st0;
+    s_ = own_.s;
+    ct_status r = run_inner(o, rep);
+    own_.detach();
+    return r;
+  }
+
+  ct_status run_inner(const ct_refine_opts* o, ct_report* rep) {
     const int max_iter = o && o->max_iter > 0 ? o->max_iter : 200;
     tol_ = o && o->tol > 0.0 ? o->tol : 1e-12;
     lam_ = o && o->lambda > 0.0 ? o->lambda : 0.0;
@@ -146,7 +159,12 @@ class Refiner {
         if (cgls_now) { go_cgls = true; break; }
         continue;
       }
+      // The first residual tells whether B is consistent: a residual well
+      // above rounding level means noisy data, where only CGLS can reach the
+      // least-squares solution.
+      if (it == 1 && method == 0 && resid_ > 1e-6) { go_cgls = true; break; }
       last_ = worst;
+      if (trace_) fprintf(stderr, "ctqr classical %d: max |dx|/|x| = %.3e\n", it, worst);
       if (worst <= tol_) { result = CT_OK; break; }
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
       if (!classical_only && it >= 2 && worst > 0.25 * prev) { go_cgls = true; break; }
@@ -166,6 +184,27 @@ class Refiner {
   }
 
  private:
+  // A non-blocking stream that follows `parent` (declared first: destroyed
+  // after the scratch buffers whose frees are queued on it).
+  struct OwnStream {
+    cudaStream_t s = nullptr, parent = nullptr;
+    cudaEvent_t ev = nullptr;
+    ct_status attach(cudaStream_t p) {
+      parent = p;
+      CT_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      CT_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      CT_CUDA_TRY(cudaEventRecord(ev, parent));
+      CT_CUDA_TRY(cudaStreamWaitEvent(s, ev, 0));
+      return CT_OK;
+    }
+    void detach() {
+      if (s && ev && cudaEventRecord(ev, s) == cudaSuccess) cudaStreamWaitEvent(parent, ev, 0);
+    }
+    ~OwnStream() {
+      if (ev) cudaEventDestroy(ev);
+      if (s) cudaStreamDestroy(s);
+    }
+  } own_;
   const ct_factor* f_;
   const void* A_;
   bool a64_;
@@ -187,6 +226,10 @@ class Refiner {
   std::vector<double> h_;
 
   bool f32() const { return f_->store == CT_F32; }
+  // Diagnostics: CTQR_TRACE=1 prints every step's update size to stderr;
+  // CTQR_PRECOND_F64=1 runs the preconditioner solves in FP64 arithmetic.
+  bool trace_ = getenv("CTQR_TRACE") != nullptr;
+  bool precond_f64_ = getenv("CTQR_PRECOND_F64") != nullptr;
 
   ct_status alloc() {
     ct_status st;
@@ -283,11 +326,52 @@ class Refiner {
     return CT_OK;
   }
 
+  // A captured sequence of launches replayed as one CUDA graph.
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;
+    GraphCounts counts{};
+    ~Graph() {
+      if (exec) cudaGraphExecDestroy(exec);
+    }
+  };
+  Graph g_solve_, g_solve_t_;
+
+  // The preconditioner solve on the fixed buffer Z, captured into a graph on
+  // first use (hundreds of small launches) and replayed afterwards.
+  ct_status precond_graph(double* Z, bool transpose, Graph& g) {
+    if (getenv("CTQR_NO_GRAPHS")) return precond(Z, transpose);
+    if (!g.exec && !g.failed) {
+      cudaGraph_t graph = nullptr;
+      profile_begin_capture();
+      cudaError_t e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeRelaxed);
+      ct_status st = e == cudaSuccess ? precond(Z, transpose) : CT_ERR_CUDA;
+      cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(s_, &graph) : e;
+      profile_end_capture(&g.counts);
+      if (st != CT_OK || e2 != cudaSuccess || !graph ||
+          cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        g.exec = nullptr;
+        g.failed = true;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      if (trace_) fprintf(stderr, "ctqr: preconditioner solve %s graph %s\n", transpose ? "R^-T" : "R^-1",
+                          g.exec ? "captured" : "capture failed, launching directly");
+      if (!g.exec) return precond(Z, transpose);
+    }
+    if (!g.exec) return precond(Z, transpose);
+    LaunchScope ls(K_TRSM_DIAG, s_, 0.0, 0.0);
+    CT_CUDA_TRY(cudaGraphLaunch(g.exec, s_));
+    profile_note_replay(g.counts);
+    return CT_OK;
+  }
+
   // In-place preconditioner solves on an n x k FP64 block (ld n): R^{-1}
   // (transpose = false) or R^{-T}; FP32 arithmetic for an FP32-stored R.
   ct_status precond(double* Z, bool transpose) {
     ct_status st;
-    if (!f32()) return transpose ? launch_trsm_t(f_, Z, true, n_, k_, s_) : launch_trsm(f_, Z, true, n_, k_, s_);
+    if (!f32() || precond_f64_)
+      return transpose ? launch_trsm_t(f_, Z, true, n_, k_, s_) : launch_trsm(f_, Z, true, n_, k_, s_);
     float* D = (float*)D_.p;
     if ((st = launch_copy_matrix(Z, CT_F64, n_, D, CT_F32, n_, n_, k_, s_)) != CT_OK) return st;
     if ((st = transpose ? launch_trsm_t(f_, D, false, n_, k_, s_) : launch_trsm(f_, D, false, n_, k_, s_)) != CT_OK)
@@ -304,7 +388,7 @@ class Refiner {
       return st;
     }
     if (lam_ > 0.0 && (st = launch_colwise(0, lam_, nullptr, Yd_ + ma_, ldw_, S, n_, n_, k_, s_)) != CT_OK) return st;
-    return precond(S, true);
+    return precond_graph(S, true, g_solve_t_);
   }
 
   // Flexible preconditioned CGLS on min ||[A; lambda I] x - B|| from the
@@ -335,7 +419,7 @@ class Refiner {
       *used = it + 1;
       // t = R^{-1} p ; q = [A; lambda I] t
       if ((st = launch_copy_matrix(P_, CT_F64, n_, T_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
-      if ((st = precond(T_, false)) != CT_OK) return st;
+      if ((st = precond_graph(T_, false, g_solve_)) != CT_OK) return st;
       if ((st = mul_A(T_, n_, Q_)) != CT_OK) return st;
       if ((st = launch_col_dots(Yd_, ldw_, Q_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;   // <r, q>
       if ((st = launch_col_norms2(Q_, ldw_, m_, k_, n2_, s_)) != CT_OK) return st;           // ||q||^2
@@ -354,6 +438,7 @@ class Refiner {
       if ((st = launch_colwise(0, 1.0, a_, T_, n_, X_, ldx_, n_, k_, s_)) != CT_OK) return st;    // x += a t
       if ((st = launch_colwise(0, -1.0, a_, Q_, ldw_, Yd_, ldw_, m_, k_, s_)) != CT_OK) return st;  // r -= a q
       last_ = worst;
+      if (trace_) fprintf(stderr, "ctqr cgls %d: max |dx|/|x| = %.3e\n", it, worst);
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
       if (worst <= tol_) {
         CT_CUDA_TRY(cudaStreamSynchronize(s_));

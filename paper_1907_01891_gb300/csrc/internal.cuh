@@ -87,6 +87,16 @@ enum KernelClass {
   K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_COUNT
 };
 
+// Graph capture: launches made between begin and end are recorded into
+// `GraphCounts` instead of the counters; each replay adds them back.
+struct GraphCounts {
+  uint64_t launches[K_COUNT];
+  double flops[K_COUNT];
+};
+void profile_begin_capture();
+void profile_end_capture(GraphCounts* out);
+void profile_note_replay(const GraphCounts& c);
+
 class LaunchScope {
  public:
   LaunchScope(int cls, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
@@ -225,6 +235,12 @@ struct SparseSystem {
   // S = A^T R; R m x k, S n x k.
   ct_status apply_t(const double* R, int64_t ldr, int64_t k, double* S, int64_t lds, cudaStream_t s) const;
 };
+
+// C (M x N) -= A^T B, persistent tensor-core kernel on operands split into
+// TF32 high (Ah, Bh) and low (Al, Bl) parts (low parts unused unless split3).
+ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, const float* Bh, const float* Bl,
+                             int64_t ldb, int64_t M, int64_t N, int64_t K, float* C, int64_t ldc, bool split3,
+                             int sms, int* status, cudaStream_t s);
 
 // ---- utilities (util.cu) ---------------------------------------------------
 ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,

@@ -21,12 +21,16 @@ namespace {
 
 constexpr int kNB = 128;
 
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 // Vc (column-major, ld ldvc) and Vr (row-major, row stride kNB) get the
 // explicit reflectors of the block: V(r, a) = F stored value for r > a, 1 on
-// the diagonal, 0 above; columns a >= nbo are zero.
+// the diagonal, 0 above; columns a >= nbo are zero.  With Vrl != NULL the
+// row-major copy is split for error-compensated TF32: Vr = hi part (exact in
+// TF32), Vrl = x - hi.
 __global__ void __launch_bounds__(256) k_extract_v(const float* __restrict__ F, int64_t ld, int64_t mr,
                                                    int nbo, float* __restrict__ Vc, int64_t ldvc,
-                                                   float* __restrict__ Vr) {
+                                                   float* __restrict__ Vr, float* __restrict__ Vrl) {
   __shared__ float tile[32][kNB + 1];
   const int64_t r0 = (int64_t)blockIdx.x * 32;
   for (int e = threadIdx.x; e < 32 * kNB; e += 256) {
@@ -41,7 +45,16 @@ __global__ void __launch_bounds__(256) k_extract_v(const float* __restrict__ F, 
   for (int e = threadIdx.x; e < 32 * kNB; e += 256) {
     const int a = e % kNB, rr = e / kNB;
     const int64_t r = r0 + rr;
-    if (r < mr) Vr[r * kNB + a] = tile[rr][a];
+    if (r < mr) {
+      const float x = tile[rr][a];
+      if (Vrl) {
+        const float h = tf32_hi(x);
+        Vr[r * kNB + a] = h;
+        Vrl[r * kNB + a] = x - h;
+      } else {
+        Vr[r * kNB + a] = x;
+      }
+    }
   }
 }
 
@@ -53,7 +66,7 @@ constexpr size_t kSolveSmem = (size_t)(kNB * kGS + kNB) * sizeof(float);
 __global__ void __launch_bounds__(256) k_solve_st(const float* __restrict__ Wp, int wsplits, int64_t wstride,
                                                   const float* __restrict__ Gp, int gsplits, int64_t gstride,
                                                   const double* __restrict__ tau, int nbo, int64_t nc,
-                                                  float* __restrict__ Wout) {
+                                                  float* __restrict__ Wout, float* __restrict__ Wlo) {
   extern __shared__ float sm[];
   float* G = sm;              // G[i * kGS + r] = (V^T V)(i, r), strict upper part
   float* ts = sm + kNB * kGS;
@@ -88,7 +101,16 @@ __global__ void __launch_bounds__(256) k_solve_st(const float* __restrict__ Wp, 
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Wout[lane + 32 * q + c * kNB] = w[q];
+    for (int q = 0; q < 4; ++q) {
+      const int64_t o = lane + 32 * q + c * kNB;
+      if (Wlo) {
+        const float h = tf32_hi(w[q]);
+        Wout[o] = h;
+        Wlo[o] = w[q] - h;
+      } else {
+        Wout[o] = w[q];
+      }
+    }
   }
 }
 
@@ -98,9 +120,9 @@ size_t outer_work_floats(int sms, int64_t m, int64_t n) {
   const int64_t mp = (m + 3) / 4 * 4;
   const int64_t wcols = n > (int64_t)4 * sms * 128 ? n : (int64_t)4 * sms * 128;
   return (size_t)mp * kNB          // Vc
-         + (size_t)m * kNB         // Vr
+         + (size_t)2 * m * kNB     // Vr (high, low)
          + (size_t)kNB * wcols     // W partials
-         + (size_t)kNB * n         // W'
+         + (size_t)2 * kNB * n     // W' (high, low)
          + (size_t)2 * sms * kNB * kNB;  // G partials
 }
 
@@ -115,13 +137,16 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
   const int64_t wcols = n > (int64_t)4 * sms * 128 ? n : (int64_t)4 * sms * 128;
   float* Vc = work;
   float* Vr = Vc + (size_t)ldvc * kNB;
-  float* Wp = Vr + (size_t)m * kNB;
+  float* Vrl = Vr + (size_t)m * kNB;
+  float* Wp = Vrl + (size_t)m * kNB;
   float* Wq = Wp + (size_t)kNB * wcols;
-  float* Gp = Wq + (size_t)kNB * n;
+  float* Wql = Wq + (size_t)kNB * n;
+  float* Gp = Wql + (size_t)kNB * n;
   if (outer_work_floats(sms, m, n) > work_floats) return CT_ERR_INVALID;
   {
     LaunchScope ls(K_COPY, s, 0.0, (double)mr * kNB * 12);
-    k_extract_v<<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, Vc, ldvc, Vr);
+    k_extract_v<<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, Vc, ldvc, Vr,
+                                                           split3 ? Vrl : nullptr);
     CT_LAUNCH_CHECK();
   }
   ct_status st;
@@ -162,11 +187,12 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
       attr = true;
     }
     k_solve_st<<<grid, 256, kSolveSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Gp, gs, (int64_t)kNB * kNB,
-                                    f->tau + J, nbo, nc, Wq);
+                                    f->tau + J, nbo, nc, Wq, split3 ? Wql : nullptr);
     CT_LAUNCH_CHECK();
   }
-  // C -= V W'  (A = V stored row-major: kNB x mr column-major with ld kNB).
-  return tc_gemm_tn(Vr, kNB, Wq, kNB, mr, nc, kNB, C, ld, 0, 1, 1, split3, f->status, s);
+  // C -= V W'  (A = V stored row-major: kNB x mr column-major with ld kNB),
+  // persistent kernel on the pre-split operands.
+  return tc_update_presplit(Vr, Vrl, kNB, Wq, Wql, kNB, mr, nc, kNB, C, ld, split3, sms, f->status, s);
 }
 
 }  // namespace ctqr

@@ -19,6 +19,9 @@ struct Pending {
 struct Profiler {
   std::mutex mu;
   bool timing = false;
+  bool capturing = false;           // launches are being recorded into a graph
+  uint64_t captured[K_COUNT] = {};  // launches recorded since begin_capture
+  double captured_flops[K_COUNT] = {};
   uint64_t launches[K_COUNT] = {};
   uint64_t timed[K_COUNT] = {};
   double ms[K_COUNT] = {};
@@ -72,6 +75,11 @@ LaunchScope::LaunchScope(int cls, cudaStream_t s, double flops, double bytes)
     : cls_(cls), s_(s), start_(nullptr) {
   Profiler& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
+  if (p.capturing) {  // recorded into a graph: counted when the graph is replayed
+    p.captured[cls] += 1;
+    p.captured_flops[cls] += flops;
+    return;
+  }
   p.launches[cls] += 1;
   p.flops[cls] += flops;
   p.bytes[cls] += bytes;
@@ -89,6 +97,35 @@ LaunchScope::~LaunchScope() {
   if (!stop) return;
   cudaEventRecord(stop, s_);
   p.pending.push_back({(cudaEvent_t)start_, stop, cls_});
+}
+
+void profile_begin_capture() {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.capturing = true;
+  for (int i = 0; i < K_COUNT; ++i) {
+    p.captured[i] = 0;
+    p.captured_flops[i] = 0.0;
+  }
+}
+
+void profile_end_capture(GraphCounts* out) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.capturing = false;
+  for (int i = 0; i < K_COUNT; ++i) {
+    out->launches[i] = p.captured[i];
+    out->flops[i] = p.captured_flops[i];
+  }
+}
+
+void profile_note_replay(const GraphCounts& c) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  for (int i = 0; i < K_COUNT; ++i) {
+    p.launches[i] += c.launches[i];
+    p.flops[i] += c.flops[i];
+  }
 }
 
 }  // namespace ctqr

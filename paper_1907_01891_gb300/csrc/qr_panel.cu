@@ -231,6 +231,17 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   }
 }
 
+// CTAs for an mr-row panel: about 64 rows each, at most one per SM (measured:
+// fewer, fuller CTAs were slower for both arithmetic types).
+int panel_grid(int64_t mr, const DeviceInfo& di, size_t mth) {
+  (void)mth;
+  const int rows_per_cta = 64;
+  int grid = (int)((mr + rows_per_cta - 1) / rows_per_cta);
+  if (grid > di.sms) grid = di.sms;
+  if (grid < 1) grid = 1;
+  return grid;
+}
+
 size_t panel_smem_bytes(int nbp, int rp, size_t mth) {
   const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb) * sizeof(double) + kMaxNb * mth;
   size_t bytes = small + (size_t)nbp * rp * mth;
@@ -242,9 +253,7 @@ template <typename S, typename Mth>
 ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStream_t s,
                          const DeviceInfo& di) {
   const int64_t mr = f->m - j0;
-  int grid = (int)((mr + 63) / 64);
-  if (grid > di.sms) grid = di.sms;
-  if (grid < 1) grid = 1;
+  int grid = panel_grid(mr, di, sizeof(Mth));
   int rp = (int)((mr + grid - 1) / grid);
   const size_t smem = panel_smem_bytes(nbp, rp, sizeof(Mth));
   if (smem > (size_t)di.smem_optin) return CT_ERR_UNSUPPORTED;
@@ -285,9 +294,7 @@ size_t panel_partials_elems(int sms, int nb) {
 // Largest panel width <= want (halving when pow2) whose shared-memory slab
 // fits for mr rows; mth = bytes of the panel arithmetic type.
 int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth, bool pow2) {
-  int grid = (int)((mr + 63) / 64);
-  if (grid > di.sms) grid = di.sms;
-  if (grid < 1) grid = 1;
+  int grid = panel_grid(mr, di, mth);
   const int rp = (int)((mr + grid - 1) / grid);
   int nb = want > kMaxNb ? kMaxNb : want;
   while (nb > 8 && panel_smem_bytes(nb, rp, mth) > (size_t)di.smem_optin) nb = pow2 ? nb / 2 : nb - 8;

@@ -306,6 +306,170 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent update C (M x N) -= A^T B for a short contraction (K = 128 in the
+// outer-block update), operands already split into TF32 high/low arrays by
+// the kernels that produce them.  One CTA per SM walks output tiles
+// t = blockIdx.x, +gridDim.x, ... (m fastest, so concurrent tiles share the
+// B tile in L2).  Warp 0 streams operand slices with TMA; warp 1 issues the
+// MMAs into one of two TMEM accumulators (128 columns each); warps 4-11 drain
+// the other accumulator meanwhile: each thread owns one row and 64 columns of
+// the tile, issues its 64 loads of C at once, subtracts the accumulator and
+// stores.  So a tile's epilogue overlaps the next tile's MMAs, and C's load
+// latency is paid once per tile, not once per column.
+// ---------------------------------------------------------------------------
+constexpr int kUpdThreads = 384;
+
+struct UpdArgs {
+  int64_t M, N, K;
+  float* C;
+  int64_t ldc;
+  int64_t mtiles, ntiles;
+  int* status;
+};
+
+template <bool SPLIT3, int STAGES>
+__global__ void __launch_bounds__(kUpdThreads, 1)
+    k_tc_update(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, UpdArgs args) {
+  constexpr uint32_t TILE = kBM * kBK * 4;  // 16 KB: 128 rows x 32 floats
+  constexpr uint32_t STAGE_BYTES = TILE * (SPLIT3 ? 4 : 2);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntile = args.mtiles * args.ntiles;
+  const int nk = (int)((args.K + kBK - 1) / kBK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(256u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t g = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        const int m0 = (int)((t % args.mtiles) * kBM), n0 = (int)((t / args.mtiles) * kBM);
+        for (int ks = 0; ks < nk; ++ks, ++g) {
+          const int s = (int)(g % STAGES);
+          const int64_t u = g / STAGES;
+          if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), args.status)) { ok = false; break; }
+          unsigned char* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          const int x = ks * kBK;
+          tma_load_2d(st, &tmAh, x, m0, &full[s]);
+          tma_load_2d(st + TILE, &tmBh, x, n0, &full[s]);
+          if (SPLIT3) {
+            tma_load_2d(st + 2 * TILE, &tmAl, x, m0, &full[s]);
+            tma_load_2d(st + 3 * TILE, &tmBl, x, n0, &full[s]);
+          }
+        }
+      }
+      if (!ok) {
+        // Error exit: let the copies already issued land before the CTA ends.
+        for (int64_t q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+          mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), args.status, false);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBM >> 3) << 17) |
+                             ((uint32_t)(kBM >> 4) << 24);
+      int64_t g = 0;
+      int it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1, ua = it >> 1;
+        if (ua > 0 && !mbar_wait(&tempty[acc], (uint32_t)((ua - 1) & 1), args.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * kBM);
+        for (int ks = 0; ks < nk; ++ks, ++g) {
+          const int s = (int)(g % STAGES);
+          const int64_t u = g / STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)(u & 1), args.status)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char* st = smem + s * STAGE_BYTES;
+          const uint64_t dah = sdesc_sw128(st), dbh = sdesc_sw128(st + TILE);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 8; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 2);
+            mma_tf32(d, dah + adv, dbh + adv, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+            if (SPLIT3) {
+              const uint64_t dal = sdesc_sw128(st + 2 * TILE), dbl = sdesc_sw128(st + 3 * TILE);
+              mma_tf32(d, dal + adv, dbh + adv, idesc, 1u);
+              mma_tf32(d, dah + adv, dbl + adv, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&tfull[acc]);
+      }
+    }
+  } else if (warp >= 4) {
+    const int lg = warp & 3, half = (warp - 4) >> 2;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
+      const int acc = it & 1, ua = it >> 1;
+      const int64_t m0 = (t % args.mtiles) * kBM, n0 = (t / args.mtiles) * kBM;
+      const int64_t row = m0 + lg * 32 + lane;
+      const int64_t c0 = n0 + half * 64;
+      const bool rok = row < args.M;
+      float c[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j)
+        c[j] = (rok && c0 + j < args.N) ? args.C[row + (c0 + j) * args.ldc] : 0.f;
+      if (!mbar_wait(&tfull[acc], (uint32_t)(ua & 1), args.status)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * kBM + half * 64 + q * 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) c[q * 16 + i] -= v[i];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (rok) {
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+          if (c0 + j < args.N) args.C[row + (c0 + j) * args.ldc] = c[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -357,7 +521,59 @@ ct_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& 
   return CT_OK;
 }
 
+template <bool SPLIT3, int STAGES>
+ct_status launch_upd(const CUtensorMap* maps, const UpdArgs& a, int sms, cudaStream_t s) {
+  constexpr size_t STAGE_BYTES = (size_t)kBM * kBK * 4 * (SPLIT3 ? 4 : 2);
+  const size_t smem = STAGES * STAGE_BYTES + 1024 + 256;
+  static bool attr_done = false;
+  if (!attr_done) {
+    CT_CUDA_TRY(cudaFuncSetAttribute(k_tc_update<SPLIT3, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    attr_done = true;
+  }
+  const int64_t tiles = a.mtiles * a.ntiles;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+  k_tc_update<SPLIT3, STAGES><<<grid, kUpdThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
 }  // namespace
+
+// C (M x N) -= A^T B with pre-split operands (Ah/Al: K x M, Bh/Bl: K x N,
+// column-major FP32, lda/ldb multiples of 4); Al/Bl ignored unless split3.
+ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, const float* Bh, const float* Bl,
+                             int64_t ldb, int64_t M, int64_t N, int64_t K, float* C, int64_t ldc, bool split3,
+                             int sms, int* status, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return CT_OK;
+  if (!Ah || !Bh || !C || (split3 && (!Al || !Bl)) || lda < K || ldb < K || ldc < M) return CT_ERR_INVALID;
+  if (((uintptr_t)Ah & 15) || ((uintptr_t)Bh & 15) || (split3 && (((uintptr_t)Al & 15) || ((uintptr_t)Bl & 15))) ||
+      (lda & 3) || (ldb & 3))
+    return CT_ERR_INVALID;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return CT_ERR_INVALID;
+  CUtensorMap maps[4];
+  if (!make_map(&maps[0], Ah, (uint64_t)K, (uint64_t)M, (uint64_t)lda, kBK, kBM)) return CT_ERR_CUDA;
+  if (!make_map(&maps[2], Bh, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, kBK, kBM)) return CT_ERR_CUDA;
+  if (split3) {
+    if (!make_map(&maps[1], Al, (uint64_t)K, (uint64_t)M, (uint64_t)lda, kBK, kBM)) return CT_ERR_CUDA;
+    if (!make_map(&maps[3], Bl, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, kBK, kBM)) return CT_ERR_CUDA;
+  } else {
+    maps[1] = maps[0];
+    maps[3] = maps[2];
+  }
+  UpdArgs a;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.C = C;
+  a.ldc = ldc;
+  a.mtiles = (M + kBM - 1) / kBM;
+  a.ntiles = (N + kBM - 1) / kBM;
+  a.status = status;
+  LaunchScope ls(K_TC_GEMM, s, 2.0 * M * N * K, 4.0 * ((double)K * (M + N) * (split3 ? 2 : 1) + 2.0 * M * N));
+  if (split3) return launch_upd<true, 3>(maps, a, sms, s);
+  return launch_upd<false, 6>(maps, a, sms, s);
+}
 
 // C (M x N) = / -= A^T B on the tensor cores; see the file comment.
 ct_status tc_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,

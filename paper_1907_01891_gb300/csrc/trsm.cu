@@ -4,10 +4,10 @@
 // The paper's solve runs, for each block of 3 b x b tiles, a triangular solve
 // of a diagonal block (Trsm_lunn) and matrix products with the blocks above
 // (Gemm_nn_mo), ordered by block rows to keep its disk cache small.  In HBM the
-// order is chosen for parallelism instead: blocks of nbt columns are taken
-// bottom-up; the diagonal block is solved (one warp per right-hand side) and
-// then all rows above are updated at once with a tall dense product
-// Y[0:i0] -= R[0:i0, i0:i1] X[i0:i1] that spreads over the whole GPU.
+// order is chosen for parallelism instead: the rows are halved recursively;
+// the bottom half is solved, the top half gets one dense product with it
+// (spread over the whole GPU), then the top half is solved; the leaves are
+// 64 x 64 diagonal solves (one warp per right-hand side).
 #include <math.h>
 
 #include "internal.cuh"
@@ -131,72 +131,94 @@ __global__ void __launch_bounds__(1024) k_rank_check(const S* __restrict__ F, in
 
 }  // namespace
 
-// B[0:n, 0:k] <- R^{-1} B[0:n, 0:k]; B is FP64 (b_f64) or FP32.  FP64 B is
-// solved in FP64 arithmetic whatever R's storage type; FP32 B (the correction
-// solve of the mixed-precision refinement) in FP32.
-ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k,
-                      cudaStream_t s) {
-  if (k <= 0 || f->n <= 0) return CT_OK;
-  const int64_t n = f->n;
-  const int64_t nblk = (n + kTB - 1) / kTB;
-  const bool f64 = f->store == CT_F64;
-  if (!b_f64 && f64) return CT_ERR_UNSUPPORTED;
-  const size_t esz = b_f64 ? 8 : 4;
-  for (int64_t blk = nblk - 1; blk >= 0; --blk) {
-    const int64_t i0 = blk * kTB;
-    const int nbt = (int)(n - i0 < kTB ? n - i0 : kTB);
-    const unsigned grid = (unsigned)((k + 7) / 8);
-    LaunchScope ls(K_TRSM_DIAG, s, (double)nbt * nbt * k, (double)nbt * nbt * (f64 ? 8 : 4) + 2.0 * nbt * k * esz);
-    if (f64)
-      k_trsm_diag<double, double, double><<<grid, 256, 0, s>>>((const double*)f->F, f->ld, i0, nbt, (double*)B, ldb, k);
-    else if (b_f64)
-      k_trsm_diag<float, double, double><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, (double*)B, ldb, k);
-    else
-      k_trsm_diag<float, float, float><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, (float*)B, ldb, k);
-    CT_LAUNCH_CHECK();
-    if (i0 > 0) {
-      const void* Rcol = f64 ? (const void*)((const double*)f->F + i0 * f->ld)
-                             : (const void*)((const float*)f->F + i0 * f->ld);
-      const void* Xblk = (const char*)B + (size_t)i0 * esz;
-      ct_status st = launch_dense_update(Rcol, f64, f->ld, nbt, Xblk, ldb, B, b_f64, ldb, i0, k, s);
-      if (st != CT_OK) return st;
-    }
+namespace {
+
+struct TrsmCtx {
+  const ct_factor* f;
+  void* B;
+  bool b_f64;
+  int64_t ldb, k;
+  size_t esz;
+  cudaStream_t s;
+  const void* R(int64_t r, int64_t c) const {
+    return f->store == CT_F64 ? (const void*)((const double*)f->F + r + c * f->ld)
+                              : (const void*)((const float*)f->F + r + c * f->ld);
   }
+  void* Brow(int64_t r) const { return (char*)B + (size_t)r * esz; }
+};
+
+ct_status diag_solve(const TrsmCtx& c, int64_t i0, int nbt, bool transpose) {
+  const bool f64 = c.f->store == CT_F64;
+  const unsigned grid = (unsigned)((c.k + 7) / 8);
+  LaunchScope ls(K_TRSM_DIAG, c.s, (double)nbt * nbt * c.k,
+                 (double)nbt * nbt * (f64 ? 8 : 4) + 2.0 * c.esz * nbt * c.k);
+  if (!transpose) {
+    if (f64)
+      k_trsm_diag<double, double, double><<<grid, 256, 0, c.s>>>((const double*)c.f->F, c.f->ld, i0, nbt, (double*)c.B, c.ldb, c.k);
+    else if (c.b_f64)
+      k_trsm_diag<float, double, double><<<grid, 256, 0, c.s>>>((const float*)c.f->F, c.f->ld, i0, nbt, (double*)c.B, c.ldb, c.k);
+    else
+      k_trsm_diag<float, float, float><<<grid, 256, 0, c.s>>>((const float*)c.f->F, c.f->ld, i0, nbt, (float*)c.B, c.ldb, c.k);
+  } else {
+    if (f64)
+      k_trsm_diag_t<double, double, double><<<grid, 256, 0, c.s>>>((const double*)c.f->F, c.f->ld, i0, nbt, (double*)c.B, c.ldb, c.k);
+    else if (c.b_f64)
+      k_trsm_diag_t<float, double, double><<<grid, 256, 0, c.s>>>((const float*)c.f->F, c.f->ld, i0, nbt, (double*)c.B, c.ldb, c.k);
+    else
+      k_trsm_diag_t<float, float, float><<<grid, 256, 0, c.s>>>((const float*)c.f->F, c.f->ld, i0, nbt, (float*)c.B, c.ldb, c.k);
+  }
+  CT_LAUNCH_CHECK();
   return CT_OK;
 }
 
-// B[0:n, 0:k] <- R^{-T} B[0:n, 0:k]: blocks top-down, diagonal forward solve,
-// then the rows below get B[i1:n] -= R[i0:i1, i1:n]^T Z.  FP64 B in FP64
-// arithmetic; FP32 B (FP32-stored R only) in FP32.
+// Rows [lo, hi) of R X = B, bottom half first, then the top half gets the
+// product with the solved bottom half: B[lo:mid] -= R[lo:mid, mid:hi] X[mid:hi]
+// (the Gemm_nn_mo task over a whole block row at once).
+ct_status solve_rec(const TrsmCtx& c, int64_t lo, int64_t hi) {
+  if (hi - lo <= kTB) return diag_solve(c, lo, (int)(hi - lo), false);
+  const int64_t mid = lo + ((hi - lo) / 2 + kTB - 1) / kTB * kTB;
+  ct_status st = solve_rec(c, mid, hi);
+  if (st != CT_OK) return st;
+  st = launch_dense_update(c.R(lo, mid), c.f->store == CT_F64, c.f->ld, (int)(hi - mid), c.Brow(mid), c.ldb,
+                           c.Brow(lo), c.b_f64, c.ldb, mid - lo, c.k, c.s);
+  if (st != CT_OK) return st;
+  return solve_rec(c, lo, mid);
+}
+
+// Rows [lo, hi) of R^T Z = B (forward substitution), top half first:
+// B[mid:hi] -= R[lo:mid, mid:hi]^T Z[lo:mid].
+ct_status solve_rec_t(const TrsmCtx& c, int64_t lo, int64_t hi) {
+  if (hi - lo <= kTB) return diag_solve(c, lo, (int)(hi - lo), true);
+  const int64_t mid = lo + ((hi - lo) / 2 + kTB - 1) / kTB * kTB;
+  ct_status st = solve_rec_t(c, lo, mid);
+  if (st != CT_OK) return st;
+  st = launch_dense_update_t(c.R(lo, mid), c.f->store == CT_F64, c.f->ld, (int)(mid - lo), c.Brow(lo), c.ldb,
+                             c.Brow(mid), c.b_f64, c.ldb, hi - mid, c.k, c.s);
+  if (st != CT_OK) return st;
+  return solve_rec_t(c, mid, hi);
+}
+
+}  // namespace
+
+// B[0:n, 0:k] <- R^{-1} B[0:n, 0:k]; B is FP64 (b_f64) or FP32.  FP64 B is
+// solved in FP64 arithmetic whatever R's storage type; FP32 B (the
+// preconditioner solves of the mixed-precision refinement) in FP32.
+// Recursive halving: 64 x 64 diagonal solves (Trsm_lunn) at the leaves and
+// one product per split for the block above (Gemm_nn_mo), so the products
+// are few and large instead of one K = 64 update per block column.
+ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
+  if (k <= 0 || f->n <= 0) return CT_OK;
+  if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
+  const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
+  return solve_rec(c, 0, f->n);
+}
+
+// B[0:n, 0:k] <- R^{-T} B[0:n, 0:k] (same arithmetic rules as launch_trsm).
 ct_status launch_trsm_t(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
-  const int64_t n = f->n;
-  const bool f64 = f->store == CT_F64;
-  if (!b_f64 && f64) return CT_ERR_UNSUPPORTED;
-  const size_t esz = b_f64 ? 8 : 4;
-  for (int64_t i0 = 0; i0 < n; i0 += kTB) {
-    const int nbt = (int)(n - i0 < kTB ? n - i0 : kTB);
-    const unsigned grid = (unsigned)((k + 7) / 8);
-    {
-      LaunchScope ls(K_TRSM_DIAG, s, (double)nbt * nbt * k, (double)nbt * nbt * (f64 ? 8 : 4) + 2.0 * esz * nbt * k);
-      if (f64)
-        k_trsm_diag_t<double, double, double><<<grid, 256, 0, s>>>((const double*)f->F, f->ld, i0, nbt, (double*)B, ldb, k);
-      else if (b_f64)
-        k_trsm_diag_t<float, double, double><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, (double*)B, ldb, k);
-      else
-        k_trsm_diag_t<float, float, float><<<grid, 256, 0, s>>>((const float*)f->F, f->ld, i0, nbt, (float*)B, ldb, k);
-    }
-    CT_LAUNCH_CHECK();
-    const int64_t i1 = i0 + nbt;
-    if (i1 < n) {
-      const void* Rrow = f64 ? (const void*)((const double*)f->F + i0 + i1 * f->ld)
-                             : (const void*)((const float*)f->F + i0 + i1 * f->ld);
-      ct_status st = launch_dense_update_t(Rrow, f64, f->ld, nbt, (const char*)B + i0 * esz, ldb,
-                                           (char*)B + i1 * esz, b_f64, ldb, n - i1, k, s);
-      if (st != CT_OK) return st;
-    }
-  }
-  return CT_OK;
+  if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
+  const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
+  return solve_rec_t(c, 0, f->n);
 }
 
 ct_status launch_rank_check(ct_factor* f, cudaStream_t s) {
