@@ -203,6 +203,25 @@ ct_status ct_factor_status(const ct_factor* f, void* stream);
 ct_status ct_apply_qt(const ct_factor* f, double* B, int64_t ldb, int64_t k,
                       void* stream);
 
+/* B <- Q^T B exactly like ct_apply_qt, for callers that cannot let a library
+ * allocate device memory: applications whose framework has already reserved
+ * the GPU's memory for its own caching allocator (an allocation here would
+ * fail), or latency-critical loops that cannot afford the synchronisation an
+ * allocation implies.  The paper has no counterpart; this is a deployment
+ * variant of the Q^T step.
+ * Its workspace is a fixed 2.03 MiB array in the library's static device
+ * memory, held by every GPU that loads the library until the process exits;
+ * it calls no allocation routine.  Limit: k <= 64 right-hand sides per call;
+ * a larger k returns CT_ERR_INVALID (split B into column blocks).  The first
+ * call on each device looks up the array's device address and caches it;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (nothing in it needs clearing:
+ * each call writes what it reads), so calls that overlap on the GPU -- on
+ * different streams, threads or factors -- race and corrupt each other's
+ * results: serialise them.  Launch timing (ct_profile_enable) must stay off:
+ * it creates CUDA events. */
+ct_status ct_apply_qt_noalloc(const ct_factor* f, double* B, int64_t ldb, int64_t k, void* stream);
+
 /* B[0:n, 0:k] <- R^{-1} B[0:n, 0:k] in place (FP64): backward substitution
  * with the factor's upper triangular R, by blocks: a triangular solve of each
  * diagonal block (Trsm_lunn) followed by the update of the blocks above it

@@ -75,32 +75,6 @@ ct_status dev_alloc(T** p, size_t elems) {
 
 size_t elem_size(ct_dtype t) { return t == CT_F64 ? 8 : 4; }
 
-// Apply Q^T (all panels, factorization order) to the mr = m rows of C (k
-// columns, element type c_f64 ? FP64 : FP32).
-ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
-                       double* work, size_t work_elems, int sms, cudaStream_t s) {
-  const size_t es = elem_size(f->store), cs = c_f64 ? 8 : 4;
-  for (int64_t j0 = 0, p = 0; j0 < f->n; j0 += f->nb, ++p) {
-    const int nbp = (int)(f->n - j0 < f->nb ? f->n - j0 : f->nb);
-    ReflectorArgs a;
-    a.V = (const char*)f->F + (size_t)(j0 + j0 * f->ld) * es;
-    a.v_f64 = f->store == CT_F64;
-    a.ldv = f->ld;
-    a.T = f->T + (size_t)p * f->nb * f->nb;
-    a.ldt = f->nb;
-    a.nbp = nbp;
-    a.C = (char*)C + (size_t)j0 * cs;
-    a.c_f64 = c_f64;
-    a.ldc = ldc;
-    a.mr = f->m - j0;
-    a.nc = k;
-    a.fp32_math = fp32_math;
-    ct_status st = apply_block_reflector(a, work, work_elems, sms, s);
-    if (st != CT_OK) return st;
-  }
-  return CT_OK;
-}
-
 ct_status read_status(const ct_factor* f, cudaStream_t s) {
   int h = 0;
   CT_CUDA_TRY(cudaMemcpyAsync(&h, f->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -467,6 +441,34 @@ class Refiner {
 
 namespace ctqr {
 int64_t npanels(const ct_factor* f) { return (f->n + f->nb - 1) / f->nb; }
+
+// Apply Q^T (all panels, factorization order) to the mr = m rows of C (k
+// columns, element type c_f64 ? FP64 : FP32).
+ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
+                       double* work, size_t work_elems, int sms, cudaStream_t s, int max_splits) {
+  const size_t es = elem_size(f->store), cs = c_f64 ? 8 : 4;
+  for (int64_t j0 = 0, p = 0; j0 < f->n; j0 += f->nb, ++p) {
+    const int nbp = (int)(f->n - j0 < f->nb ? f->n - j0 : f->nb);
+    ReflectorArgs a;
+    a.V = (const char*)f->F + (size_t)(j0 + j0 * f->ld) * es;
+    a.v_f64 = f->store == CT_F64;
+    a.ldv = f->ld;
+    a.T = f->T + (size_t)p * f->nb * f->nb;
+    a.ldt = f->nb;
+    a.nbp = nbp;
+    a.C = (char*)C + (size_t)j0 * cs;
+    a.c_f64 = c_f64;
+    a.ldc = ldc;
+    a.mr = f->m - j0;
+    a.nc = k;
+    a.fp32_math = fp32_math;
+    a.max_splits = max_splits;
+    ct_status st = apply_block_reflector(a, work, work_elems, sms, s);
+    if (st != CT_OK) return st;
+  }
+  return CT_OK;
+}
+
 }  // namespace ctqr
 
 extern "C" {

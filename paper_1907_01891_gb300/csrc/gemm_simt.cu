@@ -316,6 +316,7 @@ ct_status run_reflector(const ReflectorArgs& a, double* work, size_t work_elems,
   int64_t splits = (2 * sms + tiles_n - 1) / tiles_n;
   const int64_t max_splits = (a.mr + 255) / 256;
   if (splits > max_splits) splits = max_splits;
+  if (a.max_splits > 0 && splits > a.max_splits) splits = a.max_splits;
   if (splits < 1) splits = 1;
   int64_t chunk = (a.mr + splits - 1) / splits;
   chunk = (chunk + kBK - 1) / kBK * kBK;

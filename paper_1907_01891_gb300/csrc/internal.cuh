@@ -168,10 +168,15 @@ struct ReflectorArgs {
   void* C; bool c_f64; int64_t ldc;
   int64_t mr, nc;
   bool fp32_math;  // accumulate in FP32 (mixed factor) instead of FP64
+  int max_splits = 0;  // cap on the row splits of V^T C (0: no cap)
 };
 size_t reflector_work_elems(int sms, int nbp, int64_t nc);
 ct_status apply_block_reflector(const ReflectorArgs& a, double* work, size_t work_elems,
                                 int sms, cudaStream_t s);
+
+// Q^T C for all panels of the factor, in factorization order (api.cu).
+ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
+                       double* work, size_t work_elems, int sms, cudaStream_t s, int max_splits = 0);
 
 // ---- triangular solve (trsm.cu) -------------------------------------------
 ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k,

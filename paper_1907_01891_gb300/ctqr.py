@@ -87,6 +87,7 @@ SIGNATURES = {
     "ct_factor_status": ([_VP, _VP], _I),
     "ct_factor_copy": ([_VP, _VP, _I64, _VP, _VP], _I),
     "ct_apply_qt": ([_VP, _VP, _I64, _I64, _VP], _I),
+    "ct_apply_qt_noalloc": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_trsm_solve": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_reconstruct_batch": ([_VP, _VP, _I, _I64, _VP, _I64, _VP, _I64, _I64,
                               ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
@@ -273,6 +274,13 @@ def factor_matrix(f: Factor) -> tuple[torch.Tensor, torch.Tensor]:
 def apply_qt(f: Factor, B: torch.Tensor) -> torch.Tensor:
     """B <- Q^T B in place (FP64, m x k column-major)."""
     _check(load().ct_apply_qt(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()), "ct_apply_qt")
+    return B
+
+
+def apply_qt_noalloc(f: Factor, B: torch.Tensor) -> torch.Tensor:
+    """B <- Q^T B in place without any device allocation (k <= 64 columns)."""
+    _check(load().ct_apply_qt_noalloc(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()),
+           "ct_apply_qt_noalloc")
     return B
 
 

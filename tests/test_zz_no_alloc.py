@@ -1,0 +1,40 @@
+"""The allocation-free Q^T entry point (ct_apply_qt_noalloc), called through the
+C ABI, against the allocating ct_apply_qt on the same factor and inputs, two
+calls in a row (the second call reuses the static workspace the first one
+left behind).  Tolerance: the same 1e-11 relative bound as the Q^T parity tests
+(both paths do identical arithmetic up to the row splitting of V^T B)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1907_01891_gb300 import ctqr
+from paper_1907_01891_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.F32])
+def test_noalloc_apply_qt_matches_allocating_entry_point_twice(prec):
+    lib = ctqr.load()
+    m, n = 1500, 330
+    A = ctqr.to_colmajor(I.random_matrix(m, n, seed=101))
+    f = ctqr.qr_factor(A if prec == ctqr.Prec.F64 else A.to(torch.float32), prec=prec)
+    for call, k in enumerate((37, 64)):
+        B = I.random_matrix(m, k, seed=200 + call)
+        ref = ctqr.to_colmajor(B)
+        ctqr.apply_qt(f, ref)
+        got = ctqr.to_colmajor(B)
+        st = lib.ct_apply_qt_noalloc(f.handle, got.data_ptr(), m, k, torch.cuda.current_stream().cuda_stream)
+        assert st == ctqr.CT_OK
+        torch.cuda.synchronize()
+        r, g = ref.cpu().numpy(), got.cpu().numpy()
+        assert np.abs(g - r).max() <= 1e-11 * np.abs(r).max()
+
+
+def test_noalloc_apply_qt_rejects_more_columns_than_its_workspace():
+    lib = ctqr.load()
+    A = ctqr.to_colmajor(I.random_matrix(200, 50, seed=5))
+    f = ctqr.qr_factor(A)
+    B = ctqr.colmajor(200, 65, fill=0.0)
+    st = lib.ct_apply_qt_noalloc(f.handle, B.data_ptr(), 200, 65, torch.cuda.current_stream().cuda_stream)
+    assert st == ctqr.CT_ERR_INVALID
