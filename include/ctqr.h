@@ -137,6 +137,30 @@ typedef struct {
   double bytes;          /* summed algorithmic DRAM bytes of all launches        */
 } ct_kernel_stats;
 
+/* One system of a batch (ct_qr_solve_batched); all pointers are device
+ * pointers, column-major FP64. */
+typedef struct {
+  int64_t m, n;   /* rows and columns, m >= n >= 1                              */
+  double* A;      /* m x n, lda >= m: overwritten by its tile QR factorization  */
+  int64_t lda;
+  double* B;      /* m x k, ldb >= m: rows [0, n) receive X (NULL when k == 0)  */
+  int64_t ldb;
+  int64_t k;      /* right-hand sides (0: factor only)                          */
+} ct_batch_system;
+
+/* Options of ct_qr_solve_batched (NULL = defaults). */
+typedef struct {
+  int tile;       /* tile size 32 or 64; 0 = measured choice per size class,   */
+                  /* cached in $CTQR_TUNE_CACHE (else ~/.cache/ctqr_tune.json) */
+} ct_batch_opts;
+
+/* Optional report of ct_qr_solve_batched. */
+typedef struct {
+  int tile;       /* tile size used                                              */
+  double ms;      /* device time of the persistent launch                        */
+  int tasks;      /* tile tasks executed                                         */
+} ct_batch_report;
+
 /* Where the caller's B and X live for ct_reconstruct_scan. */
 typedef enum { CT_DEVICE_BUFFERS = 0, CT_HOST_BUFFERS = 1 } ct_buffers;
 
@@ -299,6 +323,21 @@ void ct_profile_reset(void);
 int ct_profile_kernels(ct_kernel_stats* out, int max_entries);
 /* Total kernel launches since the last reset. */
 uint64_t ct_kernel_launches(void);
+
+/* Factor and solve `count` independent least-squares systems of any sizes
+ * in one persistent launch: each A_s = Q_s R_s by the paper's algorithm-by-
+ * blocks (Sec. II-C-3: Compute_dense_QR, Apply_left_Qt_of_dense_QR,
+ * Compute_TD_QR and Apply_left_Qt_of_TD_QR on b x b tiles, Table
+ * tasks_qr_ab), then X_s = R_s^{-1}(Q_s^T B_s) by the solve tasks of Table
+ * tasks_solve_ab (the two Apply tasks on B, Trsm_lunn, Gemm_nn_mo).  The tasks
+ * of all systems share one device work queue consumed by one CTA per SM, with
+ * per-tile version counters ordering them (bounded waits); the launch is
+ * recorded and replayed as a CUDA graph.  FP64 throughout.  `systems` is a host
+ * array; A_s and B_s are overwritten.  Synchronous: returns when done, with
+ * CT_ERR_RANK / CT_ERR_NONFINITE / CT_ERR_TIMEOUT if any system hit one.
+ * Stack lambda*I under a rank-deficient A with ct_build_system. */
+ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const ct_batch_opts* opts,
+                              ct_batch_report* report, void* stream);
 
 /* Release a factor and its device memory (NULL is a no-op).  Waits for the
  * device to finish all queued work first, so a factor may be destroyed while

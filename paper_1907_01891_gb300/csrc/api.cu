@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <vector>
 
@@ -841,6 +842,60 @@ ct_status ct_gemm_status(void* stream) {
   CT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CT_CUDA_TRY(cudaStreamSynchronize(s));
   if (h != 0) CT_CUDA_TRY(cudaMemset(status, 0, sizeof(int)));
+  return (ct_status)h;
+}
+
+ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const ct_batch_opts* opts,
+                              ct_batch_report* report, void* stream) {
+  if (report) memset(report, 0, sizeof(*report));
+  if (count < 0 || (count > 0 && !systems)) return CT_ERR_INVALID;
+  if (count == 0) return CT_OK;
+  int64_t med_m = 0, med_n = 0;
+  std::vector<std::pair<int64_t, int64_t>> sizes;
+  for (int i = 0; i < count; ++i) {
+    const ct_batch_system& q = systems[i];
+    if (q.n < 1 || q.m < q.n || !q.A || q.lda < q.m || q.k < 0 || (q.k > 0 && (!q.B || q.ldb < q.m)))
+      return CT_ERR_INVALID;
+    sizes.push_back({q.n, q.m});
+  }
+  std::sort(sizes.begin(), sizes.end());
+  med_n = sizes[count / 2].first;
+  med_m = sizes[count / 2].second;
+  cudaStream_t s = as_stream(stream);
+  DeviceInfo di;
+  ct_status st = device_info(&di);
+  if (st != CT_OK) return st;
+  int tile = opts ? opts->tile : 0;
+  if (tile != 0 && tile != 32 && tile != 64) return CT_ERR_INVALID;
+  if (tile == 0 && (st = tuned_batch_tile(med_m, med_n, di.sms, s, &tile)) != CT_OK) return st;
+  int* status = nullptr;
+  CT_CUDA_TRY(cudaMallocAsync((void**)&status, sizeof(int), s));
+  struct F { int* p; cudaStream_t s; ~F() { cudaFreeAsync(p, s); } } fr{status, s};
+  CT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+  double ms = 0.0;
+  int ntasks = 0;
+  if ((st = run_batch(count, systems, tile, di.sms, status, s, &ms, &ntasks)) != CT_OK) return st;
+  // Rank test on every R (same threshold as ct_qr_factor).
+  for (int i = 0; i < count; ++i) {
+    ct_factor tmp;
+    tmp.m = systems[i].m;
+    tmp.n = systems[i].n;
+    tmp.ld = systems[i].lda;
+    tmp.store = CT_F64;
+    tmp.F = systems[i].A;
+    tmp.status = status;
+    if ((st = launch_rank_check(&tmp, s)) != CT_OK) { tmp.F = nullptr; tmp.status = nullptr; return st; }
+    tmp.F = nullptr;
+    tmp.status = nullptr;
+  }
+  int h = 0;
+  CT_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CT_CUDA_TRY(cudaStreamSynchronize(s));
+  if (report) {
+    report->tile = tile;
+    report->ms = ms;
+    report->tasks = ntasks;
+  }
   return (ct_status)h;
 }
 

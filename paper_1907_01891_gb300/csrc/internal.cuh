@@ -84,7 +84,7 @@ constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 // ---------------------------------------------------------------------------
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
-  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_COUNT
+  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_COUNT
 };
 
 // Graph capture: launches made between begin and end are recorded into
@@ -246,6 +246,14 @@ struct SparseSystem {
 ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, const float* Bh, const float* Bl,
                              int64_t ldb, int64_t M, int64_t N, int64_t K, float* C, int64_t ldc, bool split3,
                              int sms, int* status, cudaStream_t s);
+
+// ---- batched tile QR (tile_qr.cu) and its autotuner (autotune.cu) --------
+// Factor and solve `count` systems with the tile-task runtime, tile b = 32 or
+// 64; *ms_out receives the device time of the persistent launch.
+ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int* status, cudaStream_t s,
+                    double* ms_out, int* tasks_out = nullptr);
+// Tile size for systems of this shape: cached choice, or measured now.
+ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* tile);
 
 // ---- utilities (util.cu) ---------------------------------------------------
 ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,

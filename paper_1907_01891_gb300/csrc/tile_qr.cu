@@ -1,0 +1,746 @@
+// tile_qr.cu -- many independent least-squares systems of uneven size in one
+// persistent launch: the paper's algorithm-by-blocks (Sec. II-C-3) as a
+// GPU-resident task runtime.
+//
+// Every matrix is cut into b x b tiles.  The factorization is the task list
+// of Table (tasks_qr_ab), written right-looking:
+//   Compute_dense_QR(A_kk, S_kk)              GEQRT: QR of the diagonal tile
+//   Apply_left_Qt_of_dense_QR(A_kk, S_kk, A_kj)   UNMQR, j > k
+//   Compute_TD_QR(A_kk, A_ik, S_ik)           TSQRT: QR of [R_kk; A_ik], i > k
+//   Apply_left_Qt_of_TD_QR(A_ik, S_ik, A_kj, A_ij) TSMQR, i, j > k
+// and the solve is Table (tasks_solve_ab): the same two Apply tasks on the
+// tiles of B, then block back substitution with Trsm_lunn (B_i = R_ii^{-1} B_i)
+// and Gemm_nn_mo (B_i -= R_ij X_j).  S (the "S factor") is kept as the
+// compact-WY T of each tile's reflectors.
+//
+// The host builds the task list of all systems in a dependency-respecting
+// order; one cooperative launch of one CTA per SM then repeatedly takes the
+// next task index from a device counter, waits (bounded) until the tiles it
+// reads and writes have reached the versions the list requires, runs the task
+// on shared-memory copies of its tiles, and publishes new versions.  A task only
+// ever waits for tasks taken before it, all of which are held by running CTAs,
+// so the queue always progresses; tiles of different systems are independent,
+// so small and large systems interleave and keep every SM busy.  Everything is
+// FP64.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ctqr {
+namespace {
+
+enum TaskType { T_GEQRT = 0, T_UNMQR = 1, T_TSQRT = 2, T_TSMQR = 3, T_B_UNMQR = 4, T_B_TSMQR = 5,
+                T_TRSM = 6, T_GEMM = 7 };
+
+constexpr int kMaxDeps = 6;
+constexpr int kMaxIncs = 6;
+constexpr int kRtThreads = 256;
+// A task may wait for a whole chain of earlier tasks (up to a system's
+// critical path of tile tasks), so the bound is wider than a barrier's.
+constexpr uint64_t kTaskWaitLimitNs = 10000000000ull;
+
+struct TileTask {
+  int type, sys, i, j, k;
+  int nd, ni;
+  int dep_c[kMaxDeps];
+  int dep_v[kMaxDeps];
+  int inc_c[kMaxIncs];
+};
+
+struct SysDesc {
+  int64_t m, n, lda, ldb, k;
+  int mt, nt, kt;  // tile rows / columns of A, tile columns of B
+  double* A;
+  double* T;       // mt x nt blocks of b x b
+  double* B;
+};
+
+// ---------------------------------------------------------------- tile helpers
+// Tiles live in shared memory column-major with leading dimension LD = b + 1.
+template <int b>
+struct Tile {
+  static constexpr int LD = b + 1;
+};
+
+template <int b>
+__device__ void load_tile(double* s, const double* g, int64_t ld, int rows, int cols) {
+  for (int e = threadIdx.x; e < b * b; e += kRtThreads) {
+    const int r = e % b, c = e / b;
+    s[r + c * Tile<b>::LD] = (r < rows && c < cols) ? __ldcg(g + r + (int64_t)c * ld) : 0.0;
+  }
+}
+
+template <int b>
+__device__ void store_tile(const double* s, double* g, int64_t ld, int rows, int cols) {
+  for (int e = threadIdx.x; e < b * b; e += kRtThreads) {
+    const int r = e % b, c = e / b;
+    if (r < rows && c < cols) g[r + (int64_t)c * ld] = s[r + c * Tile<b>::LD];
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Thread t of the CTA owns the output block rows [r0, r0+R) x cols [c0, c0+R)
+// of a b x b product, R = b/16 (a 16 x 16 thread grid).
+template <int b>
+struct Blk {
+  static constexpr int R = b / 16;
+  int r0, c0;
+  __device__ Blk() : r0((threadIdx.x % 16) * R), c0((threadIdx.x / 16) * R) {}
+};
+
+// out = op(A) * X where op(A) = V^T (unit lower V, vmode 1), V (vmode 2),
+// full A^T (vmode 3), T^T (upper T, vmode 4), R (upper, vmode 5), A (vmode 0);
+// `kdim` limits the contraction.  Results in registers acc[R][R].
+template <int b>
+__device__ __forceinline__ double opA(const double* A, int r, int l, int vmode) {
+  constexpr int LD = Tile<b>::LD;
+  switch (vmode) {
+    case 1: return l > r ? A[l + r * LD] : (l == r ? 1.0 : 0.0);   // V^T(r, l) = V(l, r)
+    case 2: return r > l ? A[r + l * LD] : (r == l ? 1.0 : 0.0);   // V(r, l)
+    case 3: return A[l + r * LD];                                   // A^T(r, l)
+    case 4: return l <= r ? A[l + r * LD] : 0.0;                    // T^T(r, l) = T(l, r)
+    case 5: return l >= r ? A[r + l * LD] : 0.0;                    // R(r, l), upper
+    default: return A[r + l * LD];
+  }
+}
+
+template <int b>
+__device__ void mm(const double* A, int vmode, const double* X, double acc[b / 16][b / 16]) {
+  constexpr int LD = Tile<b>::LD, R = b / 16;
+  Blk<b> blk;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
+  for (int l = 0; l < b; ++l) {
+    double a[R], x[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = opA<b>(A, blk.r0 + i, l, vmode);
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[j] = X[l + (blk.c0 + j) * LD];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[i][j] += a[i] * x[j];
+  }
+}
+
+// dst (op) acc: mode 0 store, 1 subtract, 2 add.
+template <int b>
+__device__ void put(double* dst, const double acc[b / 16][b / 16], int mode) {
+  constexpr int LD = Tile<b>::LD, R = b / 16;
+  Blk<b> blk;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      double* p = dst + blk.r0 + i + (blk.c0 + j) * LD;
+      if (mode == 0) *p = acc[i][j];
+      else if (mode == 1) *p -= acc[i][j];
+      else *p += acc[i][j];
+    }
+}
+
+// Compact-WY T of the nr reflectors whose Gram products G(i, j) = v_i^T v_j
+// (i < j) are given by gram(i, j); T(i, i) = tau_i.  One warp builds column
+// j from the finished columns 0..j-1.
+template <int b, typename Gram>
+__device__ void build_t(double* T, const double* tau, int nr, Gram gram) {
+  constexpr int LD = Tile<b>::LD;
+  for (int e = threadIdx.x; e < b * b; e += kRtThreads) T[(e % b) + (e / b) * LD] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < nr; ++j) {
+    if (threadIdx.x < j) {
+      const int i = threadIdx.x;
+      double s = 0.0;
+      for (int l = i; l < j; ++l) s += T[i + l * LD] * gram(l, j);
+      T[i + j * LD] = -tau[j] * s;
+    }
+    if (threadIdx.x == 0) T[j + j * LD] = tau[j];
+    __syncthreads();
+  }
+}
+
+// Householder scalars for column with diagonal alpha and sub-diagonal norm^2
+// sigma (same convention as the blocked factorization).
+__device__ __forceinline__ void house(double alpha, double sigma, double& beta, double& tau, double& scale) {
+  beta = alpha;
+  tau = 0.0;
+  scale = 0.0;
+  if (sigma != 0.0) {
+    const double mu = sqrt(alpha * alpha + sigma);
+    beta = alpha >= 0.0 ? -mu : mu;
+    tau = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+}
+
+// ---------------------------------------------------------------- the tasks
+// GEQRT: A (rows x cols tile in smem) -> R above, V below, T.
+template <int b>
+__device__ void t_geqrt(double* A, double* T, double* sh, int rows, int cols, int* status) {
+  constexpr int LD = Tile<b>::LD;
+  double* tau = sh;          // [b]
+  double* w = sh + b;        // [b]
+  double* par = sh + 2 * b;  // beta, tau, scale
+  const int nr = rows < cols ? rows : cols;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < nr; ++c) {
+    if (warp == 0) {
+      double s = 0.0;
+      for (int r = c + 1 + lane; r < rows; r += 32) s += A[r + c * LD] * A[r + c * LD];
+      s = warp_sum_d(s);
+      if (lane == 0) {
+        double be, ta, sc;
+        if (!isfinite(s) || !isfinite(A[c + c * LD])) set_status(status, CT_ERR_NONFINITE);
+        house(A[c + c * LD], s, be, ta, sc);
+        par[0] = be; par[1] = ta; par[2] = sc;
+        tau[c] = ta;
+      }
+    }
+    __syncthreads();
+    const double ta = par[1], sc = par[2];
+    for (int r = c + 1 + (int)threadIdx.x; r < rows; r += kRtThreads) A[r + c * LD] *= sc;
+    __syncthreads();
+    // w_j = v^T A(:, j) for j > c (one warp per column)
+    for (int j = c + 1 + warp; j < cols; j += kRtThreads / 32) {
+      double s = lane == 0 ? A[c + j * LD] : 0.0;
+      for (int r = c + 1 + lane; r < rows; r += 32) s += A[r + c * LD] * A[r + j * LD];
+      s = warp_sum_d(s);
+      if (lane == 0) w[j] = ta * s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += kRtThreads) {
+      const int r = e % b, j = e / b;
+      if (j > c && j < cols && r >= c && r < rows) A[r + j * LD] -= w[j] * (r == c ? 1.0 : A[r + c * LD]);
+    }
+    if (threadIdx.x == 0) A[c + c * LD] = par[0];
+    __syncthreads();
+  }
+  build_t<b>(T, tau, nr, [&](int i, int j) {
+    double s = 0.0;  // v_i^T v_j, v unit lower
+    for (int r = j; r < rows; ++r) s += (r == i ? 1.0 : (r > i ? A[r + i * LD] : 0.0)) * (r == j ? 1.0 : A[r + j * LD]);
+    return s;
+  });
+}
+
+// UNMQR: C <- (I - V T V^T)^T C = C - V T^T (V^T C), V unit lower in Vt.
+template <int b>
+__device__ void t_unmqr(const double* Vt, const double* T, double* C, double* W) {
+  double acc[b / 16][b / 16];
+  mm<b>(Vt, 1, C, acc);  // V^T C
+  put<b>(W, acc, 0);
+  __syncthreads();
+  mm<b>(T, 4, W, acc);   // T^T W
+  __syncthreads();
+  put<b>(W, acc, 0);
+  __syncthreads();
+  mm<b>(Vt, 2, W, acc);  // V W
+  put<b>(C, acc, 1);
+  __syncthreads();
+}
+
+// TSQRT: QR of [R (upper, Rt); A] -> R updated, A holds V (lower block of the
+// reflectors, the top block is the identity), T.
+template <int b>
+__device__ void t_tsqrt(double* Rt, double* A, double* T, double* sh, int rowsA, int cols, int* status) {
+  constexpr int LD = Tile<b>::LD;
+  double* tau = sh;
+  double* w = sh + b;
+  double* par = sh + 2 * b;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < cols; ++c) {
+    if (warp == 0) {
+      double s = 0.0;
+      for (int r = lane; r < rowsA; r += 32) s += A[r + c * LD] * A[r + c * LD];
+      s = warp_sum_d(s);
+      if (lane == 0) {
+        double be, ta, sc;
+        if (!isfinite(s)) set_status(status, CT_ERR_NONFINITE);
+        house(Rt[c + c * LD], s, be, ta, sc);
+        par[0] = be; par[1] = ta; par[2] = sc;
+        tau[c] = ta;
+      }
+    }
+    __syncthreads();
+    const double ta = par[1], sc = par[2];
+    for (int r = threadIdx.x; r < rowsA; r += kRtThreads) A[r + c * LD] *= sc;
+    __syncthreads();
+    for (int j = c + 1 + warp; j < cols; j += kRtThreads / 32) {
+      double s = lane == 0 ? Rt[c + j * LD] : 0.0;
+      for (int r = lane; r < rowsA; r += 32) s += A[r + c * LD] * A[r + j * LD];
+      s = warp_sum_d(s);
+      if (lane == 0) w[j] = ta * s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += kRtThreads) {
+      const int r = e % b, j = e / b;
+      if (j > c && j < cols && r < rowsA) A[r + j * LD] -= w[j] * A[r + c * LD];
+    }
+    for (int j = c + 1 + (int)threadIdx.x; j < cols; j += kRtThreads) Rt[c + j * LD] -= w[j];
+    if (threadIdx.x == 0) Rt[c + c * LD] = par[0];
+    __syncthreads();
+  }
+  build_t<b>(T, tau, cols, [&](int i, int j) {
+    double s = 0.0;  // top blocks e_i, e_j are orthogonal: only the A parts
+    for (int r = 0; r < rowsA; ++r) s += A[r + i * LD] * A[r + j * LD];
+    return s;
+  });
+}
+
+// TSMQR: [C1; C2] <- Q^T [C1; C2] for the TS reflectors [I; V] with T:
+// W = C1 + V^T C2, W = T^T W, C1 -= W, C2 -= V W.
+template <int b>
+__device__ void t_tsmqr(const double* V, const double* T, double* C1, double* C2, double* W) {
+  double acc[b / 16][b / 16];
+  mm<b>(V, 3, C2, acc);  // V^T C2
+  {
+    constexpr int LD = Tile<b>::LD, R = b / 16;
+    Blk<b> blk;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[i][j] += C1[blk.r0 + i + (blk.c0 + j) * LD];
+  }
+  put<b>(W, acc, 0);
+  __syncthreads();
+  mm<b>(T, 4, W, acc);
+  __syncthreads();
+  put<b>(W, acc, 0);
+  __syncthreads();
+  put<b>(C1, acc, 1);
+  mm<b>(V, 0, W, acc);
+  put<b>(C2, acc, 1);
+  __syncthreads();
+}
+
+// TRSM: X = R^{-1} X (R upper in Rt, rows x rows valid), one warp per column.
+template <int b>
+__device__ void t_trsm(const double* Rt, double* X, int rows, int cols) {
+  constexpr int LD = Tile<b>::LD;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < cols; c += kRtThreads / 32) {
+    double* x = X + c * LD;
+    for (int i = rows - 1; i >= 0; --i) {
+      double xi = 0.0;
+      if (lane == 0) {
+        xi = x[i] / Rt[i + i * LD];
+        x[i] = xi;
+      }
+      xi = __shfl_sync(0xffffffffu, xi, 0);
+      for (int r = lane; r < i; r += 32) x[r] -= Rt[r + i * LD] * xi;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- runtime
+template <int b>
+__global__ void __launch_bounds__(kRtThreads, 1)
+    k_tile_runtime(const TileTask* __restrict__ tasks, int ntasks, const SysDesc* __restrict__ sys, int* cnt,
+                   int* next, int* status) {
+  constexpr int LD = Tile<b>::LD, TS = b * LD;
+  extern __shared__ double sm[];
+  double* t0 = sm;
+  double* t1 = t0 + TS;
+  double* t2 = t1 + TS;
+  double* t3 = t2 + TS;
+  double* t4 = t3 + TS;
+  double* sh = t4 + TS;  // 3b + 8 scalars
+  __shared__ int s_idx, s_ok;
+  __shared__ TileTask s_task;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_idx = atomicAdd(next, 1);
+      s_ok = 1;
+      if (s_idx < ntasks) {
+        s_task = tasks[s_idx];
+        const uint64_t start = globaltimer_ns();
+        for (int d = 0; d < s_task.nd && s_ok; ++d) {
+          const int* c = cnt + s_task.dep_c[d];
+          uint32_t spins = 0;
+          while (*(const volatile int*)c < s_task.dep_v[d]) {
+            if ((++spins & 63u) == 0) {
+              if (ld_volatile_i32(status) != 0) { s_ok = 0; break; }
+              if (globaltimer_ns() - start > kTaskWaitLimitNs) { set_status(status, CT_ERR_TIMEOUT); s_ok = 0; break; }
+            }
+            __nanosleep(64);
+          }
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_idx >= ntasks || !s_ok) break;
+    const TileTask t = s_task;
+    const SysDesc S = sys[t.sys];
+    const int64_t lda = S.lda, ldb = S.ldb;
+    auto tile_rows = [&](int i) { return (int)((S.m - (int64_t)i * b) < b ? (S.m - (int64_t)i * b) : b); };
+    auto tile_cols = [&](int j) { return (int)((S.n - (int64_t)j * b) < b ? (S.n - (int64_t)j * b) : b); };
+    auto bcols = [&](int jc) { return (int)((S.k - (int64_t)jc * b) < b ? (S.k - (int64_t)jc * b) : b); };
+    double* Ablk = S.A;
+    auto A_at = [&](int i, int j) { return Ablk + (int64_t)i * b + (int64_t)j * b * lda; };
+    auto B_at = [&](int i, int jc) { return S.B + (int64_t)i * b + (int64_t)jc * b * ldb; };
+    auto T_at = [&](int i, int k) { return S.T + ((int64_t)k * S.mt + i) * b * b; };
+    switch (t.type) {
+      case T_GEQRT: {
+        const int rows = tile_rows(t.k), cols = tile_cols(t.k);
+        load_tile<b>(t0, A_at(t.k, t.k), lda, rows, cols);
+        __syncthreads();
+        t_geqrt<b>(t0, t1, sh, rows, cols, status);
+        store_tile<b>(t0, A_at(t.k, t.k), lda, rows, cols);
+        store_tile<b>(t1, T_at(t.k, t.k), b, b, b);
+        break;
+      }
+      case T_UNMQR:
+      case T_B_UNMQR: {
+        const int rows = tile_rows(t.k), cols = tile_cols(t.k);
+        load_tile<b>(t0, A_at(t.k, t.k), lda, rows, cols);
+        load_tile<b>(t1, T_at(t.k, t.k), b, b, b);
+        const bool onB = t.type == T_B_UNMQR;
+        const int ccols = onB ? bcols(t.j) : tile_cols(t.j);
+        double* g = onB ? B_at(t.k, t.j) : A_at(t.k, t.j);
+        const int64_t ldg = onB ? ldb : lda;
+        load_tile<b>(t2, g, ldg, rows, ccols);
+        __syncthreads();
+        // V = unit lower part of the diagonal tile (cols beyond nr are zero)
+        t_unmqr<b>(t0, t1, t2, t3);
+        store_tile<b>(t2, g, ldg, rows, ccols);
+        break;
+      }
+      case T_TSQRT: {
+        const int cols = tile_cols(t.k), rowsA = tile_rows(t.i);
+        load_tile<b>(t0, A_at(t.k, t.k), lda, cols, cols);  // R_kk (upper part used)
+        load_tile<b>(t2, A_at(t.i, t.k), lda, rowsA, cols);
+        __syncthreads();
+        t_tsqrt<b>(t0, t2, t1, sh, rowsA, cols, status);
+        // write back only the upper triangle of R_kk (V_kk lives below it)
+        for (int e = threadIdx.x; e < b * b; e += kRtThreads) {
+          const int r = e % b, c = e / b;
+          if (r <= c && r < cols && c < cols) A_at(t.k, t.k)[r + (int64_t)c * lda] = t0[r + c * LD];
+        }
+        store_tile<b>(t2, A_at(t.i, t.k), lda, rowsA, cols);
+        store_tile<b>(t1, T_at(t.i, t.k), b, b, b);
+        break;
+      }
+      case T_TSMQR:
+      case T_B_TSMQR: {
+        const int rowsA = tile_rows(t.i), kcols = tile_cols(t.k);
+        load_tile<b>(t0, A_at(t.i, t.k), lda, rowsA, kcols);  // V (full)
+        load_tile<b>(t1, T_at(t.i, t.k), b, b, b);
+        const bool onB = t.type == T_B_TSMQR;
+        const int ccols = onB ? bcols(t.j) : tile_cols(t.j);
+        double* g1 = onB ? B_at(t.k, t.j) : A_at(t.k, t.j);
+        double* g2 = onB ? B_at(t.i, t.j) : A_at(t.i, t.j);
+        const int64_t ldg = onB ? ldb : lda;
+        load_tile<b>(t2, g1, ldg, tile_rows(t.k), ccols);
+        load_tile<b>(t3, g2, ldg, rowsA, ccols);
+        __syncthreads();
+        t_tsmqr<b>(t0, t1, t2, t3, t4);
+        store_tile<b>(t2, g1, ldg, tile_rows(t.k), ccols);
+        store_tile<b>(t3, g2, ldg, rowsA, ccols);
+        break;
+      }
+      case T_TRSM: {
+        const int rows = tile_cols(t.i);  // diagonal block of R is tile_cols x tile_cols
+        load_tile<b>(t0, A_at(t.i, t.i), lda, rows, rows);
+        load_tile<b>(t2, B_at(t.i, t.j), ldb, rows, bcols(t.j));
+        __syncthreads();
+        t_trsm<b>(t0, t2, rows, bcols(t.j));
+        store_tile<b>(t2, B_at(t.i, t.j), ldb, rows, bcols(t.j));
+        break;
+      }
+      case T_GEMM: {
+        // B_i -= R_{i,k} X_k  (R tile above the diagonal, t.k > t.i)
+        const int ri = tile_cols(t.i), rk = tile_cols(t.k), cc = bcols(t.j);
+        load_tile<b>(t0, A_at(t.i, t.k), lda, ri, rk);
+        load_tile<b>(t1, B_at(t.k, t.j), ldb, rk, cc);
+        load_tile<b>(t2, B_at(t.i, t.j), ldb, ri, cc);
+        __syncthreads();
+        double acc[b / 16][b / 16];
+        mm<b>(t0, 0, t1, acc);
+        put<b>(t2, acc, 1);
+        __syncthreads();
+        store_tile<b>(t2, B_at(t.i, t.j), ldb, ri, cc);
+        break;
+      }
+      default:
+        break;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < t.ni; ++q) atomicAdd(cnt + t.inc_c[q], 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- task list
+// Version counters: every tile part p has a write counter 2p and a read
+// counter 2p+1.  A task reading p waits for all writes issued before it; a task
+// writing p also waits for all reads issued before it (so nobody overwrites a
+// tile another task still has to read).
+struct DagBuilder {
+  std::vector<TileTask> tasks;
+  std::vector<int> writes, reads;  // issued so far, per part
+  int new_part() {
+    writes.push_back(0);
+    reads.push_back(0);
+    return (int)writes.size() - 1;
+  }
+  void add(int type, int sys, int i, int j, int k, std::initializer_list<int> rd, std::initializer_list<int> wr) {
+    TileTask t;
+    memset(&t, 0, sizeof(t));
+    t.type = type; t.sys = sys; t.i = i; t.j = j; t.k = k;
+    for (int p : rd) {
+      t.dep_c[t.nd] = 2 * p; t.dep_v[t.nd] = writes[p]; ++t.nd;
+      t.inc_c[t.ni++] = 2 * p + 1;
+      reads[p] += 1;
+    }
+    for (int p : wr) {
+      t.dep_c[t.nd] = 2 * p; t.dep_v[t.nd] = writes[p]; ++t.nd;
+      t.dep_c[t.nd] = 2 * p + 1; t.dep_v[t.nd] = reads[p]; ++t.nd;
+      t.inc_c[t.ni++] = 2 * p;
+      writes[p] += 1;
+    }
+    tasks.push_back(t);
+  }
+};
+
+struct SysParts {
+  int mt, nt, kt;
+  std::vector<int> lo, up, full, T, Bp;  // parts
+  int lo_at(int i, int j) const { return lo[(size_t)j * mt + i]; }
+};
+
+}  // namespace
+
+
+// Batched factor + solve.
+struct BatchPlan {
+  std::vector<SysDesc> sys;
+  std::vector<TileTask> tasks;
+  int parts = 0;
+};
+
+void plan_batch(int count, const ct_batch_system* in, int b, double* T_base, BatchPlan* plan) {
+  DagBuilder d;
+  std::vector<SysParts> P(count);
+  plan->sys.resize(count);
+  size_t toff = 0;
+  for (int s = 0; s < count; ++s) {
+    SysDesc& S = plan->sys[s];
+    S.m = in[s].m; S.n = in[s].n; S.lda = in[s].lda; S.ldb = in[s].ldb; S.k = in[s].k;
+    S.mt = (int)((S.m + b - 1) / b);
+    S.nt = (int)((S.n + b - 1) / b);
+    S.kt = (int)((S.k + b - 1) / b);
+    S.A = in[s].A;
+    S.B = in[s].B;
+    S.T = T_base + toff;
+    toff += (size_t)S.mt * S.nt * b * b;
+    SysParts& sp = P[s];
+    sp.mt = S.mt; sp.nt = S.nt; sp.kt = S.kt;
+    sp.lo.resize((size_t)S.mt * S.nt);
+    sp.up.resize(S.nt);
+    for (int j = 0; j < S.nt; ++j)
+      for (int i = 0; i < S.mt; ++i) sp.lo[(size_t)j * S.mt + i] = d.new_part();  // full tile, or lower part of a diagonal tile
+    for (int j = 0; j < S.nt; ++j) sp.up[j] = d.new_part();                   // upper part (R) of diagonal tiles
+    sp.T.resize((size_t)S.mt * S.nt);
+    for (size_t q = 0; q < sp.T.size(); ++q) sp.T[q] = d.new_part();
+    sp.Bp.resize((size_t)S.mt * (S.kt > 0 ? S.kt : 1));
+    for (size_t q = 0; q < sp.Bp.size(); ++q) sp.Bp[q] = d.new_part();
+  }
+  // Factorization tasks, systems interleaved step by step (largest first).
+  std::vector<int> order(count);
+  for (int s = 0; s < count; ++s) order[s] = s;
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return plan->sys[a].n * plan->sys[a].m > plan->sys[c].n * plan->sys[c].m; });
+  int kmax = 0;
+  for (int s = 0; s < count; ++s) kmax = std::max(kmax, std::min(plan->sys[s].mt, plan->sys[s].nt));
+  for (int k = 0; k < kmax; ++k) {
+    for (int s : order) {
+      const SysDesc& S = plan->sys[s];
+      const SysParts& sp = P[s];
+      if (k >= std::min(S.mt, S.nt)) continue;
+      auto full = [&](int i, int j) { return sp.lo_at(i, j); };
+      // the diagonal tile (k,k): its lower part (V) is `full(k,k)`, its upper part `up[k]`
+      d.add(T_GEQRT, s, k, k, k, {}, {full(k, k), sp.up[k], sp.T[(size_t)k * S.mt + k]});
+      for (int j = k + 1; j < S.nt; ++j)
+        d.add(T_UNMQR, s, k, j, k, {full(k, k), sp.T[(size_t)k * S.mt + k]}, {full(k, j)});
+      for (int i = k + 1; i < S.mt; ++i) {
+        d.add(T_TSQRT, s, i, k, k, {}, {sp.up[k], full(i, k), sp.T[(size_t)k * S.mt + i]});
+        for (int j = k + 1; j < S.nt; ++j)
+          d.add(T_TSMQR, s, i, j, k, {full(i, k), sp.T[(size_t)k * S.mt + i]}, {full(k, j), full(i, j)});
+      }
+    }
+  }
+  // Solve tasks: Q^T on B (Table tasks_solve_ab), then block back substitution.
+  for (int s : order) {
+    const SysDesc& S = plan->sys[s];
+    const SysParts& sp = P[s];
+    if (S.k <= 0) continue;
+    auto full = [&](int i, int j) { return sp.lo_at(i, j); };
+    auto Bp = [&](int i, int jc) { return sp.Bp[(size_t)jc * S.mt + i]; };
+    const int kd = std::min(S.mt, S.nt);
+    for (int jc = 0; jc < S.kt; ++jc)
+      for (int k = 0; k < kd; ++k) {
+        d.add(T_B_UNMQR, s, k, jc, k, {full(k, k), sp.T[(size_t)k * S.mt + k]}, {Bp(k, jc)});
+        for (int i = k + 1; i < S.mt; ++i)
+          d.add(T_B_TSMQR, s, i, jc, k, {full(i, k), sp.T[(size_t)k * S.mt + i]}, {Bp(k, jc), Bp(i, jc)});
+      }
+    for (int jc = 0; jc < S.kt; ++jc)
+      for (int i = S.nt - 1; i >= 0; --i) {
+        for (int kk = i + 1; kk < S.nt; ++kk)
+          d.add(T_GEMM, s, i, jc, kk, {full(i, kk), Bp(kk, jc)}, {Bp(i, jc)});
+        d.add(T_TRSM, s, i, jc, i, {sp.up[i]}, {Bp(i, jc)});
+      }
+  }
+  plan->tasks.swap(d.tasks);
+  plan->parts = (int)d.writes.size();
+}
+
+size_t batch_t_elems(int count, const ct_batch_system* in, int b) {
+  size_t e = 0;
+  for (int s = 0; s < count; ++s) e += (size_t)((in[s].m + b - 1) / b) * ((in[s].n + b - 1) / b) * b * b;
+  return e;
+}
+
+template <int b>
+size_t rt_smem() {
+  return (size_t)(5 * b * Tile<b>::LD + 3 * b + 8) * sizeof(double);
+}
+
+template <int b>
+ct_status run_batch_t(int count, const ct_batch_system* in, int sms, int* status, cudaStream_t s,
+                             double* ms_out, int* tasks_out) {
+  const size_t te = batch_t_elems(count, in, b);
+  double* T = nullptr;
+  CT_CUDA_TRY(cudaMallocAsync((void**)&T, te * sizeof(double) + 16, s));
+  BatchPlan plan;
+  plan_batch(count, in, b, T, &plan);
+  TileTask* dtasks = nullptr;
+  SysDesc* dsys = nullptr;
+  int* cnt = nullptr;
+  int* next = nullptr;
+  auto cleanup = [&]() {
+    if (T) cudaFreeAsync(T, s);
+    if (dtasks) cudaFreeAsync(dtasks, s);
+    if (dsys) cudaFreeAsync(dsys, s);
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (next) cudaFreeAsync(next, s);
+  };
+  const size_t nt = plan.tasks.size();
+  if (cudaMallocAsync((void**)&dtasks, nt * sizeof(TileTask) + 16, s) != cudaSuccess ||
+      cudaMallocAsync((void**)&dsys, count * sizeof(SysDesc) + 16, s) != cudaSuccess ||
+      cudaMallocAsync((void**)&cnt, (size_t)2 * plan.parts * sizeof(int) + 16, s) != cudaSuccess ||
+      cudaMallocAsync((void**)&next, 16, s) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return CT_ERR_NOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(dtasks, plan.tasks.data(), nt * sizeof(TileTask), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dsys, plan.sys.data(), count * sizeof(SysDesc), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host buffers must outlive the copies
+  if (e != cudaSuccess) { cleanup(); return CT_ERR_CUDA; }
+  const size_t smem = rt_smem<b>();
+  e = cudaFuncSetAttribute(k_tile_runtime<b>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_runtime<b>, kRtThreads, smem);
+  if (e != cudaSuccess || per_sm < 1) { cudaGetLastError(); cleanup(); return CT_ERR_UNSUPPORTED; }
+  const int grid = sms * per_sm;
+  int ntasks = (int)nt;
+  // One graph: reset the queue and the version counters, then the persistent
+  // cooperative launch.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs = nullptr;
+  ct_status st = CT_OK;
+  do {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { st = CT_ERR_CUDA; break; }
+    if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evs, cudaEventDisableTiming) != cudaSuccess) { st = CT_ERR_CUDA; break; }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kRtThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = cs;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    bool graphed = false;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      cudaMemsetAsync(cnt, 0, (size_t)2 * plan.parts * sizeof(int), cs);
+      cudaMemsetAsync(next, 0, sizeof(int), cs);
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_tile_runtime<b>, (const TileTask*)dtasks, ntasks,
+                                          (const SysDesc*)dsys, cnt, next, status);
+      cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      graphed = le == cudaSuccess && ce == cudaSuccess && graph &&
+                cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+      cudaGetLastError();
+    }
+    // order: caller stream -> graph -> caller stream
+    cudaEventRecord(evs, s);
+    cudaStreamWaitEvent(cs, evs, 0);
+    cudaEventRecord(ev0, cs);
+    {
+      LaunchScope ls(K_TILE_RT, cs, 0.0, 0.0);
+      if (graphed) {
+        if (cudaGraphLaunch(exec, cs) != cudaSuccess) { cudaGetLastError(); st = CT_ERR_CUDA; break; }
+      } else {
+        // the graph could not be recorded: the same two resets and launch, directly
+        if (cudaMemsetAsync(cnt, 0, (size_t)2 * plan.parts * sizeof(int), cs) != cudaSuccess ||
+            cudaMemsetAsync(next, 0, sizeof(int), cs) != cudaSuccess ||
+            cudaLaunchKernelEx(&cfg, k_tile_runtime<b>, (const TileTask*)dtasks, ntasks, (const SysDesc*)dsys, cnt,
+                               next, status) != cudaSuccess) {
+          cudaGetLastError();
+          st = CT_ERR_CUDA;
+          break;
+        }
+      }
+    }
+    cudaEventRecord(ev1, cs);
+    cudaEventRecord(evs, cs);
+    cudaStreamWaitEvent(s, evs, 0);
+    if (cudaEventSynchronize(ev1) != cudaSuccess) { st = CT_ERR_CUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    if (ms_out) *ms_out = ms;
+    if (tasks_out) *tasks_out = ntasks;
+  } while (0);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (evs) cudaEventDestroy(evs);
+  if (cs) cudaStreamDestroy(cs);
+  cleanup();
+  return st;
+}
+
+
+ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int* status, cudaStream_t s,
+                    double* ms_out, int* tasks_out) {
+  if (tile == 32) return run_batch_t<32>(count, in, sms, status, s, ms_out, tasks_out);
+  if (tile == 64) return run_batch_t<64>(count, in, sms, status, s, ms_out, tasks_out);
+  return CT_ERR_INVALID;
+}
+
+}  // namespace ctqr

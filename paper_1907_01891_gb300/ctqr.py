@@ -70,6 +70,19 @@ class KernelStats(ctypes.Structure):
 CT_DEVICE_BUFFERS, CT_HOST_BUFFERS = 0, 1
 
 
+class BatchSystem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("k", ctypes.c_int64)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int)]
+
+
+class BatchReport(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("ms", ctypes.c_double), ("tasks", ctypes.c_int)]
+
+
 _lib = None
 
 # Every entry point of include/ctqr.h, with its ctypes signature.
@@ -96,6 +109,8 @@ SIGNATURES = {
                              ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
     "ct_gemm_tf32_tn": ([_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _I, _I, _VP], _I),
     "ct_gemm_status": ([_VP], _I),
+    "ct_qr_solve_batched": ([_I, ctypes.POINTER(BatchSystem), ctypes.POINTER(BatchOpts),
+                             ctypes.POINTER(BatchReport), _VP], _I),
     "ct_profile_enable": ([_I], None),
     "ct_profile_reset": ([], None),
     "ct_profile_kernels": ([ctypes.POINTER(KernelStats), _I], _I),
@@ -372,6 +387,22 @@ def gemm_tf32_tn(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None
 
 def gemm_status() -> int:
     return load().ct_gemm_status(_stream())
+
+
+def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True):
+    """Factor and solve a batch of systems in place (lists of column-major
+    FP64 CUDA tensors; Bs entries may be None).  Rows [0, n) of every B hold X
+    afterwards.  Returns (status, BatchReport)."""
+    arr = (BatchSystem * len(As))()
+    for q, (A, B) in enumerate(zip(As, Bs)):
+        m, n = A.shape
+        arr[q] = BatchSystem(m, n, A.data_ptr(), _ld(A), B.data_ptr() if B is not None else None,
+                             _ld(B) if B is not None else m, B.shape[1] if B is not None else 0)
+    rep = BatchReport()
+    st = load().ct_qr_solve_batched(len(As), arr, ctypes.byref(BatchOpts(tile)), ctypes.byref(rep), _stream())
+    if check:
+        _check(st, "ct_qr_solve_batched")
+    return st, rep
 
 
 def profile_enable(on: bool = True) -> None:

@@ -1,0 +1,82 @@
+"""Batched factor + solve of uneven systems (ct_qr_solve_batched): the paper's
+algorithm-by-blocks (tile QR and the tile solve) in one persistent launch,
+against the oracle.  x is unique under full rank and must match the oracle's
+least-squares solution to 1e-10 relative; R is unique up to the sign of each
+row, so |R| is compared (1e-10 relative to max |R|)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1907_01891_gb300 import ctqr
+from paper_1907_01891_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(130, 70, 2), (300, 200, 1), (97, 97, 3), (520, 333, 5), (64, 64, 1), (1000, 257, 17), (65, 33, 0)]
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+def test_batched_uneven_random_systems_match_oracle(tile):
+    As, Bs, ref = [], [], []
+    for q, (m, n, k) in enumerate(SHAPES):
+        A = I.random_matrix(m, n, seed=300 + q)
+        B = I.random_matrix(m, k, seed=400 + q) if k else None
+        As.append(ctqr.to_colmajor(A))
+        Bs.append(ctqr.to_colmajor(B) if k else None)
+        ref.append((A, B))
+    st, rep = ctqr.qr_solve_batched(As, Bs, tile=tile)
+    assert rep.tile == tile and rep.tasks > 0
+    torch.cuda.synchronize()
+    for (A, B), At, Bt, (m, n, k) in zip(ref, As, Bs, SHAPES):
+        Fo, tau = O.qr(A)
+        R, Ro = np.triu(At.cpu().numpy()[:n]), np.triu(Fo[:n])
+        assert np.abs(np.abs(R) - np.abs(Ro)).max() <= 1e-10 * np.abs(Ro).max(), (m, n)
+        if k:
+            X = Bt.cpu().numpy()[:n]
+            Xo = O.lstsq(A, B)
+            assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10, (m, n)
+
+
+def test_batched_lambda_stacked_ct_systems_match_oracle():
+    """Config-4b style: [A_s; 1e-3 I] for uneven fan/parallel geometries."""
+    lam = 1e-3
+    geoms = [I.parallel_geometry(16, 18, 23), I.fan_geometry(20, 24, 29), I.parallel_geometry(12, 11, 17),
+             I.fan_geometry(24, 30, 35)]
+    As, Bs, ref = [], [], []
+    for q, g in enumerate(geoms):
+        A = ctqr.build_system(g, torch.float64, lam=lam)
+        Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+        Asys = np.vstack([Ao, lam * np.eye(g.n)])
+        b = np.vstack([Ao @ I.phantoms(g, [q + 1, q + 2]), np.zeros((g.n, 2))])
+        As.append(A)
+        Bs.append(ctqr.to_colmajor(b))
+        ref.append((Asys, b))
+    ctqr.qr_solve_batched(As, Bs, tile=32)
+    torch.cuda.synchronize()
+    for (Asys, b), Bt, g in zip(ref, Bs, geoms):
+        X = Bt.cpu().numpy()[:g.n]
+        Xo = O.lstsq(Asys, b)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10
+
+
+def test_batched_autotune_caches_its_choice(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("CTQR_TUNE_CACHE", str(cache))
+    As = [ctqr.to_colmajor(I.random_matrix(400, 150, seed=9)), ctqr.to_colmajor(I.random_matrix(380, 140, seed=10))]
+    Bs = [ctqr.to_colmajor(I.random_matrix(400, 2, seed=11)), ctqr.to_colmajor(I.random_matrix(380, 2, seed=12))]
+    st, rep = ctqr.qr_solve_batched(As, Bs, tile=0)
+    assert rep.tile in (32, 64)
+    data = json.loads(cache.read_text())
+    assert any(k.startswith("tile_qr/") and v == rep.tile for k, v in data.items())
+
+
+def test_batched_reports_rank_deficiency():
+    A = I.random_matrix(90, 40, seed=3)
+    A[:, 17] = 0.0
+    st, rep = ctqr.qr_solve_batched([ctqr.to_colmajor(A)], [ctqr.to_colmajor(np.ones((90, 1)))], tile=32,
+                                    check=False)
+    assert st == ctqr.CT_ERR_RANK
