@@ -344,6 +344,89 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
  * kernels that use it are still in flight. */
 void ct_factor_destroy(ct_factor* f);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate.  The paper has no learned part: it reconstructs every
+ * slice as the least-squares solution X = R^{-1} (Q^T B)[0:n] of Eq. (qr1) with
+ * the factor of Eq. (QR).  These entry points add a small convolutional
+ * network that maps the backprojection g = A^T b of one sinogram (A built as
+ * in Sec. II-A) to an image estimate x_hat, and a gate that accepts x_hat only
+ * when its FP64 data residual ||A x_hat - b|| / ||b|| is at most a tolerance;
+ * every slice that fails is solved through a QR factor instead, so the output
+ * is the QR solution wherever the network is not good enough.
+ *
+ * Network (images nx x ny, pixel j = iy * nx + ix as in the columns of A;
+ * 3x3 kernels, stride 1, zero padding 1; C = 32 channels, 6 layers):
+ *   a1 = relu(conv1(in_scale * g))             1 -> C
+ *   a_l = a_{l-1} + relu(conv_l(a_{l-1}))      l = 2..5, C -> C
+ *   x_hat = out_scale * conv6(a5)              C -> 1
+ * Weights and activations are stored in BF16, products accumulate in FP32.
+ * Parameters are one FP32 vector; layer l holds its weights [out][in][3][3]
+ * followed by its out biases, layers in order (ct_surrogate_num_params
+ * gives the length).  Training minimises the mean over pixels and images of
+ * (y - x / out_scale)^2, y the network output, with Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8) on the FP32 parameters; the BF16 copy is refreshed after
+ * each step.  All images are FP64, column-major n x k with ld = n.
+ * Errors: CT_ERR_INVALID for bad sizes or NULL pointers; CT_ERR_NOMEM when an
+ * activation buffer cannot be allocated; CT_ERR_CUDA otherwise.
+ * ------------------------------------------------------------------------ */
+typedef struct ct_surrogate ct_surrogate;
+
+typedef struct {
+  double in_scale;   /* network input = in_scale * A^T b                     */
+  double out_scale;  /* x_hat = out_scale * network output                  */
+  uint64_t seed;     /* seeds the uniform initialisation of the weights     */
+} ct_surrogate_opts;
+
+typedef struct {
+  int64_t slices;        /* k                                                 */
+  int64_t fallbacks;     /* slices that failed the gate                       */
+  double max_residual;   /* largest gate residual among the accepted slices   */
+  double ms_total;       /* host wall time of the call                        */
+  double ms_network;     /* device time: backprojection + network             */
+  double ms_gate;        /* device time: FP64 residuals and compaction        */
+  double ms_fallback;    /* device time: QR solve of the failing slices       */
+} ct_surrogate_report;
+
+/* Create a network for the geometry g (fan or parallel beam, Sec. II-A); the
+ * exact FP64 sparse A of g is built once and kept for backprojections and
+ * gates.  *out receives the handle (free with ct_surrogate_destroy). */
+ct_status ct_surrogate_init(const ct_geometry* g, const ct_surrogate_opts* opts, ct_surrogate** out);
+int64_t ct_surrogate_num_params(const ct_surrogate* s);
+/* Copy the FP32 parameters to host (set = 0) or from host (set != 0). */
+ct_status ct_surrogate_params(ct_surrogate* s, float* host, int set);
+/* G = A^T B for k sinograms B (device FP64, m rays x k, ldb >= m); G is
+ * device FP64 n x k with ld = n. */
+ct_status ct_surrogate_backproject(ct_surrogate* s, const double* B, int64_t ldb, int64_t k, double* G,
+                                   void* stream);
+/* B = A X for k images X (device FP64 n x k, ld = n): the sinograms of
+ * Eq. (sistema) computed with the exact sparse A; B device FP64, ldb >= m. */
+ct_status ct_surrogate_project(ct_surrogate* s, const double* X, int64_t k, double* B, int64_t ldb,
+                               void* stream);
+/* One Adam step on a batch: inputs G (backprojections) and targets X, both
+ * device FP64 n x batch.  *loss (may be NULL) receives the batch loss before
+ * the step. */
+ct_status ct_surrogate_train_step(ct_surrogate* s, const double* G, const double* X, int64_t batch, float lr,
+                                  double* loss, void* stream);
+/* Loss and gradient (host FP32, ct_surrogate_num_params entries, may be
+ * NULL) of a batch, without changing the parameters. */
+ct_status ct_surrogate_grad(ct_surrogate* s, const double* G, const double* X, int64_t batch, double* loss,
+                            float* grad_host, void* stream);
+/* x_hat for backprojections G (device FP64 n x k): the network alone. */
+ct_status ct_surrogate_forward(ct_surrogate* s, const double* G, double* Xhat, int64_t k, void* stream);
+/* Gated reconstruction of k sinograms B (device FP64, ldb >= m rays): X
+ * (device FP64, ldx >= n) receives x_hat for the slices whose FP64 residual
+ * ||A x_hat - b|| / ||b|| <= tol (||A x_hat|| when b = 0), and for the others
+ * the solution through the factor f of A (or of [A; lambda I] with
+ * ropts->lambda > 0; refined when f is a mixed-precision factor, as
+ * ct_reconstruct_scan does).  f may be NULL: failing slices then keep x_hat.
+ * resid (device, k doubles, may be NULL) receives every slice's gate
+ * residual (NaN or Inf fail the gate).  Returns the fallback solve's status
+ * when it fails. */
+ct_status ct_surrogate_infer(ct_surrogate* s, const double* B, int64_t ldb, double* X, int64_t ldx, int64_t k,
+                             double tol, const ct_factor* f, const ct_refine_opts* ropts, double* resid,
+                             ct_surrogate_report* report, void* stream);
+void ct_surrogate_destroy(ct_surrogate* s);
+
 #ifdef __cplusplus
 }
 #endif

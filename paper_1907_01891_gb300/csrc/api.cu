@@ -726,6 +726,17 @@ static ct_status reconstruct_impl(const ct_factor* f, const void* A, ct_dtype A_
   return st;
 }
 
+}  // extern "C"
+
+namespace ctqr {
+ct_status reconstruct_with(const ct_factor* f, const SparseSystem* sp, const double* B, int64_t ldb, double* X,
+                           int64_t ldx, int64_t k, const ct_refine_opts* ropts, ct_report* report, cudaStream_t s) {
+  return reconstruct_impl(f, nullptr, CT_F64, 0, sp, B, ldb, X, ldx, k, ropts, report, (void*)s);
+}
+}  // namespace ctqr
+
+extern "C" {
+
 ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec prec,
                               const double* B, int64_t ldb, double* X, int64_t ldx, int64_t k,
                               ct_buffers where, const ct_refine_opts* ropts, ct_report* report,

@@ -84,7 +84,7 @@ constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 // ---------------------------------------------------------------------------
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
-  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_COUNT
+  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_COUNT
 };
 
 // Graph capture: launches made between begin and end are recorded into
@@ -254,6 +254,14 @@ ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int
                     double* ms_out, int* tasks_out = nullptr);
 // Tile size for systems of this shape: cached choice, or measured now.
 ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* tile);
+
+// ---- solve through a factor (api.cu) ---------------------------------------
+// X = solution of the system f factors for the right-hand sides B (f->m rows):
+// the plain FP64 apply + back-solve when sp is NULL, else FP64-residual
+// refinement with the exact sparse A (rays only; ropts->lambda adds the
+// implicit lambda*I rows).
+ct_status reconstruct_with(const ct_factor* f, const SparseSystem* sp, const double* B, int64_t ldb, double* X,
+                           int64_t ldx, int64_t k, const ct_refine_opts* ropts, ct_report* report, cudaStream_t s);
 
 // ---- utilities (util.cu) ---------------------------------------------------
 ct_status launch_copy_matrix(const void* src, ct_dtype st, int64_t lds, void* dst, ct_dtype dt,

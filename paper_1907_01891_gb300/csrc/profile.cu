@@ -67,7 +67,8 @@ Profiler& prof() {
 const char* kNames[K_COUNT] = {"zero_fill",   "system_matrix", "panel_qr",  "reflector_vtc",
                                "reflector_tw", "block_update",  "trsm_diag", "copy",
                                "rank_check",  "col_norms",     "col_add",   "gemm_tn",
-                               "col_axpy",    "tc_gemm",       "spmm",      "tile_runtime"};
+                               "col_axpy",    "tc_gemm",       "spmm",      "tile_runtime",
+                               "conv",        "gate"};
 
 }  // namespace
 

@@ -83,6 +83,16 @@ class BatchReport(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("ms", ctypes.c_double), ("tasks", ctypes.c_int)]
 
 
+class SurrogateOpts(ctypes.Structure):
+    _fields_ = [("in_scale", ctypes.c_double), ("out_scale", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class SurrogateReport(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("max_residual", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_network", ctypes.c_double), ("ms_gate", ctypes.c_double),
+                ("ms_fallback", ctypes.c_double)]
+
+
 _lib = None
 
 # Every entry point of include/ctqr.h, with its ctypes signature.
@@ -111,6 +121,17 @@ SIGNATURES = {
     "ct_gemm_status": ([_VP], _I),
     "ct_qr_solve_batched": ([_I, ctypes.POINTER(BatchSystem), ctypes.POINTER(BatchOpts),
                              ctypes.POINTER(BatchReport), _VP], _I),
+    "ct_surrogate_init": ([ctypes.POINTER(Geometry), ctypes.POINTER(SurrogateOpts), ctypes.POINTER(_VP)], _I),
+    "ct_surrogate_num_params": ([_VP], _I64),
+    "ct_surrogate_params": ([_VP, _VP, _I], _I),
+    "ct_surrogate_backproject": ([_VP, _VP, _I64, _I64, _VP, _VP], _I),
+    "ct_surrogate_project": ([_VP, _VP, _I64, _VP, _I64, _VP], _I),
+    "ct_surrogate_train_step": ([_VP, _VP, _VP, _I64, ctypes.c_float, ctypes.POINTER(_D), _VP], _I),
+    "ct_surrogate_grad": ([_VP, _VP, _VP, _I64, ctypes.POINTER(_D), _VP, _VP], _I),
+    "ct_surrogate_forward": ([_VP, _VP, _VP, _I64, _VP], _I),
+    "ct_surrogate_infer": ([_VP, _VP, _I64, _VP, _I64, _I64, _D, _VP, ctypes.POINTER(RefineOpts), _VP,
+                            ctypes.POINTER(SurrogateReport), _VP], _I),
+    "ct_surrogate_destroy": ([_VP], None),
     "ct_profile_enable": ([_I], None),
     "ct_profile_reset": ([], None),
     "ct_profile_kernels": ([ctypes.POINTER(KernelStats), _I], _I),
@@ -403,6 +424,95 @@ def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True):
     if check:
         _check(st, "ct_qr_solve_batched")
     return st, rep
+
+
+class Surrogate:
+    """The convolutional surrogate of ``include/ctqr.h`` (ct_surrogate_*):
+    images are FP64 CUDA tensors of n x k, column-major with ld = n (one
+    image per column, pixel iy * nx + ix)."""
+
+    def __init__(self, geom, in_scale: float = 1.0, out_scale: float = 1.0, seed: int = 0):
+        h = ctypes.c_void_p()
+        opts = SurrogateOpts(in_scale, out_scale, seed)
+        _check(load().ct_surrogate_init(ctypes.byref(geometry(geom)), ctypes.byref(opts), ctypes.byref(h)),
+               "ct_surrogate_init")
+        self.handle = h.value
+        self.m, self.n = system_size(geom)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ct_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def num_params(self) -> int:
+        return int(load().ct_surrogate_num_params(self.handle))
+
+    def get_params(self):
+        import numpy as np
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        _check(load().ct_surrogate_params(self.handle, out.ctypes.data, 0), "ct_surrogate_params")
+        return out
+
+    def set_params(self, p) -> None:
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params()
+        _check(load().ct_surrogate_params(self.handle, p.ctypes.data, 1), "ct_surrogate_params")
+
+    def backproject(self, B: torch.Tensor, G: torch.Tensor | None = None) -> torch.Tensor:
+        k = B.shape[1]
+        if G is None:
+            G = colmajor(self.n, k, ld=self.n)
+        _check(load().ct_surrogate_backproject(self.handle, B.data_ptr(), _ld(B), k, G.data_ptr(), _stream()),
+               "ct_surrogate_backproject")
+        return G
+
+    def project(self, X: torch.Tensor, B: torch.Tensor | None = None) -> torch.Tensor:
+        k = X.shape[1]
+        if B is None:
+            B = colmajor(self.m, k, ld=self.m)
+        _check(load().ct_surrogate_project(self.handle, X.data_ptr(), k, B.data_ptr(), _ld(B), _stream()),
+               "ct_surrogate_project")
+        return B
+
+    def train_step(self, G: torch.Tensor, X: torch.Tensor, lr: float) -> float:
+        loss = ctypes.c_double()
+        _check(load().ct_surrogate_train_step(self.handle, G.data_ptr(), X.data_ptr(), G.shape[1], lr,
+                                              ctypes.byref(loss), _stream()), "ct_surrogate_train_step")
+        return loss.value
+
+    def grad(self, G: torch.Tensor, X: torch.Tensor):
+        import numpy as np
+        loss = ctypes.c_double()
+        g = np.zeros(self.num_params(), dtype=np.float32)
+        _check(load().ct_surrogate_grad(self.handle, G.data_ptr(), X.data_ptr(), G.shape[1], ctypes.byref(loss),
+                                        g.ctypes.data, _stream()), "ct_surrogate_grad")
+        return loss.value, g
+
+    def forward(self, G: torch.Tensor) -> torch.Tensor:
+        k = G.shape[1]
+        X = colmajor(self.n, k, ld=self.n)
+        _check(load().ct_surrogate_forward(self.handle, G.data_ptr(), X.data_ptr(), k, _stream()),
+               "ct_surrogate_forward")
+        return X
+
+    def infer(self, B: torch.Tensor, tol: float = 1e-3, factor: "Factor | None" = None, lam: float = 0.0,
+              max_iter: int = 0, X: torch.Tensor | None = None, check: bool = True):
+        """Gated reconstruction.  Returns (X, per-slice residuals, report dict)."""
+        k = B.shape[1]
+        if X is None:
+            X = colmajor(self.n, k, ld=self.n)
+        resid = torch.empty(max(k, 1), dtype=torch.float64, device=B.device)
+        ro = RefineOpts(max_iter, lam, 0.0, REFINE_AUTO)
+        rep = SurrogateReport()
+        st = load().ct_surrogate_infer(self.handle, B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), k, tol,
+                                       factor.handle if factor is not None else None, ctypes.byref(ro),
+                                       resid.data_ptr(), ctypes.byref(rep), _stream())
+        if check:
+            _check(st, "ct_surrogate_infer")
+        return X, resid[:k], dict(status=st, slices=rep.slices, fallbacks=rep.fallbacks,
+                                  max_residual=rep.max_residual, ms_total=rep.ms_total,
+                                  ms_network=rep.ms_network, ms_gate=rep.ms_gate, ms_fallback=rep.ms_fallback)
 
 
 def profile_enable(on: bool = True) -> None:

@@ -90,6 +90,11 @@ CONFIG3 = dict(name="fan256_192x363_k64_lam1e-3", geom=fan_geometry(256, 192, 36
                seeds=list(range(200, 264)), n_ellipses=5, noise_i0=None, lam=1e-3)
 CONFIG4A = dict(name="parallel32_60x45_k512", geom=parallel_geometry(32, 60, 45),
                 seeds=list(range(1000, 1512)), n_ellipses=5, noise_i0=1e4, lam=0.0)
+# Learned surrogate on the 128 x 128 fan-beam scan (noiseless b = A x):
+# training phantoms 20000 seeds, inference batch 256 on unseen seeds.
+CONFIG5 = dict(name="fan128_surrogate_train20000_k256", geom=fan_geometry(128, 128, 181),
+               train_seeds=range(10_000, 30_000), seeds=list(range(50_000, 50_256)), n_ellipses=5,
+               noise_i0=None, lam=0.0, tol=1e-3)
 
 
 def ellipse_phantom(nx: int, ny: int, pixel: float, seed: int, n_ellipses: int = 5) -> np.ndarray:
