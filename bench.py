@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 from paper_1907_01891_gb300 import inputs as I  # noqa: E402
 
 METRIC = "slices/s & QR TFLOP/s: mixed-prec+refine vs FP64 QR, 1 GB300, rel err ≤1e-10"
-WORKLOADS = {"fan128": I.CONFIG2, "fan256": I.CONFIG3, "parallel32": I.CONFIG1}
+WORKLOADS = {"fan128": I.CONFIG2, "fan256": I.CONFIG3, "parallel32": I.CONFIG1, "batch64": I.CONFIG4B}
 PREC = {"f64": 0, "f32": 1, "tf32": 2}
 DTYPE_NAME = {"f64": "f64", "f32": "f32+f64", "tf32": "tf32+f64"}
 
@@ -182,6 +182,8 @@ def main():
     args = parse()
     world, rank, local = dist_setup(args)
     cfg = WORKLOADS[args.workload]
+    if args.workload == "batch64":
+        return main_batch(args, world, rank, local, cfg)
     if args.fp64_check is None:
         args.fp64_check = 0 if args.workload == "fan256" else 1
     g = cfg["geom"]
@@ -357,6 +359,181 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, cores, desc = oracle_sample(cfg, k, args.cpu_seconds)
         line["cpu_baseline"] = {"value": k / t_cpu, "unit": "slices/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- batched workload
+def batch_inputs(cfg):
+    """Geometries, phantoms and systems of the uneven batch (host side)."""
+    geoms = I.uneven_systems(cfg["count"], cfg["seed"])
+    X = [I.phantoms(g, [cfg["seed0"] + q]) for q, g in enumerate(geoms)]
+    return geoms, X
+
+
+def oracle_batch_sample(cfg, budget_s: float):
+    """The oracle's QR + solve of the smallest system of the batch (measured),
+    scaled by flops to the whole batch.  Returns (seconds, cores, description)."""
+    from oracle import oracle as O
+    geoms, X = batch_inputs(cfg)
+    lam = cfg["lam"]
+    q = min(range(len(geoms)), key=lambda i: geoms[i].m * geoms[i].n)
+    g = geoms[q]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    A = O.system_matrix(O.Geometry(*g.as_tuple()))
+    Asys = np.vstack([A, lam * np.eye(g.n)])
+    b = np.vstack([A @ X[q], np.zeros((g.n, 1))])
+    O.lstsq(Asys, b)
+    dt = time.perf_counter() - t0
+    total = sum(qr_flops(x.m + x.n, x.n) + solve_flops(x.m + x.n, x.n, 1) for x in geoms)
+    mine = qr_flops(g.m + g.n, g.n) + solve_flops(g.m + g.n, g.n, 1)
+    desc = (f"oracle system matrix + unblocked Householder QR + solve of the smallest system "
+            f"({g.m + g.n}x{g.n}, measured {dt:.1f} s), flop-scaled to the {len(geoms)} systems")
+    return dt * total / mine, cores, desc
+
+
+def main_batch(args, world, rank, local, cfg):
+    """64 uneven [A; lambda I] systems factored and solved in one persistent
+    graph-captured launch per step (ct_qr_solve_batched); value = systems/s."""
+    count, lam = cfg["count"], cfg["lam"]
+    metric = "systems/s & QR TFLOP/s: 64 uneven [A; 1e-3 I] systems, one persistent launch, 1 GB300"
+    geoms, Xtrue = batch_inputs(cfg)
+    flops = sum(qr_flops(g.m + g.n, g.n) + solve_flops(g.m + g.n, g.n, 1) for g in geoms)
+    wl = f"{cfg['name']} ({count} systems {min(g.m + g.n for g in geoms)}..{max(g.m + g.n for g in geoms)} rows)"
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        t, cores, desc = oracle_batch_sample(cfg, args.cpu_seconds)
+        value = count / t
+        print(json.dumps({"metric": metric, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic: seeded ellipse phantoms, noiseless", "impl": "reference",
+                          "config": {"workload": wl, "parallelism": "host cores"},
+                          "cpu_baseline": {"value": value, "unit": "systems/s", "cores": cores, "kind": "oracle",
+                                           "sample": desc},
+                          "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1907_01891_gb300 import ctqr
+    ctqr.load()
+    A0, B0, As, Bs = [], [], [], []
+    for g, x in zip(geoms, Xtrue):
+        A = ctqr.build_system(g, torch.float64, lam=lam)
+        b = ctqr.colmajor(g.m + g.n, 1, fill=0.0)
+        b[:g.m].copy_(A[:g.m] @ torch.as_tensor(x, device=dev))
+        A0.append(A)
+        B0.append(b)
+        As.append(ctqr.colmajor(g.m + g.n, g.n))
+        Bs.append(ctqr.colmajor(g.m + g.n, 1))
+    torch.cuda.synchronize()
+
+    def step():
+        for A, Aw, b, bw in zip(A0, As, B0, Bs):
+            Aw.copy_(A)
+            bw.copy_(b)
+        return ctqr.qr_solve_batched(As, Bs, tile=0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # accuracy: least-squares optimality of every system (a property at any size)
+    worst = 0.0
+    for g, A, b, bw in zip(geoms, A0, B0, Bs):
+        x = bw[:g.n]
+        r = b - A @ x
+        worst = max(worst, float(torch.linalg.norm(A.t() @ r) / (torch.linalg.norm(A) ** 2 * torch.linalg.norm(x))))
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    ctqr.profile_reset()
+    ctqr.profile_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    reps = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        reps.append(step()[1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ctqr.profile_enable(False)
+    kstats = ctqr.profile_kernels()
+    ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    value = world * count * args.steps / (ms / 1e3)
+    ms_kernel = statistics.median(r.ms for r in reps)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    fp64_peak = 152 * 2 * 2 * sm_max_ghz * 1e9 / 1e12
+    achieved = flops / (ms_kernel / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": None, "kernel": "tile_runtime",
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x %.2f GHz" % sm_max_ghz,
+            "note": "algorithmic flops of Householder QR + Q^T + back-solve per system (2mn^2 - 2n^3/3 + ...)",
+            "share_of_step": ms_kernel * args.steps / ms}
+    # end to end: systems and right-hand sides from pinned host memory, X back
+    Ah = [torch.empty((g.n, g.m + g.n), dtype=torch.float64).pin_memory().t() for g in geoms]
+    for h, A in zip(Ah, A0):
+        h.copy_(A)
+    Bh = [torch.empty((1, g.m + g.n), dtype=torch.float64).pin_memory().t() for g in geoms]
+    for h, b in zip(Bh, B0):
+        h.copy_(b)
+    Xh = [torch.empty((1, g.n), dtype=torch.float64).pin_memory().t() for g in geoms]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for h, Aw, hb, bw in zip(Ah, As, Bh, Bs):
+            Aw.copy_(h, non_blocking=True)
+            bw.copy_(hb, non_blocking=True)
+        ctqr.qr_solve_batched(As, Bs, tile=0)
+        for xh, bw, g in zip(Xh, Bs, geoms):
+            xh.copy_(bw[:g.n], non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = {"value": world * count * args.e2e_steps / t_e2e, "unit": "systems/s",
+               "h2d_bytes_per_step": sum((g.m + g.n) * (g.n + 1) * 8 for g in geoms),
+               "d2h_bytes_per_step": sum(g.n * 8 for g in geoms)}
+    line = {"metric": metric, "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded ellipse phantoms, noiseless b = Ax",
+            "config": {"workload": wl, "tile": reps[-1].tile, "tasks": reps[-1].tasks,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (%.1f GB of FP64 systems)" % (
+                           sum((g.m + g.n) * g.n * 8 for g in geoms) / 1e9)},
+            "qr_tflops": achieved, "kernel_ms": ms_kernel, "normal_eq_residual_max": worst,
+            "roofline": roof, "e2e": e2e, "clocks": clk,
+            "gpu_launches": sum(s["launches"] for s in kstats),
+            "kernels": {s["name"]: {"launches": s["launches"], "ms": round(s["ms"], 3)}
+                        for s in kstats if s["launches"]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_cpu, cores, desc = oracle_batch_sample(cfg, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": count / t_cpu, "unit": "systems/s", "cores": cores, "kind": "oracle",
                                 "sample": desc}
     if rank == 0:
         print(json.dumps(line))

@@ -878,7 +878,11 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
   if (st != CT_OK) return st;
   int tile = opts ? opts->tile : 0;
   if (tile != 0 && tile != 32 && tile != 64) return CT_ERR_INVALID;
+  // Large batches take the larger tile without measuring: the task list of
+  // 32-wide tiles would exceed 2^25 tasks (~3.4 GB).
+  if (tile == 0 && batch_task_count(count, systems, 32) > (int64_t(1) << 25)) tile = 64;
   if (tile == 0 && (st = tuned_batch_tile(med_m, med_n, di.sms, s, &tile)) != CT_OK) return st;
+  if (batch_task_count(count, systems, tile) > INT32_MAX) return CT_ERR_UNSUPPORTED;
   int* status = nullptr;
   CT_CUDA_TRY(cudaMallocAsync((void**)&status, sizeof(int), s));
   struct F { int* p; cudaStream_t s; ~F() { cudaFreeAsync(p, s); } } fr{status, s};

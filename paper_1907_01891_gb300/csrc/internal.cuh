@@ -252,6 +252,9 @@ ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, cons
 // 64; *ms_out receives the device time of the persistent launch.
 ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int* status, cudaStream_t s,
                     double* ms_out, int* tasks_out = nullptr);
+// Tile tasks the batch would hold with tile size b (each task is ~100 bytes
+// of host and device memory).
+int64_t batch_task_count(int count, const ct_batch_system* in, int b);
 // Tile size for systems of this shape: cached choice, or measured now.
 ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* tile);
 

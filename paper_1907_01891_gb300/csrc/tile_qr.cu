@@ -157,10 +157,10 @@ __device__ void put(double* dst, const double acc[b / 16][b / 16], int mode) {
 }
 
 // Compact-WY T of the nr reflectors whose Gram products G(i, j) = v_i^T v_j
-// (i < j) are given by gram(i, j); T(i, i) = tau_i.  One warp builds column
-// j from the finished columns 0..j-1.
-template <int b, typename Gram>
-__device__ void build_t(double* T, const double* tau, int nr, Gram gram) {
+// (i < j) are G(i, j), precomputed in shared memory; T(i, i) = tau_i.  Column j
+// is built from the finished columns 0..j-1.
+template <int b>
+__device__ void build_t(double* T, const double* tau, int nr, const double* G) {
   constexpr int LD = Tile<b>::LD;
   for (int e = threadIdx.x; e < b * b; e += kRtThreads) T[(e % b) + (e / b) * LD] = 0.0;
   __syncthreads();
@@ -168,7 +168,7 @@ __device__ void build_t(double* T, const double* tau, int nr, Gram gram) {
     if (threadIdx.x < j) {
       const int i = threadIdx.x;
       double s = 0.0;
-      for (int l = i; l < j; ++l) s += T[i + l * LD] * gram(l, j);
+      for (int l = i; l < j; ++l) s += T[i + l * LD] * G[l + j * LD];
       T[i + j * LD] = -tau[j] * s;
     }
     if (threadIdx.x == 0) T[j + j * LD] = tau[j];
@@ -193,7 +193,7 @@ __device__ __forceinline__ void house(double alpha, double sigma, double& beta, 
 // ---------------------------------------------------------------- the tasks
 // GEQRT: A (rows x cols tile in smem) -> R above, V below, T.
 template <int b>
-__device__ void t_geqrt(double* A, double* T, double* sh, int rows, int cols, int* status) {
+__device__ void t_geqrt(double* A, double* T, double* G, double* sh, int rows, int cols, int* status) {
   constexpr int LD = Tile<b>::LD;
   double* tau = sh;          // [b]
   double* w = sh + b;        // [b]
@@ -232,11 +232,16 @@ __device__ void t_geqrt(double* A, double* T, double* sh, int rows, int cols, in
     if (threadIdx.x == 0) A[c + c * LD] = par[0];
     __syncthreads();
   }
-  build_t<b>(T, tau, nr, [&](int i, int j) {
-    double s = 0.0;  // v_i^T v_j, v unit lower
-    for (int r = j; r < rows; ++r) s += (r == i ? 1.0 : (r > i ? A[r + i * LD] : 0.0)) * (r == j ? 1.0 : A[r + j * LD]);
-    return s;
-  });
+  // G(i, j) = v_i^T v_j for i < j, v unit lower: v_i(j) = A(j, i), v_j(j) = 1
+  for (int e = threadIdx.x; e < nr * nr; e += kRtThreads) {
+    const int i = e % nr, j = e / nr;
+    if (i >= j) continue;
+    double s = A[j + i * LD];
+    for (int r = j + 1; r < rows; ++r) s += A[r + i * LD] * A[r + j * LD];
+    G[i + j * LD] = s;
+  }
+  __syncthreads();
+  build_t<b>(T, tau, nr, G);
 }
 
 // UNMQR: C <- (I - V T V^T)^T C = C - V T^T (V^T C), V unit lower in Vt.
@@ -258,7 +263,8 @@ __device__ void t_unmqr(const double* Vt, const double* T, double* C, double* W)
 // TSQRT: QR of [R (upper, Rt); A] -> R updated, A holds V (lower block of the
 // reflectors, the top block is the identity), T.
 template <int b>
-__device__ void t_tsqrt(double* Rt, double* A, double* T, double* sh, int rowsA, int cols, int* status) {
+__device__ void t_tsqrt(double* Rt, double* A, double* T, double* G, double* sh, int rowsA, int cols,
+                        int* status) {
   constexpr int LD = Tile<b>::LD;
   double* tau = sh;
   double* w = sh + b;
@@ -296,11 +302,17 @@ __device__ void t_tsqrt(double* Rt, double* A, double* T, double* sh, int rowsA,
     if (threadIdx.x == 0) Rt[c + c * LD] = par[0];
     __syncthreads();
   }
-  build_t<b>(T, tau, cols, [&](int i, int j) {
-    double s = 0.0;  // top blocks e_i, e_j are orthogonal: only the A parts
+  // G(i, j) = v_i^T v_j for i < j: the identity top blocks are orthogonal,
+  // only the A parts contribute
+  for (int e = threadIdx.x; e < cols * cols; e += kRtThreads) {
+    const int i = e % cols, j = e / cols;
+    if (i >= j) continue;
+    double s = 0.0;
     for (int r = 0; r < rowsA; ++r) s += A[r + i * LD] * A[r + j * LD];
-    return s;
-  });
+    G[i + j * LD] = s;
+  }
+  __syncthreads();
+  build_t<b>(T, tau, cols, G);
 }
 
 // TSMQR: [C1; C2] <- Q^T [C1; C2] for the TS reflectors [I; V] with T:
@@ -403,7 +415,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
         const int rows = tile_rows(t.k), cols = tile_cols(t.k);
         load_tile<b>(t0, A_at(t.k, t.k), lda, rows, cols);
         __syncthreads();
-        t_geqrt<b>(t0, t1, sh, rows, cols, status);
+        t_geqrt<b>(t0, t1, t3, sh, rows, cols, status);
         store_tile<b>(t0, A_at(t.k, t.k), lda, rows, cols);
         store_tile<b>(t1, T_at(t.k, t.k), b, b, b);
         break;
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
         load_tile<b>(t0, A_at(t.k, t.k), lda, cols, cols);  // R_kk (upper part used)
         load_tile<b>(t2, A_at(t.i, t.k), lda, rowsA, cols);
         __syncthreads();
-        t_tsqrt<b>(t0, t2, t1, sh, rowsA, cols, status);
+        t_tsqrt<b>(t0, t2, t1, t3, sh, rowsA, cols, status);
         // write back only the upper triangle of R_kk (V_kk lives below it)
         for (int e = threadIdx.x; e < b * b; e += kRtThreads) {
           const int r = e % b, c = e / b;
@@ -498,28 +510,65 @@ __global__ void __launch_bounds__(kRtThreads, 1)
 // tile another task still has to read).
 struct DagBuilder {
   std::vector<TileTask> tasks;
-  std::vector<int> writes, reads;  // issued so far, per part
+  std::vector<int> start;            // earliest start of each task (see below)
+  std::vector<int> writes, reads;    // issued so far, per part
+  std::vector<int> wdone, rdone;     // latest finish of a write / read of each part
   int new_part() {
     writes.push_back(0);
     reads.push_back(0);
+    wdone.push_back(0);
+    rdone.push_back(0);
     return (int)writes.size() - 1;
+  }
+  // Relative duration of each task type, for the earliest-start estimate.
+  static int cost(int type) {
+    switch (type) {
+      case T_GEQRT: return 2;
+      case T_TSQRT: return 3;
+      case T_UNMQR: case T_B_UNMQR: return 2;
+      case T_TSMQR: case T_B_TSMQR: return 3;
+      default: return 1;
+    }
   }
   void add(int type, int sys, int i, int j, int k, std::initializer_list<int> rd, std::initializer_list<int> wr) {
     TileTask t;
     memset(&t, 0, sizeof(t));
     t.type = type; t.sys = sys; t.i = i; t.j = j; t.k = k;
+    int st = 0;
     for (int p : rd) {
       t.dep_c[t.nd] = 2 * p; t.dep_v[t.nd] = writes[p]; ++t.nd;
       t.inc_c[t.ni++] = 2 * p + 1;
       reads[p] += 1;
+      st = std::max(st, wdone[p]);
     }
     for (int p : wr) {
       t.dep_c[t.nd] = 2 * p; t.dep_v[t.nd] = writes[p]; ++t.nd;
       t.dep_c[t.nd] = 2 * p + 1; t.dep_v[t.nd] = reads[p]; ++t.nd;
       t.inc_c[t.ni++] = 2 * p;
       writes[p] += 1;
+      st = std::max(st, std::max(wdone[p], rdone[p]));
     }
+    const int fin = st + cost(type);
+    for (int p : rd) rdone[p] = std::max(rdone[p], fin);
+    for (int p : wr) wdone[p] = fin;
     tasks.push_back(t);
+    start.push_back(st);
+  }
+  // Reorder the tasks by earliest start (stable counting sort).  Every task
+  // starts after all tasks it depends on finish, so the order stays
+  // topological, and the cumulative version counts remain valid: the writes
+  // (reads) of a part that precede a task in the new order are exactly those
+  // that preceded it when the counts were taken.
+  void order_by_start() {
+    int smax = 0;
+    for (int v : start) smax = std::max(smax, v);
+    std::vector<size_t> pos((size_t)smax + 2, 0);
+    for (int v : start) pos[(size_t)v + 1] += 1;
+    for (size_t q = 1; q < pos.size(); ++q) pos[q] += pos[q - 1];
+    std::vector<TileTask> out(tasks.size());
+    for (size_t q = 0; q < tasks.size(); ++q) out[pos[start[q]]++] = tasks[q];
+    tasks.swap(out);
+    std::vector<int>().swap(start);
   }
 };
 
@@ -610,8 +659,22 @@ void plan_batch(int count, const ct_batch_system* in, int b, double* T_base, Bat
         d.add(T_TRSM, s, i, jc, i, {sp.up[i]}, {Bp(i, jc)});
       }
   }
+  d.order_by_start();
   plan->tasks.swap(d.tasks);
   plan->parts = (int)d.writes.size();
+}
+
+// Number of tile tasks plan_batch emits for this batch and tile size.
+int64_t batch_task_count(int count, const ct_batch_system* in, int b) {
+  int64_t total = 0;
+  for (int s = 0; s < count; ++s) {
+    const int64_t mt = (in[s].m + b - 1) / b, nt = (in[s].n + b - 1) / b, kt = (in[s].k + b - 1) / b;
+    const int64_t kd = std::min(mt, nt);
+    for (int64_t k = 0; k < kd; ++k) total += 1 + (nt - k - 1) + (mt - k - 1) * (nt - k);
+    for (int64_t k = 0; k < kd; ++k) total += kt * (mt - k);
+    total += kt * nt * (nt + 1) / 2;
+  }
+  return total;
 }
 
 size_t batch_t_elems(int count, const ct_batch_system* in, int b) {

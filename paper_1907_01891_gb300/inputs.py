@@ -90,11 +90,30 @@ CONFIG3 = dict(name="fan256_192x363_k64_lam1e-3", geom=fan_geometry(256, 192, 36
                seeds=list(range(200, 264)), n_ellipses=5, noise_i0=None, lam=1e-3)
 CONFIG4A = dict(name="parallel32_60x45_k512", geom=parallel_geometry(32, 60, 45),
                 seeds=list(range(1000, 1512)), n_ellipses=5, noise_i0=1e4, lam=0.0)
+# 64 uneven lambda-stacked systems (geometries from uneven_systems(64, 4242)),
+# one noiseless phantom each (seed 2000 + system index).
+CONFIG4B = dict(name="fan_uneven32-96_x64_lam1e-3", count=64, seed=4242, seed0=2000, n_ellipses=5,
+                lam=1e-3)
 # Learned surrogate on the 128 x 128 fan-beam scan (noiseless b = A x):
 # training phantoms 20000 seeds, inference batch 256 on unseen seeds.
 CONFIG5 = dict(name="fan128_surrogate_train20000_k256", geom=fan_geometry(128, 128, 181),
                train_seeds=range(10_000, 30_000), seeds=list(range(50_000, 50_256)), n_ellipses=5,
                noise_i0=None, lam=0.0, tol=1e-3)
+
+
+def uneven_systems(count: int = 64, seed: int = 4242, npix_range=(32, 96), ratio_range=(1.2, 2.0)):
+    """Seeded fan-beam geometries of uneven size: image side uniform in
+    npix_range, rays per pixel uniform in ratio_range (detector bins ~1.42 x the
+    side, rounded to odd; views = rays / bins)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        npix = int(rng.integers(npix_range[0], npix_range[1] + 1))
+        ratio = float(rng.uniform(*ratio_range))
+        bins = int(math.ceil(1.42 * npix)) | 1
+        views = max(2, int(round(ratio * npix * npix / bins)))
+        out.append(fan_geometry(npix, views, bins))
+    return out
 
 
 def ellipse_phantom(nx: int, ny: int, pixel: float, seed: int, n_ellipses: int = 5) -> np.ndarray:

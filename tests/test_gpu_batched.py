@@ -80,3 +80,27 @@ def test_batched_reports_rank_deficiency():
     st, rep = ctqr.qr_solve_batched([ctqr.to_colmajor(A)], [ctqr.to_colmajor(np.ones((90, 1)))], tile=32,
                                     check=False)
     assert st == ctqr.CT_ERR_RANK
+
+
+def test_uneven_lambda_stacked_batch_smallest_systems_match_oracle():
+    """The four smallest systems of the 64-system uneven batch (fan beam,
+    images 32^2-96^2, [A; 1e-3 I]) in one launch with the tuned tile, against
+    the oracle's least-squares solution."""
+    cfg = I.CONFIG4B
+    geoms = I.uneven_systems(cfg["count"], cfg["seed"])
+    idx = sorted(range(len(geoms)), key=lambda q: geoms[q].m * geoms[q].n)[:4]
+    lam = cfg["lam"]
+    As, Bs, ref = [], [], []
+    for q in idx:
+        g = geoms[q]
+        Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+        b = np.vstack([Ao @ I.phantoms(g, [cfg["seed0"] + q]), np.zeros((g.n, 1))])
+        As.append(ctqr.build_system(g, torch.float64, lam=lam))
+        Bs.append(ctqr.to_colmajor(b))
+        ref.append((np.vstack([Ao, lam * np.eye(g.n)]), b, g))
+    st, rep = ctqr.qr_solve_batched(As, Bs, tile=0)
+    torch.cuda.synchronize()
+    for (Asys, b, g), Bt in zip(ref, Bs):
+        X = Bt.cpu().numpy()[:g.n]
+        Xo = O.lstsq(Asys, b)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10, (g.nx, g.m)
