@@ -91,35 +91,56 @@ __global__ void __launch_bounds__(kGT) k_vtc(const TV* __restrict__ V, int64_t l
   }
 }
 
-// W'(a, c) = sum_{b <= a} T(b, a) * sum_s P_s(b, c); 32 columns per CTA.
+// W'(a, c) = sum_{b <= a} T(b, a) * sum_s P_s(b, c); one CTA per column c.
+// Warp w sums the splits w, w + 8, w + 16, ... (lane l: rows l and l + 32),
+// then the eight warp sums are added in order: a fixed order, so the result
+// is bitwise reproducible, with many loads in flight per thread.
 template <typename Acc>
 __global__ void __launch_bounds__(kGT) k_tw(const double* __restrict__ part, int splits,
                                             int64_t nc, const double* __restrict__ T, int ldt,
                                             int nbp, double* __restrict__ W) {
-  __shared__ Acc Ts[kBM][kBM + 1];
-  __shared__ Acc Ss[32][kBM + 1];
-  const int tid = threadIdx.x;
-  const int64_t c0 = (int64_t)blockIdx.x * 32;
-  for (int e = tid; e < kBM * kBM; e += kGT) {
-    const int b = e % kBM, a = e / kBM;  // T(b, a)
-    Ts[a][b] = (b < nbp && a < nbp && b <= a) ? (Acc)T[b + a * ldt] : (Acc)0;
+  constexpr int NW = kGT / 32;
+  __shared__ double red[NW][kBM];
+  __shared__ double sv[kBM];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c = blockIdx.x;
+  const double* base = part + (size_t)c * kBM;
+  const size_t stride = (size_t)kBM * nc;
+  double s0 = 0.0, s1 = 0.0;
+  int sp = warp;
+  for (; sp + 3 * NW < splits; sp += 4 * NW) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[2 * u] = __ldcg(base + (size_t)(sp + u * NW) * stride + lane);
+      v[2 * u + 1] = __ldcg(base + (size_t)(sp + u * NW) * stride + lane + 32);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s0 += v[2 * u];
+      s1 += v[2 * u + 1];
+    }
   }
-  for (int e = tid; e < 32 * kBM; e += kGT) {
-    const int b = e % kBM, c = e / kBM;
-    const int64_t cg = c0 + c;
-    double s = 0.0;
-    if (cg < nc)
-      for (int sp = 0; sp < splits; ++sp) s += part[(size_t)sp * kBM * nc + b + cg * kBM];
-    Ss[c][b] = (Acc)s;
+  for (; sp < splits; sp += NW) {
+    s0 += __ldcg(base + (size_t)sp * stride + lane);
+    s1 += __ldcg(base + (size_t)sp * stride + lane + 32);
+  }
+  red[warp][lane] = s0;
+  red[warp][lane + 32] = s1;
+  __syncthreads();
+  if (tid < kBM) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t += red[w][tid];
+    sv[tid] = t;
   }
   __syncthreads();
-  for (int e = tid; e < 32 * kBM; e += kGT) {
-    const int a = e % kBM, c = e / kBM;
-    const int64_t cg = c0 + c;
-    if (cg >= nc) continue;
-    Acc s = (Acc)0;
-    for (int b = 0; b <= a && b < nbp; ++b) s += Ts[a][b] * Ss[c][b];
-    W[a + cg * kBM] = (double)s;
+  if (tid < kBM) {
+    const int a = tid;
+    Acc t = (Acc)0;
+    if (a < nbp)
+      for (int b = 0; b <= a; ++b) t += (Acc)T[b + a * ldt] * (Acc)sv[b];
+    W[a + c * kBM] = (double)t;
   }
 }
 
@@ -335,7 +356,7 @@ ct_status run_reflector(const ReflectorArgs& a, double* work, size_t work_elems,
   }
   {
     LaunchScope ls(K_TW, s, (double)a.nbp * a.nbp * a.nc, (double)(splits + 1) * kBM * a.nc * 8);
-    k_tw<Acc><<<(unsigned)((a.nc + 31) / 32), kGT, 0, s>>>(part, (int)splits, a.nc, a.T, a.ldt, a.nbp, W);
+    k_tw<Acc><<<(unsigned)a.nc, kGT, 0, s>>>(part, (int)splits, a.nc, a.T, a.ldt, a.nbp, W);
   }
   {
     LaunchScope ls(K_UPDATE, s, 2.0 * mnk,

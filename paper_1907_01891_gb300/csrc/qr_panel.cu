@@ -25,6 +25,7 @@
 // V^T V; the last CTA to finish sums the shares and builds T column by column:
 //   T_ii = tau_i,  T[0:i, i] = -tau_i T[0:i, 0:i] (V^T V)[0:i, i].
 #include <math.h>
+#include <stdlib.h>
 
 #include "internal.cuh"
 
@@ -56,17 +57,22 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Householder factorization of the panel whose rows this CTA holds in `slab`
+// (column-major, rp rows per column, already loaded), write-back of V / R in
+// the storage type, tau, and T by the last CTA to finish.  `small` holds the
+// reduction buffers (kSmallDoubles doubles plus kMaxNb Mth values);
+// `smem` is the start of the CTA's shared memory, reused for T at the end.
 // S: storage type of the matrix; Mth: arithmetic of the panel's dot products
 // and rank-1 updates (double for the FP64 factorization; float for the
 // mixed-precision one, where sigma, alpha, beta, tau and T stay FP64).
+constexpr int kSmallDoubles = 2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb;
+
 template <typename S, typename Mth>
-__global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
-  extern __shared__ double smem[];
-  double* red = smem;                               // [2*kMaxNb] reduced values
+__device__ void panel_householder(const PanelArgs& a, Mth* slab, double* small, double* smem) {
+  double* red = small;                              // [2*kMaxNb] reduced values
   double* wvd = red + 2 * kMaxNb;                   // [kMaxNb]  w_c
   double* scratch = wvd + kMaxNb;                   // [kNW][2*kMaxNb]
   Mth* wvm = (Mth*)(scratch + kNW * 2 * kMaxNb);    // [kMaxNb] w_c in the panel arithmetic
-  Mth* slab = wvm + kMaxNb;                         // [nbp][rp], column-major
   __shared__ int s_last;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -75,11 +81,6 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   int64_t nr64 = a.mr - rb;
   const int nr = nr64 <= 0 ? 0 : (nr64 < rp ? (int)nr64 : rp);
   S* P = (S*)a.P;
-
-  for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < nr; r += kPT) slab[(size_t)c * rp + r] = (Mth)P[rb + r + c * a.ld];
-  __syncthreads();
-
   for (int k = 0; k < nbp; ++k) {
     const int ne = nbp - k;                          // columns k..nbp-1
     const bool owner = (k >= rb) && (k < rb + nr);   // holds the diagonal row k
@@ -231,6 +232,262 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   }
 }
 
+
+template <typename S, typename Mth>
+__global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
+  extern __shared__ double smem[];
+  double* small = smem;
+  Mth* slab = (Mth*)(small + kSmallDoubles) + kMaxNb;  // after the kMaxNb Mth values of w
+  const int tid = threadIdx.x;
+  const int64_t rb = (int64_t)blockIdx.x * a.rp;
+  const int64_t nr64 = a.mr - rb;
+  const int nr = nr64 <= 0 ? 0 : (nr64 < a.rp ? (int)nr64 : a.rp);
+  const S* P = (const S*)a.P;
+  for (int c = 0; c < a.nbp; ++c)
+    for (int r = tid; r < nr; r += kPT) slab[(size_t)c * a.rp + r] = (Mth)P[rb + r + c * a.ld];
+  __syncthreads();
+  panel_householder<S, Mth>(a, slab, small, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky-QR panel with Householder reconstruction (FP32-stored factors).
+//
+// The per-column Householder panel above needs one grid barrier per column.
+// For a full-rank, reasonably conditioned panel P (mr x nbp) the same
+// Householder factorization can be reached with two:
+//   1. G = P^T P (FP64; every CTA its rows, then a split reduction) and its
+//      Cholesky factor G = R1^T R1, so Q = P R1^{-1} has orthonormal columns;
+//   2. the "modified LU" of Ballard et al. (Reconstructing Householder vectors
+//      from tall-skinny QR, 2015): Q - [S; 0] = L U without pivoting, the sign
+//      s_i = -sign of the current diagonal entry, so every pivot has modulus
+//      >= 1.  Then V = L (unit lower trapezoidal), T = -U S L1^{-T} (upper),
+//      I - V T V^T has Q S as its first nbp columns and the panel's R is S R1.
+// Only the top nbp rows of Q are formed explicitly (every CTA does the small
+// nbp x nbp algebra redundantly, in the same order, so all agree bitwise); the
+// rows below are V2 = Q2 U^{-1} = P2 M^{-1} with M = U R1, one triangular
+// solve per row.  tau_i = T_ii and V^T V are those of the equivalent sequence
+// of reflectors, so the 128-column outer update's S = T^{-1} form applies
+// unchanged.  When the Cholesky factor breaks down or kappa_1(R1) exceeds
+// kCqrMaxCond (so Q would be orthonormal only to kappa^2 u), every CTA falls
+// back to the per-column Householder path on the same resident slab.
+constexpr double kCqrMaxCond = 3.0e3;
+constexpr int kGramStride = kMaxNb * (kMaxNb + 1) / 2;  // doubles per CTA partial Gram
+
+__device__ __forceinline__ void tri_index(int e, int& i, int& j) {
+  // e = j (j + 1) / 2 + i, 0 <= i <= j
+  int jj = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (jj * (jj + 1) / 2 > e) --jj;
+  while ((jj + 1) * (jj + 2) / 2 <= e) ++jj;
+  j = jj;
+  i = e - jj * (jj + 1) / 2;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
+  extern __shared__ double smem[];
+  const int nbp = a.nbp, rp = a.rp, tid = threadIdx.x;
+  const int nn = nbp * nbp;
+  double* slab = smem;                        // [nbp][rp] this CTA's rows
+  double* G = slab + (size_t)nbp * rp;        // Gram, then R1 in its upper part
+  double* Ri = G + nn;                        // R1^{-1} (upper)
+  double* W = Ri + nn;                        // P1, then Q1 - S -> L1 (strict lower) / U (upper)
+  double* M = W + nn;                         // U R1 (upper)
+  double* X = M + nn;                         // L1^{-1}, then T
+  double* sv = X + nn;                        // [nbp] s_i
+  double* dv = sv + nbp;                      // [nbp] 1 / M_jj, column sums
+  __shared__ int s_ok;
+  const int64_t rb = (int64_t)blockIdx.x * rp;
+  const int64_t nr64 = a.mr - rb;
+  const int nr = nr64 <= 0 ? 0 : (nr64 < rp ? (int)nr64 : rp);
+  S* P = (S*)a.P;
+
+  for (int c = 0; c < nbp; ++c)
+    for (int r = tid; r < nr; r += kPT) slab[(size_t)c * rp + r] = (double)P[rb + r + c * a.ld];
+  // the top nbp rows of the panel (held by CTA 0, read by all before CTA 0
+  // can overwrite them, i.e. before the second barrier)
+  for (int e = tid; e < nn; e += kPT) W[e] = (double)P[(e % nbp) + (int64_t)(e / nbp) * a.ld];
+  __syncthreads();
+
+  // 1. This CTA's share of the upper Gram matrix, packed.
+  const int ng = nbp * (nbp + 1) / 2;
+  double* gp = a.gram_part + (size_t)blockIdx.x * kGramStride;
+  for (int e = tid; e < ng; e += kPT) {
+    int i, j;
+    tri_index(e, i, j);
+    const double* ci = slab + (size_t)i * rp;
+    const double* cj = slab + (size_t)j * rp;
+    double s = 0.0;
+    for (int r = 0; r < nr; ++r) s += ci[r] * cj[r];
+    gp[e] = s;
+  }
+  if (!grid_barrier(&a.bar[0], a.grid, a.status, kBarrierLimitNs)) return;
+  // Split reduction: CTA c sums entries [c ng / grid, (c+1) ng / grid) over
+  // all CTAs' partials in a fixed order.
+  double* gred = a.gram_part + (size_t)a.grid * kGramStride;
+  {
+    const int e0 = (int)((int64_t)blockIdx.x * ng / a.grid), e1 = (int)((int64_t)(blockIdx.x + 1) * ng / a.grid);
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int e = e0 + warp; e < e1; e += kNW) {
+      double s = 0.0;
+      for (int b = lane; b < a.grid; b += 32) s += __ldcg(a.gram_part + (size_t)b * kGramStride + e);
+      s = warp_sum(s);
+      if (lane == 0) gred[e] = s;
+    }
+  }
+  if (!grid_barrier(&a.bar[0], a.grid, a.status, kBarrierLimitNs)) return;
+
+  // 2. Every CTA: the full Gram matrix, its Cholesky factor R1 (upper, in G).
+  for (int e = tid; e < ng; e += kPT) {
+    int i, j;
+    tri_index(e, i, j);
+    const double v = __ldcg(gred + e);
+    G[i + j * nbp] = v;
+    G[j + i * nbp] = v;
+  }
+  if (tid == 0) s_ok = 1;
+  __syncthreads();
+  for (int k = 0; k < nbp; ++k) {
+    if (tid == 0) {
+      const double d = G[k + k * nbp];
+      if (!(d > 0.0) || !isfinite(d)) s_ok = 0;
+      G[k + k * nbp] = s_ok ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double rkk = G[k + k * nbp];
+    for (int j = k + 1 + tid; j < nbp; j += kPT) G[k + j * nbp] /= rkk;
+    __syncthreads();
+    const int w = nbp - k - 1;  // trailing block (k+1..nbp-1)^2, upper part
+    for (int e = tid; e < w * w; e += kPT) {
+      const int i = k + 1 + e % w, j = k + 1 + e / w;
+      if (i <= j) G[i + j * nbp] -= G[k + i * nbp] * G[k + j * nbp];
+    }
+    __syncthreads();
+  }
+  // R1^{-1}: column j solved by thread j (back substitution)
+  for (int j = tid; j < nbp; j += kPT) {
+    for (int i = 0; i < nbp; ++i) Ri[i + j * nbp] = 0.0;
+    Ri[j + j * nbp] = 1.0 / G[j + j * nbp];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s += G[i + k * nbp] * Ri[k + j * nbp];
+      Ri[i + j * nbp] = -s / G[i + i * nbp];
+    }
+  }
+  __syncthreads();
+  // kappa_1(R1) = ||R1||_1 ||R1^{-1}||_1
+  if (tid < nbp) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i <= tid; ++i) {
+      s1 += fabs(G[i + tid * nbp]);
+      s2 += fabs(Ri[i + tid * nbp]);
+    }
+    dv[tid] = s1;
+    sv[tid] = s2;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double n1 = 0.0, n2 = 0.0;
+    for (int j = 0; j < nbp; ++j) {
+      n1 = fmax(n1, dv[j]);
+      n2 = fmax(n2, sv[j]);
+    }
+    if (!(n1 * n2 <= kCqrMaxCond)) s_ok = 0;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    // per-column Householder on the same slab; G.. onward is free
+    panel_householder<S, double>(a, slab, G, smem);
+    return;
+  }
+
+  // 3. Q1 = P1 R1^{-1} (in W), then the modified LU of Q1 - S in place.
+  for (int e = tid; e < nn; e += kPT) {
+    const int r = e % nbp, j = e / nbp;
+    double s = 0.0;
+    for (int k = 0; k <= j; ++k) s += W[r + k * nbp] * Ri[k + j * nbp];
+    X[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < nn; e += kPT) W[e] = X[e];
+  __syncthreads();
+  for (int i = 0; i < nbp; ++i) {
+    if (tid == 0) {
+      const double q = W[i + i * nbp];
+      const double si = q >= 0.0 ? -1.0 : 1.0;
+      sv[i] = si;
+      W[i + i * nbp] = q - si;  // |pivot| >= 1
+    }
+    __syncthreads();
+    const double piv = W[i + i * nbp];
+    for (int r = i + 1 + tid; r < nbp; r += kPT) W[r + i * nbp] /= piv;
+    __syncthreads();
+    const int w = nbp - i - 1;
+    for (int e = tid; e < w * w; e += kPT) {
+      const int r = i + 1 + e % w, c = i + 1 + e / w;
+      W[r + c * nbp] -= W[r + i * nbp] * W[i + c * nbp];
+    }
+    __syncthreads();
+  }
+  // M = U R1 (upper) and 1 / M_jj
+  for (int e = tid; e < nn; e += kPT) {
+    const int i = e % nbp, j = e / nbp;
+    double s = 0.0;
+    if (i <= j)
+      for (int k = i; k <= j; ++k) s += W[i + k * nbp] * G[k + j * nbp];
+    M[e] = s;
+  }
+  __syncthreads();
+  if (tid < nbp) dv[tid] = 1.0 / M[tid + tid * nbp];
+  __syncthreads();
+
+  // 4. This CTA's rows: V2 = P2 M^{-1} (rows with panel index >= nbp); the top
+  //    nbp rows (CTA 0) become R = S R1 on/above and L1 below the diagonal.
+  for (int r = tid; r < nr; r += kPT) {
+    const int64_t gr = rb + r;
+    if (gr >= nbp) {
+      for (int j = 0; j < nbp; ++j) {
+        double s = slab[(size_t)j * rp + r];
+        for (int i = 0; i < j; ++i) s -= slab[(size_t)i * rp + r] * M[i + j * nbp];
+        slab[(size_t)j * rp + r] = s * dv[j];
+      }
+    } else {
+      const int i = (int)gr;
+      for (int j = 0; j < nbp; ++j)
+        slab[(size_t)j * rp + r] = j >= i ? sv[i] * G[i + j * nbp] : W[i + j * nbp];
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < nbp; ++c)
+    for (int r = tid; r < nr; r += kPT) P[rb + r + c * a.ld] = (S)slab[(size_t)c * rp + r];
+
+  // 5. CTA 0: T = -U S L1^{-T} and tau = diag(T).
+  if (blockIdx.x != 0) return;
+  // L1^{-1} (unit lower): column j by thread j, forward substitution
+  for (int j = tid; j < nbp; j += kPT) {
+    for (int i = 0; i < nbp; ++i) X[i + j * nbp] = i == j ? 1.0 : 0.0;
+    for (int i = j + 1; i < nbp; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += W[i + k * nbp] * X[k + j * nbp];
+      X[i + j * nbp] = -s;
+    }
+  }
+  __syncthreads();
+  // T_ij = -sum_{k=i..j} U_ik s_k (L1^{-1})_jk, i <= j (into Ri, free now)
+  for (int e = tid; e < nn; e += kPT) {
+    const int i = e % nbp, j = e / nbp;
+    double s = 0.0;
+    if (i <= j)
+      for (int k = i; k <= j; ++k) s += W[i + k * nbp] * sv[k] * X[j + k * nbp];
+    Ri[e] = i <= j ? -s : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < nn; e += kPT) {
+    const int i = e % nbp, j = e / nbp;
+    a.T[i + (size_t)j * a.ldt] = Ri[e];
+  }
+  for (int i = tid; i < nbp; i += kPT) a.tau[i] = Ri[i + i * nbp];
+}
+
 // CTAs for an mr-row panel: about 64 rows each, at most one per SM (measured:
 // fewer, fuller CTAs were slower for both arithmetic types).
 int panel_grid(int64_t mr, const DeviceInfo& di, size_t mth) {
@@ -242,11 +499,30 @@ int panel_grid(int64_t mr, const DeviceInfo& di, size_t mth) {
   return grid;
 }
 
+size_t panel_cqr_smem_bytes(int nbp, int rp) {
+  size_t bytes = ((size_t)nbp * rp + 5 * (size_t)nbp * nbp + 2 * nbp) * sizeof(double);
+  // the Householder fallback: its buffers in place of G.., T at the start
+  const size_t fb = ((size_t)nbp * rp + kSmallDoubles + kMaxNb) * sizeof(double);
+  const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
+  bytes = bytes < fb ? fb : bytes;
+  return bytes < t_need ? t_need : bytes;
+}
+
 size_t panel_smem_bytes(int nbp, int rp, size_t mth) {
   const size_t small = (size_t)(2 * kMaxNb + kMaxNb + kNW * 2 * kMaxNb) * sizeof(double) + kMaxNb * mth;
   size_t bytes = small + (size_t)nbp * rp * mth;
   const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
   return bytes < t_need ? t_need : bytes;
+}
+
+// Cholesky-QR panels are used for FP32-stored factors unless
+// CTQR_PANEL_HOUSEHOLDER=1 asks for the per-column kernel everywhere.
+bool cqr_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("CTQR_PANEL_HOUSEHOLDER");
+    return !(e && *e == '1');
+  }();
+  return on;
 }
 
 template <typename S, typename Mth>
@@ -255,11 +531,14 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   const int64_t mr = f->m - j0;
   int grid = panel_grid(mr, di, sizeof(Mth));
   int rp = (int)((mr + grid - 1) / grid);
-  const size_t smem = panel_smem_bytes(nbp, rp, sizeof(Mth));
+  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp &&
+             panel_cqr_smem_bytes(nbp, rp) <= (size_t)di.smem_optin;
+  const void* fn = cqr ? (const void*)k_panel_cqr<S> : (const void*)k_panel<S, Mth>;
+  const size_t smem = cqr ? panel_cqr_smem_bytes(nbp, rp) : panel_smem_bytes(nbp, rp, sizeof(Mth));
   if (smem > (size_t)di.smem_optin) return CT_ERR_UNSUPPORTED;
-  CT_CUDA_TRY(cudaFuncSetAttribute(k_panel<S, Mth>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel<S, Mth>, kPT, smem));
+  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPT, smem));
   if (per_sm < 1) return CT_ERR_UNSUPPORTED;
   if (grid > per_sm * di.sms) return CT_ERR_UNSUPPORTED;
 
@@ -280,7 +559,7 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   CT_CUDA_TRY(cudaMemsetAsync(f->barrier, 0, 2 * sizeof(unsigned long long), s));
   void* args[] = {&a};
   LaunchScope ls(K_PANEL, s, 3.0 * (double)mr * nbp * nbp, 2.0 * (double)mr * nbp * sizeof(S));
-  CT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel<S, Mth>, dim3(grid), dim3(kPT), args, smem, s));
+  CT_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPT), args, smem, s));
   return CT_OK;
 }
 
@@ -288,7 +567,9 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
 
 size_t panel_partials_elems(int sms, int nb) {
   (void)nb;
-  return (size_t)2 * sms * 2 * kMaxNb + (size_t)sms * (kMaxNb * (kMaxNb - 1) / 2);
+  // column partials [2][sms][2*kMaxNb]; per-CTA Gram partials (and the
+  // reduced Gram of the Cholesky-QR panel after them)
+  return (size_t)2 * sms * 2 * kMaxNb + (size_t)(sms + 1) * kGramStride;
 }
 
 // Largest panel width <= want (halving when pow2) whose shared-memory slab
