@@ -253,6 +253,17 @@ ct_status ct_apply_qt_noalloc(const ct_factor* f, double* B, int64_t ldb, int64_
 ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k,
                         void* stream);
 
+/* The preconditioner solves of the mixed-precision refinement, exposed on
+ * their own: B[0:n, 0:k] <- R^{-1} B (transpose = 0) or R^{-T} B
+ * (transpose != 0) in FP32 arithmetic with the FP32-stored R of a
+ * CT_PREC_F32 / CT_PREC_TF32 factor; B is an FP32 device matrix, ldb >= n.
+ * The paper's factor is FP64 and has no counterpart; the operation is the
+ * back substitution of Sec. II-C-4 at lower precision.  One persistent
+ * launch walks the 64-row block rows in dependency order for every 64
+ * columns of B.  CT_ERR_UNSUPPORTED for an FP64 factor. */
+ct_status ct_trsm_solve_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k, int transpose,
+                            void* stream);
+
 /* X = R^{-1} (Q^T B)[0:n] for k slices (Eq. (qr1)): B is m x k (ldb >= m,
  * read only), X is n x k (ldx >= n), both FP64 device matrices.
  * Without A (A == NULL) this is one Q^T application and one back-solve in

@@ -675,6 +675,15 @@ ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k, v
   return launch_trsm(f, B, true, ldb, k, as_stream(stream));
 }
 
+ct_status ct_trsm_solve_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k, int transpose, void* stream) {
+  if (!f || k < 0) return CT_ERR_INVALID;
+  if (f->store != CT_F32) return CT_ERR_UNSUPPORTED;
+  if (k == 0) return CT_OK;
+  if (!B || !aligned16(B) || ldb < f->n) return CT_ERR_INVALID;
+  cudaStream_t s = as_stream(stream);
+  return transpose ? launch_trsm_t(f, B, false, ldb, k, s) : launch_trsm(f, B, false, ldb, k, s);
+}
+
 static ct_status reconstruct_impl(const ct_factor* f, const void* A, ct_dtype A_dtype, int64_t lda,
                                   const SparseSystem* sp, const double* B, int64_t ldb, double* X, int64_t ldx,
                                   int64_t k, const ct_refine_opts* ropts, ct_report* report, void* stream);

@@ -35,6 +35,9 @@ namespace {
 constexpr int kPT = 256;  // threads per CTA
 constexpr int kNW = kPT / 32;
 constexpr int kMaxNb = 64;
+// Bytes of the opt-in shared memory left for the panel kernels' static
+// __shared__ variables (a few ints) when sizing their dynamic shared memory.
+constexpr size_t kStaticSmemReserve = 1024;
 
 struct PanelArgs {
   void* P;               // &F[j0 + j0*ld]
@@ -531,11 +534,13 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   const int64_t mr = f->m - j0;
   int grid = panel_grid(mr, di, sizeof(Mth));
   int rp = (int)((mr + grid - 1) / grid);
-  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp &&
-             panel_cqr_smem_bytes(nbp, rp) <= (size_t)di.smem_optin;
+  // dynamic shared memory may use the opt-in limit minus the kernels' few
+  // bytes of static shared memory
+  const size_t limit = (size_t)di.smem_optin - kStaticSmemReserve;
+  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp && panel_cqr_smem_bytes(nbp, rp) <= limit;
   const void* fn = cqr ? (const void*)k_panel_cqr<S> : (const void*)k_panel<S, Mth>;
   const size_t smem = cqr ? panel_cqr_smem_bytes(nbp, rp) : panel_smem_bytes(nbp, rp, sizeof(Mth));
-  if (smem > (size_t)di.smem_optin) return CT_ERR_UNSUPPORTED;
+  if (smem > limit) return CT_ERR_UNSUPPORTED;
   CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPT, smem));
@@ -578,7 +583,8 @@ int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth
   int grid = panel_grid(mr, di, mth);
   const int rp = (int)((mr + grid - 1) / grid);
   int nb = want > kMaxNb ? kMaxNb : want;
-  while (nb > 8 && panel_smem_bytes(nb, rp, mth) > (size_t)di.smem_optin) nb = pow2 ? nb / 2 : nb - 8;
+  while (nb > 8 && panel_smem_bytes(nb, rp, mth) > (size_t)di.smem_optin - kStaticSmemReserve)
+    nb = pow2 ? nb / 2 : nb - 8;
   return nb;
 }
 

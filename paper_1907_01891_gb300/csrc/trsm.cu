@@ -9,6 +9,7 @@
 // (spread over the whole GPU), then the top half is solved; the leaves are
 // 64 x 64 diagonal solves (one warp per right-hand side).
 #include <math.h>
+#include <stdlib.h>
 
 #include "internal.cuh"
 
@@ -129,6 +130,186 @@ __global__ void __launch_bounds__(1024) k_rank_check(const S* __restrict__ F, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-launch block substitution for FP32 R and FP32 right-hand sides (the
+// preconditioner solves of the mixed-precision refinement, k <= 64).
+//
+// The recursive scheme above issues about two launches per 64-row block; for
+// a few right-hand sides each launch is tiny and the solve is a chain of
+// launch latencies.  Here one persistent launch walks the block rows in
+// dependency order: a CTA takes the next block row i from a ticket counter
+// (bottom-up for R X = B, top-down for R^T Z = B), subtracts the products
+// with every finished block X_j as soon as that block's flag is set, solves
+// its 64 x 64 diagonal block and publishes X_i with a release store of flag i.
+// A CTA only waits for blocks whose tickets were taken earlier, by CTAs that
+// are running, so the launch always progresses; every wait is bounded (2 s,
+// then CT_ERR_TIMEOUT in the status word and the CTA leaves).
+constexpr int kPB = 64;  // block rows and the most right-hand sides per launch
+
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ F, int64_t ld, int64_t n,
+                                                      float* __restrict__ B, int64_t ldb, int k,
+                                                      int* __restrict__ flags, int* __restrict__ ticket,
+                                                      int* __restrict__ status) {
+  extern __shared__ float psm[];
+  float (*Rs)[kPB + 1] = (float (*)[kPB + 1])psm;                       // an off-diagonal block, then R_ii
+  float (*Xs)[kPB + 1] = (float (*)[kPB + 1])(psm + kPB * (kPB + 1));   // X_j [row][column]
+  float (*Ys)[kPB + 1] = (float (*)[kPB + 1])(psm + 2 * kPB * (kPB + 1));  // B_i minus the products so far
+  __shared__ int s_t, s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (int)((n + kPB - 1) / kPB);
+  for (;;) {
+    if (tid == 0) {
+      s_t = atomicAdd(ticket, 1);
+      s_fail = 0;
+    }
+    __syncthreads();
+    const int t = s_t;
+    if (t >= nb) return;
+    const int i = TRANS ? t : nb - 1 - t;
+    const int64_t i0 = (int64_t)i * kPB;
+    const int ni = (int)(n - i0 < kPB ? n - i0 : kPB);
+    // B_i, and the diagonal block R_ii (upper part) held in registers until
+    // the end so that loading it is off the dependency chain
+    float dreg[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * u, r = e % kPB, c = e / kPB;
+      Ys[r][c] = (r < ni && c < k) ? __ldcg(B + i0 + r + c * ldb) : 0.f;
+      dreg[u] = (r < ni && c < ni && r <= c) ? F[i0 + r + (i0 + c) * ld] : 0.f;
+    }
+    const int deps = TRANS ? i : nb - 1 - i;
+    // the 64 x 64 block op(R)_{ij} for contribution q, 16 elements per
+    // thread held in registers so its loads overlap the previous product:
+    // element u is (r, c) = (e % 64, e / 64) of the stored block, e = tid + 256 u
+    float rreg[16];
+    auto load_r = [&](int q) {
+      const int j = TRANS ? q : nb - 1 - q;
+      const int64_t j0 = (int64_t)j * kPB;
+      const int nj = (int)(n - j0 < kPB ? n - j0 : kPB);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u, a = e % kPB, b = e / kPB;
+        // !TRANS: R(i0 + a, j0 + b); TRANS: R(j0 + a, i0 + b) (contiguous along a)
+        const bool ok = TRANS ? (a < nj && b < ni) : (a < ni && b < nj);
+        rreg[u] = ok ? __ldcg(TRANS ? F + j0 + a + (i0 + b) * ld : F + i0 + a + (j0 + b) * ld) : 0.f;
+      }
+    };
+    if (deps > 0) load_r(0);
+    for (int q = 0; q < deps; ++q) {
+      const int j = TRANS ? q : nb - 1 - q;  // finished blocks first
+      const int64_t j0 = (int64_t)j * kPB;
+      const int nj = (int)(n - j0 < kPB ? n - j0 : kPB);
+      if (tid == 0) {
+        const uint64_t start = globaltimer_ns();
+        while (ld_acquire_i32(flags + j) == 0) {
+          if (ld_volatile_i32(status) != 0) { s_fail = 1; break; }
+          if (globaltimer_ns() - start > kBarrierLimitNs) {
+            set_status(status, CT_ERR_TIMEOUT);
+            s_fail = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __syncthreads();
+      if (s_fail) return;
+      float xreg[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u, r = e % kPB, c = e / kPB;
+        xreg[u] = (r < nj && c < k) ? __ldcg(B + j0 + r + c * ldb) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u, a = e % kPB, b = e / kPB;
+        // Rs[r][c] = op(R)_{ij}(r, c)
+        if (TRANS) Rs[b][a] = rreg[u];
+        else Rs[a][b] = rreg[u];
+        Xs[a][b] = xreg[u];
+      }
+      __syncthreads();
+      if (q + 1 < deps) load_r(q + 1);
+      // Ys -= Rs Xs with a 4 x 4 register tile per thread: rows
+      // 4 * (tid % 16) + 0..3, columns tid / 16 + 16 * w (w < 4, c < k)
+      {
+        const int r4 = (tid % 16) * 4, cgp = tid / 16;
+        const int ncol = (k - cgp + 15) / 16;  // 0..4 columns for this thread
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[a][w] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < kPB; ++l) {
+          float rv[4], xv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) rv[a] = Rs[r4 + a][l];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) xv[w] = Xs[l][(cgp + 16 * w) & (kPB - 1)];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[a][w] = fmaf(rv[a], xv[w], acc[a][w]);
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          if (w < ncol)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) Ys[r4 + a][cgp + 16 * w] -= acc[a][w];
+      }
+      __syncthreads();
+    }
+    // diagonal block: X_i = R_ii^{-1} Ys (or R_ii^{-T}); one warp per column,
+    // with the reciprocals of the diagonal computed once
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * u, r = e % kPB, c = e / kPB;
+      Rs[r][c] = dreg[u];
+    }
+    __syncthreads();
+    float* rdiag = &Xs[0][0];  // free now
+    if (tid < ni) rdiag[tid] = 1.f / Rs[tid][tid];
+    __syncthreads();
+    for (int c = warp; c < k; c += 8) {
+      float y0 = lane < ni ? Ys[lane][c] : 0.f;
+      float y1 = lane + 32 < ni ? Ys[lane + 32][c] : 0.f;
+      if (!TRANS) {
+        for (int q = ni - 1; q >= 0; --q) {
+          const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
+          const float xq = yq * rdiag[q];
+          if (q < 32) { if (lane == q) y0 = xq; } else if (lane == q - 32) { y1 = xq; }
+          if (lane < q) y0 -= Rs[lane][q] * xq;
+          if (lane + 32 < q) y1 -= Rs[lane + 32][q] * xq;
+        }
+      } else {
+        for (int q = 0; q < ni; ++q) {
+          const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
+          const float zq = yq * rdiag[q];
+          if (q < 32) { if (lane == q) y0 = zq; } else if (lane == q - 32) { y1 = zq; }
+          if (lane > q && lane < ni) y0 -= Rs[q][lane] * zq;
+          if (lane + 32 > q && lane + 32 < ni) y1 -= Rs[q][lane + 32] * zq;
+        }
+      }
+      if (lane < ni) B[i0 + lane + c * ldb] = y0;
+      if (lane + 32 < ni) B[i0 + lane + 32 + c * ldb] = y1;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release_i32(flags + i, 1);
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -206,9 +387,62 @@ ct_status solve_rec_t(const TrsmCtx& c, int64_t lo, int64_t hi) {
 // Recursive halving: 64 x 64 diagonal solves (Trsm_lunn) at the leaves and
 // one product per split for the block above (Gemm_nn_mo), so the products
 // are few and large instead of one K = 64 update per block column.
+namespace {
+
+bool persist_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("CTQR_TRSM_RECURSIVE");
+    return !(e && *e == '1');
+  }();
+  return on;
+}
+
+// One persistent launch per group of up to 64 columns (FP32 R and B).
+ct_status trsm_persist(const ct_factor* f, float* B, int64_t ldb, int64_t k, bool transpose, cudaStream_t s) {
+  DeviceInfo di;
+  ct_status st = device_info(&di);
+  if (st != CT_OK) return st;
+  const int nb = (int)((f->n + kPB - 1) / kPB);
+  int* flags = nullptr;
+  const size_t words = (size_t)nb + 4;
+  CT_CUDA_TRY(cudaMallocAsync((void**)&flags, words * sizeof(int), s));
+  struct Free { int* p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{flags, s};
+  const size_t smem = (size_t)3 * kPB * (kPB + 1) * sizeof(float);
+  const void* fn = transpose ? (const void*)k_trsm_persist<true> : (const void*)k_trsm_persist<false>;
+  CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
+  int grid = di.sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > nb) grid = nb;
+  for (int64_t c0 = 0; c0 < k; c0 += kPB) {
+    const int kc = (int)(k - c0 < kPB ? k - c0 : kPB);
+    CT_CUDA_TRY(cudaMemsetAsync(flags, 0, words * sizeof(int), s));
+    LaunchScope ls(K_TRSM_DIAG, s, (double)f->n * f->n * kc, (double)f->n * f->n * 2.0 + 8.0 * f->n * kc);
+    if (transpose)
+      k_trsm_persist<true><<<grid, 256, smem, s>>>((const float*)f->F, f->ld, f->n, B + c0 * ldb, ldb, kc, flags,
+                                                flags + nb, f->status);
+    else
+      k_trsm_persist<false><<<grid, 256, smem, s>>>((const float*)f->F, f->ld, f->n, B + c0 * ldb, ldb, kc, flags,
+                                                 flags + nb, f->status);
+    CT_LAUNCH_CHECK();
+  }
+  return CT_OK;
+}
+
+}  // namespace
+
+// B[0:n, 0:k] <- R^{-1} B[0:n, 0:k]; B is FP64 (b_f64) or FP32.  FP64 B is
+// solved in FP64 arithmetic whatever R's storage type; FP32 B (the
+// preconditioner solves of the mixed-precision refinement) in FP32, in one
+// persistent launch per 64 columns (CTQR_TRSM_RECURSIVE=1: the recursive
+// scheme below).  Recursive halving: 64 x 64 diagonal solves (Trsm_lunn) at
+// the leaves and one product per split for the block above (Gemm_nn_mo), so
+// the products are few and large instead of one K = 64 update per block
+// column.
 ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
   if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
+  if (!b_f64 && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, false, s);
   const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
   return solve_rec(c, 0, f->n);
 }
@@ -217,6 +451,7 @@ ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int6
 ct_status launch_trsm_t(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
   if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
+  if (!b_f64 && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, true, s);
   const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
   return solve_rec_t(c, 0, f->n);
 }

@@ -112,6 +112,7 @@ SIGNATURES = {
     "ct_apply_qt": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_apply_qt_noalloc": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_trsm_solve": ([_VP, _VP, _I64, _I64, _VP], _I),
+    "ct_trsm_solve_f32": ([_VP, _VP, _I64, _I64, _I, _VP], _I),
     "ct_reconstruct_batch": ([_VP, _VP, _I, _I64, _VP, _I64, _VP, _I64, _I64,
                               ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
     "ct_factor_destroy": ([_VP], None),
@@ -317,6 +318,13 @@ def apply_qt_noalloc(f: Factor, B: torch.Tensor) -> torch.Tensor:
     """B <- Q^T B in place without any device allocation (k <= 64 columns)."""
     _check(load().ct_apply_qt_noalloc(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()),
            "ct_apply_qt_noalloc")
+    return B
+
+
+def trsm_solve_f32(f: Factor, B: torch.Tensor, transpose: bool = False) -> torch.Tensor:
+    """B <- R^{-1} B (or R^{-T} B) in FP32 with a mixed-precision factor's R."""
+    _check(load().ct_trsm_solve_f32(f.handle, B.data_ptr(), _ld(B), B.shape[1], 1 if transpose else 0, _stream()),
+           "ct_trsm_solve_f32")
     return B
 
 

@@ -342,3 +342,31 @@ def test_lambda_stacked_scan_matches_oracle(prec):
     Xo = O.lstsq(As, bs)
     X, rep = ctqr.reconstruct_scan(g, bs, prec=prec, lam=lam)
     assert np.linalg.norm(X.numpy() - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
+
+
+@pytest.mark.parametrize("n,k", [(200, 3), (1000, 17), (257, 70)])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_fp32_triangular_solve_matches_oracle(n, k, transpose):
+    """ct_trsm_solve_f32 (the refinement's preconditioner solve, one
+    persistent launch per 64 columns) on a factor whose R is known exactly:
+    an upper triangular matrix with FP32-exact entries factors to R = +-A
+    (the Householder panel keeps it, the Cholesky-QR panel flips every
+    row's sign), so the oracle solves with +-A in FP64."""
+    rng = np.random.default_rng(70 + n + k)
+    A = np.triu(rng.uniform(-1.0, 1.0, (n, n)) / n)  # diagonally dominant: well conditioned
+    A[np.diag_indices(n)] = rng.uniform(1.0, 2.0, n)
+    A = A.astype(np.float32).astype(np.float64)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A, dtype=torch.float32), prec=ctqr.Prec.F32)
+    F, _ = ctqr.factor_matrix(f)
+    sign = 1.0 if _np(F)[0, 0] > 0 else -1.0  # which of the two exact R the panel produced
+    R = sign * A
+    Y = rng.standard_normal((n, k)).astype(np.float32)
+    B = ctqr.to_colmajor(Y, dtype=torch.float32)
+    ctqr.trsm_solve_f32(f, B, transpose=transpose)
+    X = _np(B).astype(np.float64)
+    if transpose:
+        ref = np.linalg.solve(R.T, Y.astype(np.float64))   # lower triangular system, library solve
+    else:
+        ref = O.backsolve(np.asfortranarray(R), np.asfortranarray(Y.astype(np.float64)))
+    err = np.linalg.norm(X - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, err
