@@ -258,9 +258,10 @@ ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k,
  * (transpose != 0) in FP32 arithmetic with the FP32-stored R of a
  * CT_PREC_F32 / CT_PREC_TF32 factor; B is an FP32 device matrix, ldb >= n.
  * The paper's factor is FP64 and has no counterpart; the operation is the
- * back substitution of Sec. II-C-4 at lower precision.  One persistent
- * launch walks the 64-row block rows in dependency order for every 64
- * columns of B.  CT_ERR_UNSUPPORTED for an FP64 factor. */
+ * back substitution of Sec. II-C-4 at lower precision.  For k <= 64 one
+ * persistent launch walks the 64-row block rows in dependency order; wider B
+ * uses recursive halving with one product per split.  CT_ERR_UNSUPPORTED for
+ * an FP64 factor. */
 ct_status ct_trsm_solve_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k, int transpose,
                             void* stream);
 

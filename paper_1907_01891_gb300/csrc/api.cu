@@ -59,6 +59,7 @@ void free_factor(ct_factor* f) {
   if (f->status) cudaFree(f->status);
   if (f->barrier) cudaFree(f->barrier);
   if (f->partials) cudaFree(f->partials);
+  if (f->Gblk) cudaFree(f->Gblk);
   delete f;
 }
 
@@ -448,7 +449,19 @@ int64_t npanels(const ct_factor* f) { return (f->n + f->nb - 1) / f->nb; }
 ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
                        double* work, size_t work_elems, int sms, cudaStream_t s, int max_splits) {
   const size_t es = elem_size(f->store), cs = c_f64 ? 8 : 4;
-  for (int64_t j0 = 0, p = 0; j0 < f->n; j0 += f->nb, ++p) {
+  // Two-level factors apply each 128-column outer block at once (its panels'
+  // reflectors in the same order), except the last block, whose V^T V the
+  // factorization did not form; the allocation-free path (max_splits) keeps
+  // the per-panel application.
+  int64_t jblk = 0;
+  if (f->Gblk && max_splits == 0) {
+    for (; jblk + 128 < f->n; jblk += 128) {
+      ct_status st = apply_outer_reflector(f, jblk, (char*)C + (size_t)jblk * cs, c_f64, ldc, k, fp32_math, work,
+                                           work_elems, sms, s);
+      if (st != CT_OK) return st;
+    }
+  }
+  for (int64_t j0 = jblk, p = jblk / f->nb; j0 < f->n; j0 += f->nb, ++p) {
     const int nbp = (int)(f->n - j0 < f->nb ? f->n - j0 : f->nb);
     ReflectorArgs a;
     a.V = (const char*)f->F + (size_t)(j0 + j0 * f->ld) * es;
@@ -553,7 +566,8 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       (st = dev_alloc(&f->T, (size_t)np * f->nb * f->nb)) != CT_OK ||
       (st = dev_alloc(&f->status, 1)) != CT_OK ||
       (st = dev_alloc(&f->barrier, 2)) != CT_OK ||
-      (st = dev_alloc(&f->partials, f->partials_elems)) != CT_OK) {
+      (st = dev_alloc(&f->partials, f->partials_elems)) != CT_OK ||
+      (tc && (st = dev_alloc(&f->Gblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK)) {
     free_factor(f);
     return st;
   }

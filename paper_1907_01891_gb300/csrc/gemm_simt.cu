@@ -33,26 +33,29 @@ __device__ __forceinline__ Acc v_at(const TV* V, int64_t ldv, int64_t r, int a, 
   return (Acc)V[r + a * ldv];
 }
 
-template <typename TV, typename TC, typename Acc, int BN>
+// P_s = V^T C over the row chunk of split s (blockIdx.y): BM rows of V^T
+// (reflectors, padded) x BN columns of C per CTA, RM = BM / 16 rows and
+// TN = BN / 16 columns per thread.
+template <typename TV, typename TC, typename Acc, int BN, int BM = kBM>
 __global__ void __launch_bounds__(kGT) k_vtc(const TV* __restrict__ V, int64_t ldv, int nbp,
                                               const TC* __restrict__ C, int64_t ldc, int64_t mr,
                                               int64_t nc, int64_t chunk, double* __restrict__ part) {
-  constexpr int TN = BN / 16;
-  __shared__ Acc Vs[kBK][kBM + 1];
+  constexpr int TN = BN / 16, RM = BM / 16;
+  __shared__ Acc Vs[kBK][BM + 1];
   __shared__ Acc Cs[kBK][BN + 1];
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   const int64_t c0 = (int64_t)blockIdx.x * BN;
   const int64_t rbeg = (int64_t)blockIdx.y * chunk;
   const int64_t rend = rbeg + chunk < mr ? rbeg + chunk : mr;
-  Acc acc[4][TN];
+  Acc acc[RM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = (Acc)0;
 
   for (int64_t r0 = rbeg; r0 < rend; r0 += kBK) {
 #pragma unroll
-    for (int i = 0; i < kBM * kBK / kGT; ++i) {
+    for (int i = 0; i < BM * kBK / kGT; ++i) {
       const int e = tid + kGT * i, a = e / kBK, rr = e % kBK;
       const int64_t r = r0 + rr;
       Vs[rr][a] = r < rend ? v_at<Acc>(V, ldv, r, a, mr, nbp, true) : (Acc)0;
@@ -69,25 +72,25 @@ __global__ void __launch_bounds__(kGT) k_vtc(const TV* __restrict__ V, int64_t l
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      Acc av[4], cv[TN];
+      Acc av[RM], cv[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty * 4 + i];
+      for (int i = 0; i < RM; ++i) av[i] = Vs[kk][ty * RM + i];
 #pragma unroll
       for (int j = 0; j < TN; ++j) cv[j] = Cs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * cv[j];
     }
     __syncthreads();
   }
-  double* out = part + (size_t)blockIdx.y * kBM * nc;
+  double* out = part + (size_t)blockIdx.y * BM * nc;
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
     const int64_t cg = c0 + tx * TN + j;
     if (cg < nc)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) out[ty * 4 + i + cg * kBM] = (double)acc[i][j];
+      for (int i = 0; i < RM; ++i) out[ty * RM + i + cg * BM] = (double)acc[i][j];
   }
 }
 
@@ -102,8 +105,13 @@ __global__ void __launch_bounds__(kGT) k_tw(const double* __restrict__ part, int
   constexpr int NW = kGT / 32;
   __shared__ double red[NW][kBM];
   __shared__ double sv[kBM];
+  __shared__ Acc Ts[kBM][kBM + 1];  // T(b, a) at Ts[a][b]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c = blockIdx.x;
+  for (int e = tid; e < kBM * kBM; e += kGT) {
+    const int b = e % kBM, a = e / kBM;
+    Ts[a][b] = (a < nbp && b <= a) ? (Acc)T[b + (int64_t)a * ldt] : (Acc)0;
+  }
   const double* base = part + (size_t)c * kBM;
   const size_t stride = (size_t)kBM * nc;
   double s0 = 0.0, s1 = 0.0;
@@ -139,12 +147,73 @@ __global__ void __launch_bounds__(kGT) k_tw(const double* __restrict__ part, int
     const int a = tid;
     Acc t = (Acc)0;
     if (a < nbp)
-      for (int b = 0; b <= a; ++b) t += (Acc)T[b + a * ldt] * (Acc)sv[b];
+      for (int b = 0; b <= a; ++b) t += Ts[a][b] * (Acc)sv[b];
     W[a + c * kBM] = (double)t;
   }
 }
 
-// C(r, c) -= sum_{a < K} V(r, a) W(a, c); 64 x BN tile per CTA, K <= 64.
+// Outer-block form of W' = T^T sum_s P_s for a 128-column block reflector
+// given through S = T^{-1} = diag(1/tau) + striu(G): W' solves S^T W' = W by
+// forward substitution (w'_i = tau_i w_i, then w_r -= G(i, r) w'_i for
+// r > i; tau_i = 0 gives w'_i = 0).  One CTA per column c: the eight warps
+// sum the splits (fixed order), warp 0 substitutes (lane l: rows l + 32 q).
+constexpr int kOB = 128;
+template <typename Acc>
+__global__ void __launch_bounds__(kGT) k_solve_blk(const double* __restrict__ part, int splits, int64_t nc,
+                                                   const float* __restrict__ G, const double* __restrict__ tau,
+                                                   int nbo, double* __restrict__ W) {
+  constexpr int NW = kGT / 32;
+  extern __shared__ float gs[];  // G(i, r) at gs[i * (kOB + 1) + r]
+  __shared__ double red[NW][kOB];
+  __shared__ Acc ts[kOB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c = blockIdx.x;
+  for (int e = tid; e < kOB * kOB; e += kGT) {
+    const int i = e % kOB, r = e / kOB;
+    gs[i * (kOB + 1) + r] = G[e];
+  }
+  for (int i = tid; i < kOB; i += kGT) ts[i] = i < nbo ? (Acc)tau[i] : (Acc)0;
+  const double* base = part + (size_t)c * kOB;
+  const size_t stride = (size_t)kOB * nc;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int sp = warp; sp < splits; sp += NW) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __ldcg(base + (size_t)sp * stride + lane + 32 * q);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] += v[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[warp][lane + 32 * q] = s[q];
+  __syncthreads();
+  if (warp != 0) return;
+  Acc w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) t += red[u][lane + 32 * q];
+    w[q] = (Acc)t;
+  }
+  for (int i = 0; i < nbo; ++i) {
+    const int qi = i >> 5;
+    const Acc src = qi == 0 ? w[0] : (qi == 1 ? w[1] : (qi == 2 ? w[2] : w[3]));
+    const Acc wi = __shfl_sync(0xffffffffu, src, i & 31) * ts[i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = lane + 32 * q;
+      if (r == i) w[q] = wi;
+      else if (r > i) w[q] -= (Acc)gs[i * (kOB + 1) + r] * wi;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = lane + 32 * q;
+    W[r + c * kOB] = r < nbo ? (double)w[q] : 0.0;
+  }
+}
+
+// C(r, c) -= sum_{a < K} V(r, a) W(a, c); 64 x BN tile per CTA, any K.
 template <typename TV, typename TW, typename TC, typename Acc, int BN>
 __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_t ldv, int K,
                                                  bool mask, const TW* __restrict__ W,
@@ -470,6 +539,68 @@ ct_status launch_gemm_tn(const void* A, bool a_f64, int64_t lda, const double* R
   }
   CT_LAUNCH_CHECK();
   return CT_OK;
+}
+
+namespace {
+
+template <typename TC, typename Acc>
+ct_status run_outer(const ct_factor* f, int64_t J, TC* C, int64_t ldc, int64_t k, double* work, size_t work_elems,
+                    int sms, cudaStream_t s) {
+  constexpr int BN = 16;
+  const float* V = (const float*)f->F + J + J * f->ld;
+  const int64_t mr = f->m - J;
+  const int nbo = kOB;
+  const int64_t tiles_n = (k + BN - 1) / BN;
+  // splits over rows: about one CTA per SM in all, and the partials (plus W')
+  // must fit the work area
+  int64_t splits = (sms + tiles_n - 1) / tiles_n;
+  const int64_t max_rows = (mr + 255) / 256;
+  if (splits > max_rows) splits = max_rows;
+  const int64_t fit = (int64_t)(work_elems / ((size_t)kOB * k)) - 1;
+  if (splits > fit) splits = fit;
+  if (splits < 1) return CT_ERR_INVALID;
+  int64_t chunk = (mr + splits - 1) / splits;
+  chunk = (chunk + kBK - 1) / kBK * kBK;
+  splits = (mr + chunk - 1) / chunk;
+  double* part = work;
+  double* W = work + (size_t)splits * kOB * k;
+  const double mnk = (double)mr * nbo * k;
+  {
+    LaunchScope ls(K_VTC, s, 2.0 * mnk, (double)mr * k * sizeof(TC) + (double)mr * nbo * 4.0);
+    k_vtc<float, TC, Acc, BN, kOB><<<dim3((unsigned)tiles_n, (unsigned)splits), kGT, 0, s>>>(
+        V, f->ld, nbo, C, ldc, mr, k, chunk, part);
+  }
+  {
+    const size_t smem = (size_t)kOB * (kOB + 1) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_solve_blk<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    LaunchScope ls(K_TW, s, (double)kOB * kOB * k, (double)(splits + 1) * kOB * k * 8 + smem);
+    k_solve_blk<Acc><<<(unsigned)k, kGT, smem, s>>>(part, (int)splits, k, f->Gblk + (size_t)(J / kOB) * kOB * kOB,
+                                                    f->tau + J, nbo, W);
+  }
+  {
+    LaunchScope ls(K_UPDATE, s, 2.0 * mnk, 2.0 * mr * k * sizeof(TC) + (double)mr * nbo * 4.0);
+    k_update<float, double, TC, Acc, BN><<<dim3((unsigned)((mr + kBM - 1) / kBM), (unsigned)tiles_n), kGT, 0, s>>>(
+        V, f->ld, nbo, true, W, kOB, C, ldc, mr, k);
+  }
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
+
+}  // namespace
+
+ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f64, int64_t ldc, int64_t k,
+                                bool fp32_math, double* work, size_t work_elems, int sms, cudaStream_t s) {
+  if (k <= 0) return CT_OK;
+  if (!f->Gblk || f->store != CT_F32 || J + kOB > f->n) return CT_ERR_INVALID;
+  if (c_f64) {
+    if (fp32_math) return run_outer<double, float>(f, J, (double*)C, ldc, k, work, work_elems, sms, s);
+    return run_outer<double, double>(f, J, (double*)C, ldc, k, work, work_elems, sms, s);
+  }
+  return run_outer<float, float>(f, J, (float*)C, ldc, k, work, work_elems, sms, s);
 }
 
 }  // namespace ctqr

@@ -138,6 +138,9 @@ struct ct_factor {
   unsigned long long* barrier = nullptr;  // grid-barrier counter
   double* partials = nullptr;   // panel-kernel reduction scratch
   size_t partials_elems = 0;
+  float* Gblk = nullptr;        // two-level factors: V^T V of every 128-column outer
+                                // block (128 x 128, strict upper part; blocks whose
+                                // update ran, i.e. all but the last)
   int device = 0;
 };
 
@@ -173,6 +176,13 @@ struct ReflectorArgs {
 size_t reflector_work_elems(int sms, int nbp, int64_t nc);
 ct_status apply_block_reflector(const ReflectorArgs& a, double* work, size_t work_elems,
                                 int sms, cudaStream_t s);
+
+// C <- (I - V T V^T)^T C for the 128-column outer block [J, J + 128) of a
+// two-level factor, T given through its UT-transform form S = T^{-1} =
+// diag(1/tau) + striu(G), G = V^T V (gemm_simt.cu); work as for
+// apply_block_reflector.
+ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f64, int64_t ldc, int64_t k,
+                                bool fp32_math, double* work, size_t work_elems, int sms, cudaStream_t s);
 
 // Q^T C for all panels of the factor, in factorization order (api.cu).
 ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,

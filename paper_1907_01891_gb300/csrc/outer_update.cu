@@ -58,37 +58,66 @@ __global__ void __launch_bounds__(256) k_extract_v(const float* __restrict__ F, 
   }
 }
 
-// W' (kNB x nc, ld kNB) from the split partials of W and G = V^T V (split
-// partials too), one warp per column; lane l holds rows l, l+32, l+64, l+96.
+// G = V^T V from its split partials: G(i, r) (strict upper part, i < r <
+// nbo; zero elsewhere) into Gout[i + r * kNB], one entry per thread, the
+// splits added in order with their loads in flight.
+__global__ void __launch_bounds__(256) k_reduce_gram(const float* __restrict__ Gp, int gsplits, int64_t gstride,
+                                                     int nbo, float* __restrict__ Gout) {
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e >= kNB * kNB) return;
+  const int i = e % kNB, r = e / kNB;
+  float s = 0.f;
+  if (i < nbo && r < nbo && i < r) {
+    int z = 0;
+    for (; z + 8 <= gsplits; z += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(Gp + (z + u) * gstride + i + (int64_t)r * kNB);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; z < gsplits; ++z) s += __ldcg(Gp + z * gstride + i + (int64_t)r * kNB);
+  }
+  Gout[e] = s;
+}
+
+// W' (kNB x nc, ld kNB) from the split partials of W and the reduced
+// G = V^T V, one warp per column; lane l holds rows l, l+32, l+64, l+96.
 constexpr int kGS = kNB + 1;  // row stride of the Gram matrix in shared memory
 constexpr size_t kSolveSmem = (size_t)(kNB * kGS + kNB) * sizeof(float);
 
 __global__ void __launch_bounds__(256) k_solve_st(const float* __restrict__ Wp, int wsplits, int64_t wstride,
-                                                  const float* __restrict__ Gp, int gsplits, int64_t gstride,
-                                                  const double* __restrict__ tau, int nbo, int64_t nc,
-                                                  float* __restrict__ Wout, float* __restrict__ Wlo) {
+                                                  const float* __restrict__ Gred, const double* __restrict__ tau,
+                                                  int nbo, int64_t nc, float* __restrict__ Wout,
+                                                  float* __restrict__ Wlo) {
   extern __shared__ float sm[];
   float* G = sm;              // G[i * kGS + r] = (V^T V)(i, r), strict upper part
   float* ts = sm + kNB * kGS;
   for (int e = threadIdx.x; e < kNB * kNB; e += 256) {
-    const int i = e % kNB, r = e / kNB;  // G(i, r) = column r, row i
-    float s = 0.f;
-    if (i < nbo && r < nbo && i < r)
-      for (int z = 0; z < gsplits; ++z) s += Gp[z * gstride + i + (int64_t)r * kNB];
-    G[i * kGS + r] = s;
+    const int i = e % kNB, r = e / kNB;
+    G[i * kGS + r] = __ldcg(Gred + e);
   }
   for (int i = threadIdx.x; i < kNB; i += 256) ts[i] = i < nbo ? (float)tau[i] : 0.f;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t c = (int64_t)blockIdx.x * 8 + warp; c < nc; c += (int64_t)gridDim.x * 8) {
-    float w[4];
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* wc = Wp + lane + c * kNB;
+    int z = 0;
+    for (; z + 4 <= wsplits; z += 4) {
+      float v[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float s = 0.f;
-      const int r = lane + 32 * q;
-      for (int z = 0; z < wsplits; ++z) s += Wp[z * wstride + r + c * kNB];
-      w[q] = s;
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[u][q] = __ldcg(wc + (z + u) * wstride + 32 * q);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] += v[u][q];
     }
+    for (; z < wsplits; ++z)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] += __ldcg(wc + z * wstride + 32 * q);
     for (int i = 0; i < nbo; ++i) {
       const int qi = i >> 5;
       const float src = qi == 0 ? w[0] : (qi == 1 ? w[1] : (qi == 2 ? w[2] : w[3]));
@@ -123,7 +152,7 @@ size_t outer_work_floats(int sms, int64_t m, int64_t n) {
          + (size_t)2 * m * kNB     // Vr (high, low)
          + (size_t)kNB * wcols     // W partials
          + (size_t)2 * kNB * n     // W' (high, low)
-         + (size_t)2 * sms * kNB * kNB;  // G partials
+         + (size_t)(2 * sms + 1) * kNB * kNB;  // G partials, reduced G
 }
 
 // Update C = F[J:m, J+nbo:n] with the block reflector of F[J:m, J:J+nbo].
@@ -177,6 +206,14 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     gchunk = (gchunk + 31) / 32 * 32;
     gs = (int)((mr + gchunk - 1) / gchunk);
   }
+  // The reduced G goes to the factor's per-block store (kept for later
+  // applications of this block reflector), else into the split area's tail.
+  float* Gred = f->Gblk ? f->Gblk + (size_t)(J / kNB) * kNB * kNB : Gp + (size_t)gs * kNB * kNB;
+  {
+    LaunchScope ls(K_TW, s, (double)kNB * kNB * gs, 4.0 * kNB * kNB * (gs + 1));
+    k_reduce_gram<<<kNB * kNB / 256, 256, 0, s>>>(Gp, gs, (int64_t)kNB * kNB, nbo, Gred);
+    CT_LAUNCH_CHECK();
+  }
   {
     LaunchScope ls(K_TW, s, (double)kNB * kNB * nc, 4.0 * kNB * nc * (ws + 1));
     unsigned grid = (unsigned)((nc + 7) / 8);
@@ -186,8 +223,8 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
       CT_CUDA_TRY(cudaFuncSetAttribute(k_solve_st, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem));
       attr = true;
     }
-    k_solve_st<<<grid, 256, kSolveSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Gp, gs, (int64_t)kNB * kNB,
-                                    f->tau + J, nbo, nc, Wq, split3 ? Wql : nullptr);
+    k_solve_st<<<grid, 256, kSolveSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Gred, f->tau + J, nbo, nc, Wq,
+                                             split3 ? Wql : nullptr);
     CT_LAUNCH_CHECK();
   }
   // C -= V W'  (A = V stored row-major: kNB x mr column-major with ld kNB),

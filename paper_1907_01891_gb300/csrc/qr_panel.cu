@@ -49,10 +49,27 @@ struct PanelArgs {
   double* T;             // nbp x nbp, leading dimension ldt
   int ldt;
   double* col_part;      // [2][grid][2*kMaxNb]
-  double* gram_part;     // [grid][kMaxNb*(kMaxNb-1)/2]
+  double* gram_part;     // [grid][kGramStride] partial Gram matrices, then the reduced one
   unsigned long long* bar;  // [0] grid-barrier counter, [1] finish counter
   int* status;
+  int row0;              // rows held by CTA 0 (the panel's top nbp rows), the
+                         // others rp each after them; 0: rp rows per CTA from row 0
 };
+
+// First panel row and row count of CTA b.
+__device__ __forceinline__ void cta_rows(const PanelArgs& a, int b, int64_t& rb, int& nr) {
+  int64_t n64;
+  if (a.row0 > 0) {
+    rb = b == 0 ? 0 : a.row0 + (int64_t)(b - 1) * a.rp;
+    const int cap = b == 0 ? a.row0 : a.rp;
+    n64 = a.mr - rb;
+    nr = n64 <= 0 ? 0 : (n64 < cap ? (int)n64 : cap);
+  } else {
+    rb = (int64_t)b * a.rp;
+    n64 = a.mr - rb;
+    nr = n64 <= 0 ? 0 : (n64 < a.rp ? (int)n64 : a.rp);
+  }
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -80,9 +97,9 @@ __device__ void panel_householder(const PanelArgs& a, Mth* slab, double* small, 
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbp = a.nbp, rp = a.rp;
-  const int64_t rb = (int64_t)blockIdx.x * rp;      // first panel row of this CTA
-  int64_t nr64 = a.mr - rb;
-  const int nr = nr64 <= 0 ? 0 : (nr64 < rp ? (int)nr64 : rp);
+  int64_t rb;                                       // first panel row of this CTA
+  int nr;
+  cta_rows(a, blockIdx.x, rb, nr);
   S* P = (S*)a.P;
   for (int k = 0; k < nbp; ++k) {
     const int ne = nbp - k;                          // columns k..nbp-1
@@ -242,9 +259,9 @@ __global__ void __launch_bounds__(kPT, 1) k_panel(PanelArgs a) {
   double* small = smem;
   Mth* slab = (Mth*)(small + kSmallDoubles) + kMaxNb;  // after the kMaxNb Mth values of w
   const int tid = threadIdx.x;
-  const int64_t rb = (int64_t)blockIdx.x * a.rp;
-  const int64_t nr64 = a.mr - rb;
-  const int nr = nr64 <= 0 ? 0 : (nr64 < a.rp ? (int)nr64 : a.rp);
+  int64_t rb;
+  int nr;
+  cta_rows(a, blockIdx.x, rb, nr);
   const S* P = (const S*)a.P;
   for (int c = 0; c < a.nbp; ++c)
     for (int r = tid; r < nr; r += kPT) slab[(size_t)c * a.rp + r] = (Mth)P[rb + r + c * a.ld];
@@ -285,43 +302,155 @@ __device__ __forceinline__ void tri_index(int e, int& i, int& j) {
   i = e - jj * (jj + 1) / 2;
 }
 
+__host__ __device__ inline int pow2_at_least(int n) {
+  int p = 1;
+  while (p < n) p *= 2;
+  return p;
+}
+
+// X = A^{-1} for the upper triangular n x n matrix a(i, j) (i <= j), in P x P
+// shared storage with leading dimension P (P a power of two >= n; rows and
+// columns >= n act as the identity).  Block doubling: the diagonal
+// reciprocals, then for s = 1, 2, 4, ... and every pair of diagonal blocks
+// A = [p, p+s), C = [p+s, p+2s): X_AC = -X_A (a_AC X_C).  Each step is a pair
+// of small products spread over all threads (no long serial chains, which
+// GB300's FP64 pipe makes expensive).  tmp: P x P scratch.
+template <typename Acc>
+__device__ void tri_inv_upper(Acc a, double* X, double* tmp, int n, int P) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < P * P; e += kPT) {
+    const int i = e % P, j = e / P;
+    X[e] = i == j ? (i < n ? 1.0 / a(i, i) : 1.0) : 0.0;
+  }
+  __syncthreads();
+  for (int s = 1; s < P; s *= 2) {
+    const int ent = (P / (2 * s)) * s * s;
+    for (int e = tid; e < ent; e += kPT) {
+      const int pr = e / (s * s), rr = e % (s * s), r = rr % s, c = rr / s;
+      const int p0 = pr * 2 * s, gi = p0 + r, gc = p0 + s + c;
+      double acc = 0.0;
+      for (int k = 0; k <= c; ++k) {  // X_C is upper triangular
+        const int gk = p0 + s + k;
+        if (gi < n && gk < n) acc += a(gi, gk) * X[gk + gc * P];
+      }
+      tmp[gi + gc * P] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ent; e += kPT) {
+      const int pr = e / (s * s), rr = e % (s * s), r = rr % s, c = rr / s;
+      const int p0 = pr * 2 * s, gi = p0 + r, gc = p0 + s + c;
+      double acc = 0.0;
+      for (int k = r; k < s; ++k) acc += X[gi + (p0 + k) * P] * tmp[(p0 + k) + gc * P];  // X_A upper
+      X[gi + gc * P] = -acc;
+    }
+    __syncthreads();
+  }
+}
+
+// 1/sqrt(d) and 1/x in FP64 from an FP32 seed refined by two Newton-Raphson
+// steps (y <- y (3 - d y^2) / 2 and y <- y (2 - x y)); the seed's relative
+// error ~1e-7 squares at every step, so the result is within a few FP64 ulps.
+// A few FP64 instructions instead of a full-precision square root or
+// division: on GB300 every FP64 instruction of a single thread costs the
+// FP64 pipe the time of a whole warp.  Outside the FP32 range the exact
+// operations are used.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double y = (double)(1.0f / (float)x);
+  y = y * (2.0 - x * y);
+  y = y * (2.0 - x * y);
+  return y;
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   extern __shared__ double smem[];
   const int nbp = a.nbp, rp = a.rp, tid = threadIdx.x;
-  const int nn = nbp * nbp;
+  const int P = pow2_at_least(nbp);           // leading dimension of the small matrices
+  const int nn = P * P;
   double* slab = smem;                        // [nbp][rp] this CTA's rows
   double* G = slab + (size_t)nbp * rp;        // Gram, then R1 in its upper part
-  double* Ri = G + nn;                        // R1^{-1} (upper)
+  double* Ri = G + nn;                        // R1^{-1} (upper), later T
   double* W = Ri + nn;                        // P1, then Q1 - S -> L1 (strict lower) / U (upper)
-  double* M = W + nn;                         // U R1 (upper)
-  double* X = M + nn;                         // L1^{-1}, then T
-  double* sv = X + nn;                        // [nbp] s_i
-  double* dv = sv + nbp;                      // [nbp] 1 / M_jj, column sums
+  double* M = W + nn;                         // scratch, then M^{-1} = R1^{-1} U^{-1}
+  double* X = M + nn;                         // scratch / U^{-1} / (L1^T)^{-1}
+  double* sv = X + nn;                        // [P] s_i
+  double* dv = sv + P;                        // [P] column sums
   __shared__ int s_ok;
-  const int64_t rb = (int64_t)blockIdx.x * rp;
-  const int64_t nr64 = a.mr - rb;
-  const int nr = nr64 <= 0 ? 0 : (nr64 < rp ? (int)nr64 : rp);
-  S* P = (S*)a.P;
+  int64_t rb;
+  int nr;
+  cta_rows(a, blockIdx.x, rb, nr);
+  S* P_ = (S*)a.P;
 
-  for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < nr; r += kPT) slab[(size_t)c * rp + r] = (double)P[rb + r + c * a.ld];
+  // the slab, eight columns' loads in flight per thread
+  for (int r = tid; r < nr; r += kPT) {
+    const S* src = P_ + rb + r;
+    int c = 0;
+    for (; c + 8 <= nbp; c += 8) {
+      S v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = src[(int64_t)(c + u) * a.ld];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) slab[(size_t)(c + u) * rp + r] = (double)v[u];
+    }
+    for (; c < nbp; ++c) slab[(size_t)c * rp + r] = (double)src[(int64_t)c * a.ld];
+  }
   // the top nbp rows of the panel (held by CTA 0, read by all before CTA 0
   // can overwrite them, i.e. before the second barrier)
-  for (int e = tid; e < nn; e += kPT) W[e] = (double)P[(e % nbp) + (int64_t)(e / nbp) * a.ld];
+  for (int e = tid; e < nbp * nbp; e += kPT) {
+    const int r = e % nbp, c = e / nbp;
+    W[r + c * P] = (double)P_[r + (int64_t)c * a.ld];
+  }
   __syncthreads();
 
   // 1. This CTA's share of the upper Gram matrix, packed.
   const int ng = nbp * (nbp + 1) / 2;
   double* gp = a.gram_part + (size_t)blockIdx.x * kGramStride;
-  for (int e = tid; e < ng; e += kPT) {
+  // whole rounds of kPT entries, one thread per entry; the remaining entries
+  // (if few) with g threads per entry over interleaved rows, so that no
+  // round runs on a handful of threads
+  const int full = (ng / kPT) * kPT, rem = ng - full;
+  int g = 1;
+  while (rem > 0 && g < 32 && rem * g * 2 <= kPT) g *= 2;
+  const int split_from = g > 1 ? full : ng;
+  for (int e = tid; e < split_from; e += kPT) {
     int i, j;
     tri_index(e, i, j);
     const double* ci = slab + (size_t)i * rp;
     const double* cj = slab + (size_t)j * rp;
+    double s0 = 0.0, s1 = 0.0;
+    int r = 0;
+    for (; r + 1 < nr; r += 2) {
+      s0 += ci[r] * cj[r];
+      s1 += ci[r + 1] * cj[r + 1];
+    }
+    if (r < nr) s0 += ci[r] * cj[r];
+    gp[e] = s0 + s1;
+  }
+  // rem * g <= kPT; g is a power of two <= 32, so the groups of g lanes never
+  // straddle a warp; whole warps take part in the shuffles
+  if (g > 1 && tid < (rem * g + 31) / 32 * 32) {
+    const bool act = tid < rem * g;
+    const int e = full + tid / g, part = tid % g;
     double s = 0.0;
-    for (int r = 0; r < nr; ++r) s += ci[r] * cj[r];
-    gp[e] = s;
+    if (act) {
+      int i, j;
+      tri_index(e, i, j);
+      const double* ci = slab + (size_t)i * rp;
+      const double* cj = slab + (size_t)j * rp;
+      for (int r = part; r < nr; r += g) s += ci[r] * cj[r];
+    }
+    for (int o = g / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
+    if (act && part == 0) gp[e] = s;
   }
   if (!grid_barrier(&a.bar[0], a.grid, a.status, kBarrierLimitNs)) return;
   // Split reduction: CTA c sums entries [c ng / grid, (c+1) ng / grid) over
@@ -339,62 +468,62 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   }
   if (!grid_barrier(&a.bar[0], a.grid, a.status, kBarrierLimitNs)) return;
 
-  // 2. Every CTA: the full Gram matrix, its Cholesky factor R1 (upper, in G).
+  // 2. Every CTA: the full Gram matrix (identity outside nbp), its Cholesky
+  //    factor R1 (upper, in G; one reciprocal per pivot).
+  for (int e = tid; e < nn; e += kPT) {
+    const int i = e % P, j = e / P;
+    G[e] = (i >= nbp || j >= nbp) ? (i == j ? 1.0 : 0.0) : 0.0;
+  }
+  __syncthreads();
   for (int e = tid; e < ng; e += kPT) {
     int i, j;
     tri_index(e, i, j);
     const double v = __ldcg(gred + e);
-    G[i + j * nbp] = v;
-    G[j + i * nbp] = v;
+    G[i + j * P] = v;
+    G[j + i * P] = v;
   }
   if (tid == 0) s_ok = 1;
   __syncthreads();
   for (int k = 0; k < nbp; ++k) {
     if (tid == 0) {
-      const double d = G[k + k * nbp];
+      const double d = G[k + k * P];
       if (!(d > 0.0) || !isfinite(d)) s_ok = 0;
-      G[k + k * nbp] = s_ok ? sqrt(d) : 1.0;
+      const double y = s_ok ? rsqrt_nr(d) : 1.0;  // 1 / sqrt(d)
+      G[k + k * P] = s_ok ? d * y : 1.0;
+      dv[0] = y;
     }
     __syncthreads();
-    const double rkk = G[k + k * nbp];
-    for (int j = k + 1 + tid; j < nbp; j += kPT) G[k + j * nbp] /= rkk;
+    const double rinv = dv[0];
+    for (int j = k + 1 + tid; j < nbp; j += kPT) G[k + j * P] *= rinv;
     __syncthreads();
     const int w = nbp - k - 1;  // trailing block (k+1..nbp-1)^2, upper part
     for (int e = tid; e < w * w; e += kPT) {
       const int i = k + 1 + e % w, j = k + 1 + e / w;
-      if (i <= j) G[i + j * nbp] -= G[k + i * nbp] * G[k + j * nbp];
+      if (i <= j) G[i + j * P] -= G[k + i * P] * G[k + j * P];
     }
     __syncthreads();
   }
-  // R1^{-1}: column j solved by thread j (back substitution)
-  for (int j = tid; j < nbp; j += kPT) {
-    for (int i = 0; i < nbp; ++i) Ri[i + j * nbp] = 0.0;
-    Ri[j + j * nbp] = 1.0 / G[j + j * nbp];
-    for (int i = j - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s += G[i + k * nbp] * Ri[k + j * nbp];
-      Ri[i + j * nbp] = -s / G[i + i * nbp];
+  // R1^{-1} and kappa_1(R1) = ||R1||_1 ||R1^{-1}||_1
+  tri_inv_upper(
+      [&](int i, int j) { return G[i + j * P]; }, Ri, M, nbp, P);
+  // (an estimate: FP32 sums of the FP64 entries suffice)
+  if (tid < 32) {
+    float n1 = 0.f, n2 = 0.f;
+    for (int j = tid; j < nbp; j += 32) {
+      float s1 = 0.f, s2 = 0.f;
+      for (int i = 0; i <= j; ++i) {
+        s1 += fabsf((float)G[i + j * P]);
+        s2 += fabsf((float)Ri[i + j * P]);
+      }
+      n1 = fmaxf(n1, s1);
+      n2 = fmaxf(n2, s2);
     }
-  }
-  __syncthreads();
-  // kappa_1(R1) = ||R1||_1 ||R1^{-1}||_1
-  if (tid < nbp) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i <= tid; ++i) {
-      s1 += fabs(G[i + tid * nbp]);
-      s2 += fabs(Ri[i + tid * nbp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n1 = fmaxf(n1, __shfl_xor_sync(0xffffffffu, n1, o));
+      n2 = fmaxf(n2, __shfl_xor_sync(0xffffffffu, n2, o));
     }
-    dv[tid] = s1;
-    sv[tid] = s2;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double n1 = 0.0, n2 = 0.0;
-    for (int j = 0; j < nbp; ++j) {
-      n1 = fmax(n1, dv[j]);
-      n2 = fmax(n2, sv[j]);
-    }
-    if (!(n1 * n2 <= kCqrMaxCond)) s_ok = 0;
+    if (tid == 0 && !(n1 * n2 <= (float)kCqrMaxCond)) s_ok = 0;
   }
   __syncthreads();
   if (!s_ok) {
@@ -403,92 +532,91 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
     return;
   }
 
-  // 3. Q1 = P1 R1^{-1} (in W), then the modified LU of Q1 - S in place.
-  for (int e = tid; e < nn; e += kPT) {
+  // 3. Q1 = P1 R1^{-1} (into M, then W), then the modified LU of Q1 - S in
+  //    place (one reciprocal per pivot).
+  for (int e = tid; e < nbp * nbp; e += kPT) {
     const int r = e % nbp, j = e / nbp;
     double s = 0.0;
-    for (int k = 0; k <= j; ++k) s += W[r + k * nbp] * Ri[k + j * nbp];
-    X[e] = s;
+    for (int k = 0; k <= j; ++k) s += W[r + k * P] * Ri[k + j * P];
+    M[r + j * P] = s;
   }
   __syncthreads();
-  for (int e = tid; e < nn; e += kPT) W[e] = X[e];
+  for (int e = tid; e < nbp * nbp; e += kPT) {
+    const int r = e % nbp, j = e / nbp;
+    W[r + j * P] = M[r + j * P];
+  }
   __syncthreads();
   for (int i = 0; i < nbp; ++i) {
     if (tid == 0) {
-      const double q = W[i + i * nbp];
+      const double q = W[i + i * P];
       const double si = q >= 0.0 ? -1.0 : 1.0;
       sv[i] = si;
-      W[i + i * nbp] = q - si;  // |pivot| >= 1
+      W[i + i * P] = q - si;  // |pivot| >= 1
+      dv[0] = rcp_nr(q - si);
     }
     __syncthreads();
-    const double piv = W[i + i * nbp];
-    for (int r = i + 1 + tid; r < nbp; r += kPT) W[r + i * nbp] /= piv;
+    const double pinv = dv[0];
+    for (int r = i + 1 + tid; r < nbp; r += kPT) W[r + i * P] *= pinv;
     __syncthreads();
     const int w = nbp - i - 1;
     for (int e = tid; e < w * w; e += kPT) {
       const int r = i + 1 + e % w, c = i + 1 + e / w;
-      W[r + c * nbp] -= W[r + i * nbp] * W[i + c * nbp];
+      W[r + c * P] -= W[r + i * P] * W[i + c * P];
     }
     __syncthreads();
   }
-  // M = U R1 (upper) and 1 / M_jj
-  for (int e = tid; e < nn; e += kPT) {
+  // U^{-1} (into X), then M^{-1} = (U R1)^{-1} = R1^{-1} U^{-1} (into M)
+  tri_inv_upper(
+      [&](int i, int j) { return W[i + j * P]; }, X, M, nbp, P);
+  for (int e = tid; e < nbp * nbp; e += kPT) {
     const int i = e % nbp, j = e / nbp;
     double s = 0.0;
     if (i <= j)
-      for (int k = i; k <= j; ++k) s += W[i + k * nbp] * G[k + j * nbp];
-    M[e] = s;
+      for (int k = i; k <= j; ++k) s += Ri[i + k * P] * X[k + j * P];
+    M[i + j * P] = s;
   }
   __syncthreads();
-  if (tid < nbp) dv[tid] = 1.0 / M[tid + tid * nbp];
-  __syncthreads();
 
-  // 4. This CTA's rows: V2 = P2 M^{-1} (rows with panel index >= nbp); the top
-  //    nbp rows (CTA 0) become R = S R1 on/above and L1 below the diagonal.
+  // 4. This CTA's rows: V2 = P2 M^{-1} (rows with panel index >= nbp, columns
+  //    from the last so that each row is updated in place); the top nbp rows
+  //    (CTA 0) become R = S R1 on/above and L1 below the diagonal.
   for (int r = tid; r < nr; r += kPT) {
     const int64_t gr = rb + r;
     if (gr >= nbp) {
-      for (int j = 0; j < nbp; ++j) {
-        double s = slab[(size_t)j * rp + r];
-        for (int i = 0; i < j; ++i) s -= slab[(size_t)i * rp + r] * M[i + j * nbp];
-        slab[(size_t)j * rp + r] = s * dv[j];
+      for (int j = nbp - 1; j >= 0; --j) {
+        double s = 0.0;
+        for (int i = 0; i <= j; ++i) s += slab[(size_t)i * rp + r] * M[i + j * P];
+        slab[(size_t)j * rp + r] = s;
       }
     } else {
       const int i = (int)gr;
       for (int j = 0; j < nbp; ++j)
-        slab[(size_t)j * rp + r] = j >= i ? sv[i] * G[i + j * nbp] : W[i + j * nbp];
+        slab[(size_t)j * rp + r] = j >= i ? sv[i] * G[i + j * P] : W[i + j * P];
     }
   }
   __syncthreads();
   for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < nr; r += kPT) P[rb + r + c * a.ld] = (S)slab[(size_t)c * rp + r];
+    for (int r = tid; r < nr; r += kPT) P_[rb + r + c * a.ld] = (S)slab[(size_t)c * rp + r];
 
-  // 5. CTA 0: T = -U S L1^{-T} and tau = diag(T).
+  // 5. CTA 0 (which holds only the top rows, so it has no row solves):
+  //    T = -U S L1^{-T} and tau = diag(T).  L1^{-T} is the inverse of the
+  //    unit upper triangular L1^T.
   if (blockIdx.x != 0) return;
-  // L1^{-1} (unit lower): column j by thread j, forward substitution
-  for (int j = tid; j < nbp; j += kPT) {
-    for (int i = 0; i < nbp; ++i) X[i + j * nbp] = i == j ? 1.0 : 0.0;
-    for (int i = j + 1; i < nbp; ++i) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s += W[i + k * nbp] * X[k + j * nbp];
-      X[i + j * nbp] = -s;
-    }
-  }
-  __syncthreads();
-  // T_ij = -sum_{k=i..j} U_ik s_k (L1^{-1})_jk, i <= j (into Ri, free now)
-  for (int e = tid; e < nn; e += kPT) {
+  tri_inv_upper(
+      [&](int i, int j) { return i == j ? 1.0 : W[j + i * P]; }, X, M, nbp, P);
+  for (int e = tid; e < nbp * nbp; e += kPT) {
     const int i = e % nbp, j = e / nbp;
     double s = 0.0;
     if (i <= j)
-      for (int k = i; k <= j; ++k) s += W[i + k * nbp] * sv[k] * X[j + k * nbp];
-    Ri[e] = i <= j ? -s : 0.0;
+      for (int k = i; k <= j; ++k) s += W[i + k * P] * sv[k] * X[k + j * P];
+    Ri[i + j * P] = i <= j ? -s : 0.0;
   }
   __syncthreads();
-  for (int e = tid; e < nn; e += kPT) {
+  for (int e = tid; e < nbp * nbp; e += kPT) {
     const int i = e % nbp, j = e / nbp;
-    a.T[i + (size_t)j * a.ldt] = Ri[e];
+    a.T[i + (size_t)j * a.ldt] = Ri[i + j * P];
   }
-  for (int i = tid; i < nbp; i += kPT) a.tau[i] = Ri[i + i * nbp];
+  for (int i = tid; i < nbp; i += kPT) a.tau[i] = Ri[i + i * P];
 }
 
 // CTAs for an mr-row panel: about 64 rows each, at most one per SM (measured:
@@ -503,7 +631,8 @@ int panel_grid(int64_t mr, const DeviceInfo& di, size_t mth) {
 }
 
 size_t panel_cqr_smem_bytes(int nbp, int rp) {
-  size_t bytes = ((size_t)nbp * rp + 5 * (size_t)nbp * nbp + 2 * nbp) * sizeof(double);
+  const size_t P = (size_t)pow2_at_least(nbp);
+  size_t bytes = ((size_t)nbp * rp + 5 * P * P + 2 * P) * sizeof(double);
   // the Householder fallback: its buffers in place of G.., T at the start
   const size_t fb = ((size_t)nbp * rp + kSmallDoubles + kMaxNb) * sizeof(double);
   const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
@@ -537,7 +666,18 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   // dynamic shared memory may use the opt-in limit minus the kernels' few
   // bytes of static shared memory
   const size_t limit = (size_t)di.smem_optin - kStaticSmemReserve;
-  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp && panel_cqr_smem_bytes(nbp, rp) <= limit;
+  // Cholesky-QR: CTA 0 holds only the top nbp rows (it forms T while the
+  // others solve their rows), the other CTAs the rest in equal parts
+  int row0 = 0, rp_c = rp;
+  if (grid >= 2 && mr > nbp) {
+    rp_c = (int)((mr - nbp + grid - 2) / (grid - 1));
+    if (rp_c < nbp) rp_c = nbp;
+  }
+  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp && panel_cqr_smem_bytes(nbp, rp_c) <= limit;
+  if (cqr) {
+    if (grid >= 2 && mr > nbp) row0 = nbp;
+    rp = rp_c;
+  }
   const void* fn = cqr ? (const void*)k_panel_cqr<S> : (const void*)k_panel<S, Mth>;
   const size_t smem = cqr ? panel_cqr_smem_bytes(nbp, rp) : panel_smem_bytes(nbp, rp, sizeof(Mth));
   if (smem > limit) return CT_ERR_UNSUPPORTED;
@@ -554,11 +694,12 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   a.nbp = nbp;
   a.rp = rp;
   a.grid = grid;
+  a.row0 = row0;
   a.tau = f->tau + j0;
   a.T = T;
   a.ldt = f->nb;
   a.col_part = f->partials;
-  a.gram_part = f->partials + (size_t)2 * di.sms * 2 * kMaxNb;
+  a.gram_part = f->partials + (size_t)2 * (di.sms + 1) * 2 * kMaxNb;
   a.bar = f->barrier;
   a.status = f->status;
   CT_CUDA_TRY(cudaMemsetAsync(f->barrier, 0, 2 * sizeof(unsigned long long), s));
@@ -572,9 +713,9 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
 
 size_t panel_partials_elems(int sms, int nb) {
   (void)nb;
-  // column partials [2][sms][2*kMaxNb]; per-CTA Gram partials (and the
-  // reduced Gram of the Cholesky-QR panel after them)
-  return (size_t)2 * sms * 2 * kMaxNb + (size_t)(sms + 1) * kGramStride;
+  // column partials [2][sms + 1][2*kMaxNb]; per-CTA Gram partials for up to
+  // sms + 1 CTAs and the reduced Gram of the Cholesky-QR panel after them
+  return (size_t)2 * (sms + 1) * 2 * kMaxNb + (size_t)(sms + 2) * kGramStride;
 }
 
 // Largest panel width <= want (halving when pow2) whose shared-memory slab

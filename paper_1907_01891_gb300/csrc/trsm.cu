@@ -433,16 +433,17 @@ ct_status trsm_persist(const ct_factor* f, float* B, int64_t ldb, int64_t k, boo
 
 // B[0:n, 0:k] <- R^{-1} B[0:n, 0:k]; B is FP64 (b_f64) or FP32.  FP64 B is
 // solved in FP64 arithmetic whatever R's storage type; FP32 B (the
-// preconditioner solves of the mixed-precision refinement) in FP32, in one
-// persistent launch per 64 columns (CTQR_TRSM_RECURSIVE=1: the recursive
-// scheme below).  Recursive halving: 64 x 64 diagonal solves (Trsm_lunn) at
+// preconditioner solves of the mixed-precision refinement) in FP32: up to 64
+// columns in one persistent launch (its block-row chain is latency-bound, so
+// wider right-hand sides go to the recursive scheme below, whose products
+// grow with k; CTQR_TRSM_RECURSIVE=1 always uses the recursive scheme).  Recursive halving: 64 x 64 diagonal solves (Trsm_lunn) at
 // the leaves and one product per split for the block above (Gemm_nn_mo), so
 // the products are few and large instead of one K = 64 update per block
 // column.
 ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
   if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
-  if (!b_f64 && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, false, s);
+  if (!b_f64 && k <= kPB && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, false, s);
   const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
   return solve_rec(c, 0, f->n);
 }
@@ -451,7 +452,7 @@ ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int6
 ct_status launch_trsm_t(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
   if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
-  if (!b_f64 && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, true, s);
+  if (!b_f64 && k <= kPB && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, true, s);
   const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
   return solve_rec_t(c, 0, f->n);
 }

@@ -370,3 +370,27 @@ def test_fp32_triangular_solve_matches_oracle(n, k, transpose):
         ref = O.backsolve(np.asfortranarray(R), np.asfortranarray(Y.astype(np.float64)))
     err = np.linalg.norm(X - ref) / np.linalg.norm(ref)
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("shape,k", [((700, 300), 3), ((1200, 520), 17)])
+def test_tf32_factor_qt_by_outer_blocks(shape, k):
+    """Q^T of a two-level TF32 factor is applied by 128-column outer blocks
+    (the block reflector through S = diag(1/tau) + striu(V^T V)); it matches
+    the oracle's Q^T to the factor's FP32-level accuracy, and the per-panel
+    application (the allocation-free entry point, k <= 64) to the same level."""
+    m, n = shape
+    A = I.random_matrix(m, n, seed=90 + n)
+    B = I.random_matrix(m, k, seed=91 + n)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A, dtype=torch.float32), prec=ctqr.Prec.TF32)
+    Y = _np(ctqr.apply_qt(f, ctqr.to_colmajor(B)))
+    Yp = _np(ctqr.apply_qt_noalloc(f, ctqr.to_colmajor(B)))
+    Fo, tau = O.qr(A)
+    Yo = O.apply_qt(Fo, tau, B)
+    # rows of Q^T B are fixed up to the sign of each reflector's R_ii: compare
+    # with the signs of the two R diagonals aligned
+    F, _ = ctqr.factor_matrix(f)
+    sgn = np.sign(np.diag(_np(F).astype(np.float64)[:n])) * np.sign(np.diag(Fo[:n]))
+    Yo_top = Yo[:n] * sgn[:, None]
+    assert np.linalg.norm(Y[:n] - Yo_top) <= 1e-4 * np.linalg.norm(Yo_top)
+    assert np.linalg.norm(Y - Yp) <= 1e-5 * np.linalg.norm(Y)
+    assert abs(np.linalg.norm(Y) - np.linalg.norm(B)) <= 1e-5 * np.linalg.norm(B)  # orthogonal invariance
