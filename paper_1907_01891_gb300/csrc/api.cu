@@ -612,16 +612,56 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
     const size_t owf = outer_work_floats(di.sms, m, n);
     Scratch owork;
     if ((st = owork.alloc(owf * sizeof(float), s)) != CT_OK) { free_factor(f); return st; }
+    // Look-ahead (opt-in, CTQR_LOOKAHEAD=1): while the columns beyond the
+    // next outer block are updated on a second stream (on all but kReserve
+    // SMs), the next block's panels and inner updates run on the reserved
+    // SMs, when those panels fit on kReserve CTAs.  Measured on the 128x128
+    // fan-beam system it is slower (the panels on 24 CTAs beside the
+    // bandwidth-bound update take 425 instead of 150 us), so it is off by
+    // default.  The guard below makes s wait for a deferred update on every
+    // exit, before owork is released.
+    constexpr int kReserve = 24;
+    Lookahead la;
+    la.reserve = kReserve;
+    struct LaGuard {
+      Lookahead* la;
+      cudaStream_t s;
+      ~LaGuard() {
+        if (la->rest_pending) cudaStreamWaitEvent(s, la->ev_rest, 0);
+        if (la->ev_w) cudaEventDestroy(la->ev_w);
+        if (la->ev_rest) cudaEventDestroy(la->ev_rest);
+        if (la->s2) cudaStreamDestroy(la->s2);
+      }
+    } la_guard{&la, s};
+    const char* la_env = getenv("CTQR_LOOKAHEAD");
+    const bool la_on = la_env && *la_env == '1' && di.sms > 2 * kReserve;
+    if (la_on) {
+      if (cudaStreamCreateWithFlags(&la.s2, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&la.ev_w, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&la.ev_rest, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_factor(f);
+        return CT_ERR_CUDA;
+      }
+    }
     for (int64_t J = 0; J < n; J += 128) {
       const int nbo = (int)(n - J < 128 ? n - J : 128);
+      // this block's panels run beside the previous block's deferred update
+      f->panel_cap = la.rest_pending ? kReserve : 0;
       for (int64_t j0 = J; j0 < J + nbo; j0 += f->nb) {
         const int nbp = (int)(J + nbo - j0 < f->nb ? J + nbo - j0 : f->nb);
         if ((st = panel_step(j0, nbp, J + nbo)) != CT_OK) { free_factor(f); return st; }
       }
-      if ((st = outer_block_update(f, J, nbo, (float*)owork.p, owf, di.sms, passes == 3, s)) != CT_OK) {
+      f->panel_cap = 0;
+      la.defer = la_on && J + 256 < n && panel_fits_ctas(m - (J + 128), f->nb, kReserve, di);
+      if ((st = outer_block_update(f, J, nbo, (float*)owork.p, owf, di.sms, passes == 3, s, &la)) != CT_OK) {
         free_factor(f);
         return st;
       }
+    }
+    if (la.rest_pending) {
+      CT_CUDA_TRY(cudaStreamWaitEvent(s, la.ev_rest, 0));
+      la.rest_pending = false;
     }
   }
   st = launch_rank_check(f, s);

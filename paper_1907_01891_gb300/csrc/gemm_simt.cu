@@ -214,6 +214,9 @@ __global__ void __launch_bounds__(kGT) k_solve_blk(const double* __restrict__ pa
 }
 
 // C(r, c) -= sum_{a < K} V(r, a) W(a, c); 64 x BN tile per CTA, any K.
+// Thread (ty = tid % 16, tx = tid / 16) owns rows r0 + ty + 16 i (i < 4) and
+// columns c0 + tx * TN + j, so a warp's accesses to C cover 16 consecutive
+// rows of two columns (coalesced, C is column-major).
 template <typename TV, typename TW, typename TC, typename Acc, int BN>
 __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_t ldv, int K,
                                                  bool mask, const TW* __restrict__ W,
@@ -222,8 +225,19 @@ __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_
   constexpr int TN = BN / 16;
   __shared__ Acc Vs[kBK][kBM + 1];
   __shared__ Acc Ws[kBK][BN + 1];
-  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int tid = threadIdx.x, ty = tid % 16, tx = tid / 16;
   const int64_t r0 = (int64_t)blockIdx.x * kBM, c0 = (int64_t)blockIdx.y * BN;
+  // this thread's C values, loaded first so their latency overlaps the product
+  TC cin[4][TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t cg = c0 + tx * TN + j;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + ty + 16 * i;
+      cin[i][j] = (r < mr && cg < nc) ? C[r + cg * ldc] : (TC)0;
+    }
+  }
   Acc acc[4][TN];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_
     for (int kk = 0; kk < kBK; ++kk) {
       Acc av[4], wv[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty * 4 + i];
+      for (int i = 0; i < 4; ++i) av[i] = Vs[kk][ty + 16 * i];
 #pragma unroll
       for (int j = 0; j < TN; ++j) wv[j] = Ws[kk][tx * TN + j];
 #pragma unroll
@@ -265,8 +279,8 @@ __global__ void __launch_bounds__(kGT) k_update(const TV* __restrict__ V, int64_
     if (cg >= nc) continue;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int64_t r = r0 + ty * 4 + i;
-      if (r < mr) C[r + cg * ldc] = (TC)((Acc)C[r + cg * ldc] - acc[i][j]);
+      const int64_t r = r0 + ty + 16 * i;
+      if (r < mr) C[r + cg * ldc] = (TC)((Acc)cin[i][j] - acc[i][j]);
     }
   }
 }
@@ -403,9 +417,13 @@ template <typename TV, typename TC, typename Acc, int BN>
 ct_status run_reflector(const ReflectorArgs& a, double* work, size_t work_elems, int sms,
                         cudaStream_t s) {
   const int64_t tiles_n = (a.nc + BN - 1) / BN;
-  int64_t splits = (2 * sms + tiles_n - 1) / tiles_n;
-  const int64_t max_splits = (a.mr + 255) / 256;
+  // split-K over rows: about four CTAs per SM, chunks of at least 64 rows,
+  // and the partials must fit the work area
+  int64_t splits = (4 * sms + tiles_n - 1) / tiles_n;
+  const int64_t max_splits = (a.mr + 63) / 64;
   if (splits > max_splits) splits = max_splits;
+  const int64_t fit = (int64_t)(work_elems / ((size_t)kBM * a.nc)) - 1;
+  if (splits > fit) splits = fit;
   if (a.max_splits > 0 && splits > a.max_splits) splits = a.max_splits;
   if (splits < 1) splits = 1;
   int64_t chunk = (a.mr + splits - 1) / splits;

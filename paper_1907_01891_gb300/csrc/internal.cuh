@@ -138,6 +138,7 @@ struct ct_factor {
   unsigned long long* barrier = nullptr;  // grid-barrier counter
   double* partials = nullptr;   // panel-kernel reduction scratch
   size_t partials_elems = 0;
+  int panel_cap = 0;            // when > 0: at most this many CTAs per panel launch
   float* Gblk = nullptr;        // two-level factors: V^T V of every 128-column outer
                                 // block (128 x 128, strict upper part; blocks whose
                                 // update ran, i.e. all but the last)
@@ -199,8 +200,19 @@ int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth
 // reflector of F[J:m, J:J+nbo] (outer_update.cu); work holds
 // outer_work_floats(...) floats.
 size_t outer_work_floats(int sms, int64_t m, int64_t n);
+// Look-ahead: the update of the columns after the next outer block runs on
+// s2 (on all but `reserve` SMs) while the next block's panels run on s.
+struct Lookahead {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_w = nullptr, ev_rest = nullptr;
+  bool defer = false;         // defer the rest of this block's update
+  bool rest_pending = false;  // a deferred update is in flight (ev_rest recorded)
+  int reserve = 0;
+};
 ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
-                             bool split3, cudaStream_t s);
+                             bool split3, cudaStream_t s, Lookahead* la = nullptr);
+// Whether a panel of mr rows and nbp columns fits on `ctas` CTAs (qr_panel.cu).
+bool panel_fits_ctas(int64_t mr, int nbp, int ctas, const DeviceInfo& di);
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
                              cudaStream_t s);
 ct_status launch_rank_check(ct_factor* f, cudaStream_t s);

@@ -157,8 +157,13 @@ size_t outer_work_floats(int sms, int64_t m, int64_t n) {
 
 // Update C = F[J:m, J+nbo:n] with the block reflector of F[J:m, J:J+nbo].
 ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
-                             bool split3, cudaStream_t s) {
+                             bool split3, cudaStream_t s, Lookahead* la) {
   const int64_t m = f->m, n = f->n, mr = m - J, nc = n - J - nbo;
+  // the previous block's deferred update must be done before C is read
+  if (la && la->rest_pending) {
+    CT_CUDA_TRY(cudaStreamWaitEvent(s, la->ev_rest, 0));
+    la->rest_pending = false;
+  }
   if (nc <= 0) return CT_OK;
   float* F = (float*)f->F;
   const int64_t ld = f->ld;
@@ -228,7 +233,22 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     CT_LAUNCH_CHECK();
   }
   // C -= V W'  (A = V stored row-major: kNB x mr column-major with ld kNB),
-  // persistent kernel on the pre-split operands.
+  // persistent kernel on the pre-split operands.  With look-ahead the next
+  // block's kNB columns are updated here and the rest on s2, on all but
+  // la->reserve SMs, while the next block's panels proceed on s.
+  if (la && la->defer && la->s2 && nc > kNB) {
+    if ((st = tc_update_presplit(Vr, Vrl, kNB, Wq, Wql, kNB, mr, kNB, kNB, C, ld, split3, sms, f->status, s)) !=
+        CT_OK)
+      return st;
+    CT_CUDA_TRY(cudaEventRecord(la->ev_w, s));
+    CT_CUDA_TRY(cudaStreamWaitEvent(la->s2, la->ev_w, 0));
+    st = tc_update_presplit(Vr, Vrl, kNB, Wq + (size_t)kNB * kNB, Wql + (size_t)kNB * kNB, kNB, mr, nc - kNB, kNB,
+                            C + (size_t)kNB * ld, ld, split3, sms - la->reserve, f->status, la->s2);
+    if (st != CT_OK) return st;
+    CT_CUDA_TRY(cudaEventRecord(la->ev_rest, la->s2));
+    la->rest_pending = true;
+    return CT_OK;
+  }
   return tc_update_presplit(Vr, Vrl, kNB, Wq, Wql, kNB, mr, nc, kNB, C, ld, split3, sms, f->status, s);
 }
 

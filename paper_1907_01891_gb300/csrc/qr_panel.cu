@@ -662,6 +662,7 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
                          const DeviceInfo& di) {
   const int64_t mr = f->m - j0;
   int grid = panel_grid(mr, di, sizeof(Mth));
+  if (f->panel_cap > 0 && grid > f->panel_cap) grid = f->panel_cap;
   int rp = (int)((mr + grid - 1) / grid);
   // dynamic shared memory may use the opt-in limit minus the kernels' few
   // bytes of static shared memory
@@ -727,6 +728,12 @@ int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth
   while (nb > 8 && panel_smem_bytes(nb, rp, mth) > (size_t)di.smem_optin - kStaticSmemReserve)
     nb = pow2 ? nb / 2 : nb - 8;
   return nb;
+}
+
+bool panel_fits_ctas(int64_t mr, int nbp, int ctas, const DeviceInfo& di) {
+  if (ctas < 1) return false;
+  const int rp = (int)((mr + ctas - 1) / ctas);
+  return panel_smem_bytes(nbp, rp, sizeof(float)) <= (size_t)di.smem_optin - kStaticSmemReserve;
 }
 
 ct_status launch_panel(ct_factor* f, int64_t j0, int nbp, double* T, cudaStream_t s) {

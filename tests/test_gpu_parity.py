@@ -394,3 +394,18 @@ def test_tf32_factor_qt_by_outer_blocks(shape, k):
     assert np.linalg.norm(Y[:n] - Yo_top) <= 1e-4 * np.linalg.norm(Yo_top)
     assert np.linalg.norm(Y - Yp) <= 1e-5 * np.linalg.norm(Y)
     assert abs(np.linalg.norm(Y) - np.linalg.norm(B)) <= 1e-5 * np.linalg.norm(B)  # orthogonal invariance
+
+
+def test_tf32_factor_with_lookahead_refines_to_fp64(monkeypatch):
+    """The opt-in look-ahead (deferred outer-block updates on a second stream
+    while the next panels run on reserved SMs) gives the same solution."""
+    monkeypatch.setenv("CTQR_LOOKAHEAD", "1")
+    m, n = 2100, 1000
+    A = I.random_matrix(m, n, seed=77)
+    At = ctqr.to_colmajor(A)
+    f = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32)
+    assert f.status() == ctqr.CT_OK
+    b = A @ I.random_matrix(n, 3, seed=78)
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=At)
+    Xo = O.lstsq(A, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
