@@ -108,9 +108,18 @@ __global__ void __launch_bounds__(kGT) k_tw(const double* __restrict__ part, int
   __shared__ Acc Ts[kBM][kBM + 1];  // T(b, a) at Ts[a][b]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c = blockIdx.x;
-  for (int e = tid; e < kBM * kBM; e += kGT) {
-    const int b = e % kBM, a = e / kBM;
-    Ts[a][b] = (a < nbp && b <= a) ? (Acc)T[b + (int64_t)a * ldt] : (Acc)0;
+  for (int e0 = tid; e0 < kBM * kBM; e0 += kGT * 4) {  // four loads in flight per thread
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + kGT * u, b = e % kBM, a = e / kBM;  // kBM * kBM is a multiple of 4 * kGT
+      v[u] = (a < nbp && b <= a) ? T[b + (int64_t)a * ldt] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + kGT * u, b = e % kBM, a = e / kBM;
+      Ts[a][b] = (Acc)v[u];
+    }
   }
   const double* base = part + (size_t)c * kBM;
   const size_t stride = (size_t)kBM * nc;
@@ -168,9 +177,15 @@ __global__ void __launch_bounds__(kGT) k_solve_blk(const double* __restrict__ pa
   __shared__ Acc ts[kOB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c = blockIdx.x;
-  for (int e = tid; e < kOB * kOB; e += kGT) {
-    const int i = e % kOB, r = e / kOB;
-    gs[i * (kOB + 1) + r] = G[e];
+  for (int e0 = tid; e0 < kOB * kOB; e0 += kGT * 8) {  // eight loads in flight per thread
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(G + e0 + kGT * u);  // kOB * kOB is a multiple of 8 * kGT
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + kGT * u, i = e % kOB, r = e / kOB;
+      gs[i * (kOB + 1) + r] = v[u];
+    }
   }
   for (int i = tid; i < kOB; i += kGT) ts[i] = i < nbo ? (Acc)tau[i] : (Acc)0;
   const double* base = part + (size_t)c * kOB;

@@ -93,9 +93,16 @@ __global__ void __launch_bounds__(256) k_solve_st(const float* __restrict__ Wp, 
   extern __shared__ float sm[];
   float* G = sm;              // G[i * kGS + r] = (V^T V)(i, r), strict upper part
   float* ts = sm + kNB * kGS;
-  for (int e = threadIdx.x; e < kNB * kNB; e += 256) {
-    const int i = e % kNB, r = e / kNB;
-    G[i * kGS + r] = __ldcg(Gred + e);
+  // stage G, eight loads in flight per thread
+  for (int e0 = threadIdx.x; e0 < kNB * kNB; e0 += 256 * 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(Gred + e0 + 256 * u);  // kNB * kNB is a multiple of 2048
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + 256 * u, i = e % kNB, r = e / kNB;
+      G[i * kGS + r] = v[u];
+    }
   }
   for (int i = threadIdx.x; i < kNB; i += 256) ts[i] = i < nbo ? (float)tau[i] : 0.f;
   __syncthreads();

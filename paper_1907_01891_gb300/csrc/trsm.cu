@@ -156,6 +156,34 @@ __device__ __forceinline__ void st_release_i32(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+template <int NC>
+__device__ __forceinline__ void block_product(float (*Rs)[kPB + 1], float (*Xs)[kPB + 1], float (*Ys)[kPB + 1],
+                                              int k, int tid) {
+  const int r4 = (tid % 16) * 4, cgp = tid / 16;
+  float acc[4][NC];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int w = 0; w < NC; ++w) acc[a][w] = 0.f;
+#pragma unroll 8
+  for (int l = 0; l < kPB; ++l) {
+    float rv[4], xv[NC];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rv[a] = Rs[r4 + a][l];
+#pragma unroll
+    for (int w = 0; w < NC; ++w) xv[w] = Xs[l][cgp + 16 * w];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int w = 0; w < NC; ++w) acc[a][w] = fmaf(rv[a], xv[w], acc[a][w]);
+  }
+#pragma unroll
+  for (int w = 0; w < NC; ++w)
+    if (cgp + 16 * w < k)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) Ys[r4 + a][cgp + 16 * w] -= acc[a][w];
+}
+
 template <bool TRANS>
 __global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ F, int64_t ld, int64_t n,
                                                       float* __restrict__ B, int64_t ldb, int k,
@@ -240,33 +268,14 @@ __global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ 
       }
       __syncthreads();
       if (q + 1 < deps) load_r(q + 1);
-      // Ys -= Rs Xs with a 4 x 4 register tile per thread: rows
-      // 4 * (tid % 16) + 0..3, columns tid / 16 + 16 * w (w < 4, c < k)
-      {
-        const int r4 = (tid % 16) * 4, cgp = tid / 16;
-        const int ncol = (k - cgp + 15) / 16;  // 0..4 columns for this thread
-        float acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) acc[a][w] = 0.f;
-#pragma unroll 4
-        for (int l = 0; l < kPB; ++l) {
-          float rv[4], xv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) rv[a] = Rs[r4 + a][l];
-#pragma unroll
-          for (int w = 0; w < 4; ++w) xv[w] = Xs[l][(cgp + 16 * w) & (kPB - 1)];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[a][w] = fmaf(rv[a], xv[w], acc[a][w]);
-        }
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-          if (w < ncol)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) Ys[r4 + a][cgp + 16 * w] -= acc[a][w];
+      // Ys -= Rs Xs with a 4 x NC register tile per thread: rows
+      // 4 * (tid % 16) + 0..3, columns tid / 16 + 16 * w (w < NC, c < k);
+      // NC = ceil(k / 16) so that a few right-hand sides cost few products
+      switch ((k + 15) / 16) {
+        case 1: block_product<1>(Rs, Xs, Ys, k, tid); break;
+        case 2: block_product<2>(Rs, Xs, Ys, k, tid); break;
+        case 3: block_product<3>(Rs, Xs, Ys, k, tid); break;
+        default: block_product<4>(Rs, Xs, Ys, k, tid); break;
       }
       __syncthreads();
     }
@@ -281,28 +290,52 @@ __global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ 
     float* rdiag = &Xs[0][0];  // free now
     if (tid < ni) rdiag[tid] = 1.f / Rs[tid][tid];
     __syncthreads();
-    for (int c = warp; c < k; c += 8) {
+    // warp w solves columns w and w + 8 (then w + 16, w + 24, ...) in pairs,
+    // interleaving the two dependency chains
+    for (int c = warp; c < k; c += 16) {
+      const bool two = c + 8 < k;
+      const int c2 = two ? c + 8 : c;
       float y0 = lane < ni ? Ys[lane][c] : 0.f;
       float y1 = lane + 32 < ni ? Ys[lane + 32][c] : 0.f;
+      float u0 = lane < ni ? Ys[lane][c2] : 0.f;
+      float u1 = lane + 32 < ni ? Ys[lane + 32][c2] : 0.f;
       if (!TRANS) {
         for (int q = ni - 1; q >= 0; --q) {
-          const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
-          const float xq = yq * rdiag[q];
-          if (q < 32) { if (lane == q) y0 = xq; } else if (lane == q - 32) { y1 = xq; }
-          if (lane < q) y0 -= Rs[lane][q] * xq;
-          if (lane + 32 < q) y1 -= Rs[lane + 32][q] * xq;
+          const float rq = rdiag[q];
+          const float xq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31) * rq;
+          const float zq = __shfl_sync(0xffffffffu, q < 32 ? u0 : u1, q & 31) * rq;
+          if (q < 32) {
+            if (lane == q) { y0 = xq; u0 = zq; }
+          } else if (lane == q - 32) {
+            y1 = xq;
+            u1 = zq;
+          }
+          const float ra = Rs[lane][q], rb = Rs[lane + 32][q];
+          if (lane < q) { y0 -= ra * xq; u0 -= ra * zq; }
+          if (lane + 32 < q) { y1 -= rb * xq; u1 -= rb * zq; }
         }
       } else {
         for (int q = 0; q < ni; ++q) {
-          const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
-          const float zq = yq * rdiag[q];
-          if (q < 32) { if (lane == q) y0 = zq; } else if (lane == q - 32) { y1 = zq; }
-          if (lane > q && lane < ni) y0 -= Rs[q][lane] * zq;
-          if (lane + 32 > q && lane + 32 < ni) y1 -= Rs[q][lane + 32] * zq;
+          const float rq = rdiag[q];
+          const float xq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31) * rq;
+          const float zq = __shfl_sync(0xffffffffu, q < 32 ? u0 : u1, q & 31) * rq;
+          if (q < 32) {
+            if (lane == q) { y0 = xq; u0 = zq; }
+          } else if (lane == q - 32) {
+            y1 = xq;
+            u1 = zq;
+          }
+          const float ra = Rs[q][lane], rb = Rs[q][lane + 32];
+          if (lane > q && lane < ni) { y0 -= ra * xq; u0 -= ra * zq; }
+          if (lane + 32 > q && lane + 32 < ni) { y1 -= rb * xq; u1 -= rb * zq; }
         }
       }
       if (lane < ni) B[i0 + lane + c * ldb] = y0;
       if (lane + 32 < ni) B[i0 + lane + 32 + c * ldb] = y1;
+      if (two) {
+        if (lane < ni) B[i0 + lane + c2 * ldb] = u0;
+        if (lane + 32 < ni) B[i0 + lane + 32 + c2 * ldb] = u1;
+      }
     }
     __threadfence();
     __syncthreads();
