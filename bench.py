@@ -307,9 +307,13 @@ def main():
     fp32_peak = 152 * 128 * 2 * sm_max_ghz * 1e9 / 1e12    # 128 FFMA/clk/SM
     bf16 = peaks.get("bf16_tflops_sustained") or 1705.3
     tf32_peak = bf16 * 1.1 / 2.25
-    if dom["name"] in ("zero_fill", "copy", "system_matrix"):
+    if dom["name"] in ("zero_fill", "copy", "system_matrix", "tc_update"):
         roof = {"bound": "hbm", "achieved": dom["bytes"] / (dom["ms"] / 1e3) / 1e9,
                 "peak": peaks.get("hbm_gbs") or 6809.3, "unit": "GB/s"}
+        if dom["name"] == "tc_update":
+            roof["note"] = ("C -= V W' streams C (read + write) and the TF32 operands; achieved counts those "
+                            "algorithmic bytes; tensor rate %.1f TFLOP/s algorithmic" % (
+                                dom["flops"] / (dom["ms"] / 1e3) / 1e12))
     elif dom["name"] == "tc_gemm":
         roof = {"bound": "tensor", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12,
                 "peak": tf32_peak, "unit": "TFLOP/s",

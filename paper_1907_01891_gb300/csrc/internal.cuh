@@ -84,7 +84,7 @@ constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 // ---------------------------------------------------------------------------
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
-  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_COUNT
+  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_TC_UPDATE, K_COUNT
 };
 
 // Graph capture: launches made between begin and end are recorded into

@@ -570,7 +570,7 @@ ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, cons
   a.mtiles = (M + kBM - 1) / kBM;
   a.ntiles = (N + kBM - 1) / kBM;
   a.status = status;
-  LaunchScope ls(K_TC_GEMM, s, 2.0 * M * N * K, 4.0 * ((double)K * (M + N) * (split3 ? 2 : 1) + 2.0 * M * N));
+  LaunchScope ls(K_TC_UPDATE, s, 2.0 * M * N * K, 4.0 * ((double)K * (M + N) * (split3 ? 2 : 1) + 2.0 * M * N));
   if (split3) return launch_upd<true, 3>(maps, a, sms, s);
   return launch_upd<false, 6>(maps, a, sms, s);
 }
