@@ -46,7 +46,8 @@ constexpr int kMaxDeps = 6;
 constexpr int kMaxIncs = 6;
 constexpr int kRtThreads = 256;
 // A task may wait for a whole chain of earlier tasks (up to a system's
-// critical path of tile tasks), so the bound is wider than a barrier's.
+// critical path of tile tasks), so the bound is wider than a barrier's
+// (CTQR_WAIT_LIMIT_MS overrides it, e.g. for the timeout test).
 constexpr uint64_t kTaskWaitLimitNs = 10000000000ull;
 
 struct TileTask {
@@ -366,7 +367,7 @@ __device__ void t_trsm(const double* Rt, double* X, int rows, int cols) {
 template <int b>
 __global__ void __launch_bounds__(kRtThreads, 1)
     k_tile_runtime(const TileTask* __restrict__ tasks, int ntasks, const SysDesc* __restrict__ sys, int* cnt,
-                   int* next, int* status) {
+                   int* next, int* status, uint64_t wait_limit_ns) {
   constexpr int LD = Tile<b>::LD, TS = b * LD;
   extern __shared__ double sm[];
   double* t0 = sm;
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
           while (*(const volatile int*)c < s_task.dep_v[d]) {
             if ((++spins & 63u) == 0) {
               if (ld_volatile_i32(status) != 0) { s_ok = 0; break; }
-              if (globaltimer_ns() - start > kTaskWaitLimitNs) { set_status(status, CT_ERR_TIMEOUT); s_ok = 0; break; }
+              if (globaltimer_ns() - start > wait_limit_ns) { set_status(status, CT_ERR_TIMEOUT); s_ok = 0; break; }
             }
             __nanosleep(64);
           }
@@ -696,6 +697,26 @@ ct_status run_batch_t(int count, const ct_batch_system* in, int sms, int* status
   CT_CUDA_TRY(cudaMallocAsync((void**)&T, te * sizeof(double) + 16, s));
   BatchPlan plan;
   plan_batch(count, in, b, T, &plan);
+  uint64_t wait_ns = kTaskWaitLimitNs;
+  if (const char* e = getenv("CTQR_WAIT_LIMIT_MS")) {
+    const long ms = atol(e);
+    if (ms > 0) wait_ns = (uint64_t)ms * 1000000ull;
+  }
+  // Host-side fault injection for the bounded-wait test: task k of the list
+  // waits for a version of its first counter that no task ever produces, so
+  // its CTA (and every task behind it) gives up after wait_ns with
+  // CT_ERR_TIMEOUT.
+  if (const char* e = getenv("CTQR_FAULT_STALL_TASK")) {
+    const long k = atol(e);
+    if (k >= 0 && k < (long)plan.tasks.size()) {
+      TileTask& t = plan.tasks[(size_t)k];
+      if (t.nd == 0) {
+        t.nd = 1;
+        t.dep_c[0] = 0;
+      }
+      t.dep_v[0] = 1 << 30;
+    }
+  }
   TileTask* dtasks = nullptr;
   SysDesc* dsys = nullptr;
   int* cnt = nullptr;
@@ -753,7 +774,7 @@ ct_status run_batch_t(int count, const ct_batch_system* in, int sms, int* status
       cudaMemsetAsync(cnt, 0, (size_t)2 * plan.parts * sizeof(int), cs);
       cudaMemsetAsync(next, 0, sizeof(int), cs);
       cudaError_t le = cudaLaunchKernelEx(&cfg, k_tile_runtime<b>, (const TileTask*)dtasks, ntasks,
-                                          (const SysDesc*)dsys, cnt, next, status);
+                                          (const SysDesc*)dsys, cnt, next, status, wait_ns);
       cudaError_t ce = cudaStreamEndCapture(cs, &graph);
       graphed = le == cudaSuccess && ce == cudaSuccess && graph &&
                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
@@ -772,7 +793,7 @@ ct_status run_batch_t(int count, const ct_batch_system* in, int sms, int* status
         if (cudaMemsetAsync(cnt, 0, (size_t)2 * plan.parts * sizeof(int), cs) != cudaSuccess ||
             cudaMemsetAsync(next, 0, sizeof(int), cs) != cudaSuccess ||
             cudaLaunchKernelEx(&cfg, k_tile_runtime<b>, (const TileTask*)dtasks, ntasks, (const SysDesc*)dsys, cnt,
-                               next, status) != cudaSuccess) {
+                               next, status, wait_ns) != cudaSuccess) {
           cudaGetLastError();
           st = CT_ERR_CUDA;
           break;

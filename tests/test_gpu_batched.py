@@ -104,3 +104,23 @@ def test_uneven_lambda_stacked_batch_smallest_systems_match_oracle():
         X = Bt.cpu().numpy()[:g.n]
         Xo = O.lstsq(Asys, b)
         assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10, (g.nx, g.m)
+
+
+def test_batched_stalled_task_times_out_and_context_survives(monkeypatch):
+    """A task whose dependency never arrives (host-side injection) makes the
+    persistent launch give up after the bounded wait with CT_ERR_TIMEOUT; the
+    next call on the same context succeeds."""
+    A = I.random_matrix(300, 120, seed=21)
+    B = I.random_matrix(300, 2, seed=22)
+    monkeypatch.setenv("CTQR_WAIT_LIMIT_MS", "200")
+    monkeypatch.setenv("CTQR_FAULT_STALL_TASK", "7")
+    st, _ = ctqr.qr_solve_batched([ctqr.to_colmajor(A)], [ctqr.to_colmajor(B)], tile=32, check=False)
+    assert st == ctqr.CT_ERR_TIMEOUT
+    monkeypatch.delenv("CTQR_FAULT_STALL_TASK")
+    At, Bt = ctqr.to_colmajor(A), ctqr.to_colmajor(B)
+    st, _ = ctqr.qr_solve_batched([At], [Bt], tile=32)
+    assert st == ctqr.CT_OK
+    torch.cuda.synchronize()
+    X = Bt.cpu().numpy()[:120]
+    Xo = O.lstsq(A, B)
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10

@@ -409,3 +409,34 @@ def test_tf32_factor_with_lookahead_refines_to_fp64(monkeypatch):
     X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=At)
     Xo = O.lstsq(A, b)
     assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
+
+
+def test_allocation_failure_is_reported_without_leaking(monkeypatch):
+    """Host-side injection (CTQR_FAULT_NOMEM): the factorization reports
+    CT_ERR_NOMEM and frees what it had allocated; the next call works."""
+    A = ctqr.to_colmajor(I.random_matrix(400, 200, seed=5))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    monkeypatch.setenv("CTQR_FAULT_NOMEM", "1")
+    with pytest.raises(ctqr.CtError) as ei:
+        ctqr.qr_factor(A)
+    assert ei.value.status == ctqr.CT_ERR_NOMEM
+    monkeypatch.delenv("CTQR_FAULT_NOMEM")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (1 << 20)
+    f = ctqr.qr_factor(A)
+    assert f.status() == ctqr.CT_OK
+
+
+def test_refinement_cap_reports_noconverge():
+    """A mixed-precision factor on noisy data with the refinement capped at
+    one correction does not reach the tolerance: CT_ERR_NOCONVERGE, finite X."""
+    g = I.CONFIG1["geom"]
+    A = ctqr.build_system(g, torch.float64)
+    Anp = _np(A)
+    b = I.poisson_noise(Anp @ I.phantoms(g, [1001, 1002]), g.fov, 1e4, seed=9)
+    f = ctqr.qr_factor(A.to(torch.float32), prec=ctqr.Prec.F32)
+    X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A, max_iter=1, tol=1e-14, check=False)
+    assert rep.status == ctqr.CT_ERR_NOCONVERGE
+    assert np.all(np.isfinite(_np(X)))
