@@ -133,6 +133,17 @@ def barrier(world: int):
         dist.barrier()
 
 
+def replica_seeds(seeds, rank: int):
+    """Every rank reconstructs its own scan: the same phantom recipe with the
+    seeds shifted by 100000 per rank (independent replicas, no exchange)."""
+    return [s + 100000 * rank for s in seeds]
+
+
+def job_throughput(world: int, units_per_rank: int, steps: int, ms_max: float) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 # ---------------------------------------------------------------- oracle timing
 def oracle_sample(cfg, k: int, budget_s: float):
     """Time the plain CPU oracle on a bounded sample of the workload and scale
@@ -218,7 +229,7 @@ def main():
     # ---- inputs (outside the timed region): phantoms, sinograms B = A x (+ noise)
     lam = cfg.get("lam", 0.0)
     m_sys, n_sys = ctqr.system_size(g, lam)
-    seeds = [s + 100000 * rank for s in cfg["seeds"]]
+    seeds = replica_seeds(cfg["seeds"], rank)
     Xtrue = I.phantoms(g, seeds)
     A = ctqr.build_system(g, torch.float64)  # rays only, for the inputs and the checks
     B = ctqr.colmajor(m_sys, k, fill=0.0)     # [b; 0] when lambda*I is stacked
@@ -290,7 +301,7 @@ def main():
     kstats = ctqr.profile_kernels()
     ms = e0.elapsed_time(e1)
     ms_max = reduce_max(ms, world, dev)
-    value = world * k * args.steps / (ms_max / 1e3)
+    value = job_throughput(world, k, args.steps, ms_max)
     ms_factor = statistics.median(r.ms_factor for r in reps)
     ms_solve = statistics.median(r.ms_solve for r in reps)
     ms_build = statistics.median(r.ms_build for r in reps)
@@ -487,7 +498,7 @@ def main_batch(args, world, rank, local, cfg):
     clk = clocks.stop()
     kstats = ctqr.profile_kernels()  # launch counts of the timed steps
     ms = reduce_max(e0.elapsed_time(e1), world, dev)
-    value = world * count * args.steps / (ms / 1e3)
+    value = job_throughput(world, count, args.steps, ms)
     ms_kernel = statistics.median(r.ms for r in reps)
     peaks = {}
     try:
