@@ -81,70 +81,128 @@ __global__ void __launch_bounds__(256) k_reduce_gram(const float* __restrict__ G
   Gout[e] = s;
 }
 
-// W' (kNB x nc, ld kNB) from the split partials of W and the reduced
-// G = V^T V, one warp per column; lane l holds rows l, l+32, l+64, l+96.
-constexpr int kGS = kNB + 1;  // row stride of the Gram matrix in shared memory
-constexpr size_t kSolveSmem = (size_t)(kNB * kGS + kNB) * sizeof(float);
+// T = S^{-1} for S = diag(1/tau) + striu(G), the compact-WY T of the block's
+// nbo reflectors (rows and columns >= nbo are zero).  Block doubling on one
+// CTA: T_ii = tau_i (no division, so tau_i = 0 gives H_i = I), then for
+// s = 1, 2, ..., 64 and the diagonal block pairs A = [p, p+s), C = [p+s, p+2s):
+// T_AC = -T_A S_AC T_C.  T is written column-major, T(i, j) at i + j * kNB.
+constexpr int kGS = kNB + 1;  // leading dimension of the 128 x 128 matrices in shared memory
+constexpr size_t kTinvSmem = (size_t)3 * kNB * kGS * sizeof(float);
 
-__global__ void __launch_bounds__(256) k_solve_st(const float* __restrict__ Wp, int wsplits, int64_t wstride,
-                                                  const float* __restrict__ Gred, const double* __restrict__ tau,
-                                                  int nbo, int64_t nc, float* __restrict__ Wout,
+__global__ void __launch_bounds__(256) k_tinv(const float* __restrict__ Gred, const double* __restrict__ tau, int nbo,
+                                              float* __restrict__ Tout) {
+  extern __shared__ float sm[];
+  float* S = sm;              // S(i, j) = G(i, j) for i < j
+  float* X = S + kNB * kGS;   // T
+  float* Y = X + kNB * kGS;   // S_AC T_C
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kNB * kNB; e += 256) {
+    const int i = e % kNB, j = e / kNB;
+    S[i + j * kGS] = __ldcg(Gred + e);
+    X[i + j * kGS] = (i == j && i < nbo) ? (float)tau[i] : 0.f;
+  }
+  __syncthreads();
+  for (int s = 1; s < kNB; s *= 2) {
+    const int ent = (kNB / (2 * s)) * s * s;
+    for (int e = tid; e < ent; e += 256) {
+      const int pr = e / (s * s), rr = e % (s * s), r = rr % s, c = rr / s;
+      const int p0 = pr * 2 * s, gi = p0 + r, gc = p0 + s + c;
+      float acc = 0.f;
+      for (int k = 0; k <= c; ++k) acc += S[gi + (p0 + s + k) * kGS] * X[(p0 + s + k) + gc * kGS];
+      Y[gi + gc * kGS] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ent; e += 256) {
+      const int pr = e / (s * s), rr = e % (s * s), r = rr % s, c = rr / s;
+      const int p0 = pr * 2 * s, gi = p0 + r, gc = p0 + s + c;
+      float acc = 0.f;
+      for (int k = r; k < s; ++k) acc += X[gi + (p0 + k) * kGS] * Y[(p0 + k) + gc * kGS];
+      X[gi + gc * kGS] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kNB * kNB; e += 256) {
+    const int i = e % kNB, j = e / kNB;
+    Tout[e] = X[i + j * kGS];
+  }
+}
+
+// W' = T^T sum_z W_z for 64 columns per CTA (the UT-transform solve written as
+// a product with the explicit T), split into TF32 high and low parts when Wlo
+// is given.  Thread (ty = tid % 16, tx = tid / 16) computes rows ty + 16 i
+// (i < 8) and columns tx * 4 + j (j < 4).
+constexpr int kTC = 64;
+constexpr size_t kApplyTtSmem = (size_t)(kNB * kNB + kNB * kTC) * sizeof(float);
+
+__global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, int wsplits, int64_t wstride,
+                                                  const float* __restrict__ T, int64_t nc, float* __restrict__ Wout,
                                                   float* __restrict__ Wlo) {
   extern __shared__ float sm[];
-  float* G = sm;              // G[i * kGS + r] = (V^T V)(i, r), strict upper part
-  float* ts = sm + kNB * kGS;
-  // stage G, eight loads in flight per thread
-  for (int e0 = threadIdx.x; e0 < kNB * kNB; e0 += 256 * 8) {
+  float* Ts = sm;               // Ts[k * kNB + r] = T(k, r)
+  float* Ws = Ts + kNB * kNB;   // Ws[k * kTC + c] = W(k, c0 + c)
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * kTC;
+  for (int e0 = tid; e0 < kNB * kNB; e0 += 256 * 8) {
     float v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldcg(Gred + e0 + 256 * u);  // kNB * kNB is a multiple of 2048
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(T + e0 + 256 * u);  // T(k, r) at k + r * kNB
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = e0 + 256 * u, i = e % kNB, r = e / kNB;
-      G[i * kGS + r] = v[u];
+      const int e = e0 + 256 * u, k = e % kNB, r = e / kNB;
+      Ts[k * kNB + r] = v[u];
     }
   }
-  for (int i = threadIdx.x; i < kNB; i += 256) ts[i] = i < nbo ? (float)tau[i] : 0.f;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t c = (int64_t)blockIdx.x * 8 + warp; c < nc; c += (int64_t)gridDim.x * 8) {
-    float w[4] = {0.f, 0.f, 0.f, 0.f};
-    const float* wc = Wp + lane + c * kNB;
-    int z = 0;
-    for (; z + 4 <= wsplits; z += 4) {
-      float v[4][4];
+  for (int e0 = tid; e0 < kNB * kTC; e0 += 256 * 4) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int z = 0; z < wsplits; ++z) {
+      float w[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[u][q] = __ldcg(wc + (z + u) * wstride + 32 * q);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] += v[u][q];
-    }
-    for (; z < wsplits; ++z)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) w[q] += __ldcg(wc + z * wstride + 32 * q);
-    for (int i = 0; i < nbo; ++i) {
-      const int qi = i >> 5;
-      const float src = qi == 0 ? w[0] : (qi == 1 ? w[1] : (qi == 2 ? w[2] : w[3]));
-      const float wi = __shfl_sync(0xffffffffu, src, i & 31) * ts[i];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        if (r == i) w[q] = wi;
-        else if (r > i) w[q] -= G[i * kGS + r] * wi;
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 256 * u, k = e % kNB, c = e / kNB;
+        w[u] = c0 + c < nc ? __ldcg(Wp + z * wstride + k + (c0 + c) * kNB) : 0.f;
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] += w[u];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t o = lane + 32 * q + c * kNB;
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + 256 * u, k = e % kNB, c = e / kNB;
+      Ws[k * kTC + c] = v[u];
+    }
+  }
+  __syncthreads();
+  const int ty = tid % 16, tx = tid / 16;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < kNB; ++k) {
+    float a[8], b[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = Ts[k * kNB + ty + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Ws[k * kTC + tx * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t c = c0 + tx * 4 + j;
+    if (c >= nc) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t o = ty + 16 * i + c * kNB;
+      const float w = acc[i][j];
       if (Wlo) {
-        const float h = tf32_hi(w[q]);
+        const float h = tf32_hi(w);
         Wout[o] = h;
-        Wlo[o] = w[q] - h;
+        Wlo[o] = w - h;
       } else {
-        Wout[o] = w[q];
+        Wout[o] = w;
       }
     }
   }
@@ -159,7 +217,7 @@ size_t outer_work_floats(int sms, int64_t m, int64_t n) {
          + (size_t)2 * m * kNB     // Vr (high, low)
          + (size_t)kNB * wcols     // W partials
          + (size_t)2 * kNB * n     // W' (high, low)
-         + (size_t)(2 * sms + 1) * kNB * kNB;  // G partials, reduced G
+         + (size_t)(2 * sms + 2) * kNB * kNB;  // G partials, reduced G, T
 }
 
 // Update C = F[J:m, J+nbo:n] with the block reflector of F[J:m, J:J+nbo].
@@ -226,17 +284,23 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     k_reduce_gram<<<kNB * kNB / 256, 256, 0, s>>>(Gp, gs, (int64_t)kNB * kNB, nbo, Gred);
     CT_LAUNCH_CHECK();
   }
+  // W' = T^T W: T = S^{-1} once for the block, then one product per 64 columns.
+  float* Tb = Gp + (size_t)(2 * sms + 1) * kNB * kNB;
   {
-    LaunchScope ls(K_TW, s, (double)kNB * kNB * nc, 4.0 * kNB * nc * (ws + 1));
-    unsigned grid = (unsigned)((nc + 7) / 8);
-    if (grid > (unsigned)(4 * sms)) grid = (unsigned)(4 * sms);
+    LaunchScope ls(K_TW, s, (double)kNB * kNB * kNB / 3.0, 8.0 * kNB * kNB);
     static bool attr = false;
     if (!attr) {
-      CT_CUDA_TRY(cudaFuncSetAttribute(k_solve_st, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplyTtSmem));
       attr = true;
     }
-    k_solve_st<<<grid, 256, kSolveSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Gred, f->tau + J, nbo, nc, Wq,
-                                             split3 ? Wql : nullptr);
+    k_tinv<<<1, 256, kTinvSmem, s>>>(Gred, f->tau + J, nbo, Tb);
+    CT_LAUNCH_CHECK();
+  }
+  {
+    LaunchScope ls(K_TW, s, 2.0 * kNB * kNB * nc, 4.0 * kNB * nc * (ws + 2));
+    k_apply_tt<<<(unsigned)((nc + kTC - 1) / kTC), 256, kApplyTtSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Tb, nc,
+                                                                           Wq, split3 ? Wql : nullptr);
     CT_LAUNCH_CHECK();
   }
   // C -= V W'  (A = V stored row-major: kNB x mr column-major with ld kNB),
