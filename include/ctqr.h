@@ -227,6 +227,16 @@ ct_status ct_factor_status(const ct_factor* f, void* stream);
 ct_status ct_apply_qt(const ct_factor* f, double* B, int64_t ldb, int64_t k,
                       void* stream);
 
+/* B <- Q^T B in place in FP32 arithmetic for the m x k FP32 device matrix B
+ * (ldb >= m, B 16-byte aligned) with a CT_PREC_F32 / CT_PREC_TF32 factor: the
+ * first sub-step of Eq. (qr1) at the factor's precision, as the refinement's
+ * first solve X_0 uses it.  Two-level (TF32) factors with 1 <= k <= 32 apply
+ * all their 128-column outer blocks in one cooperative launch when each SM's
+ * share of the rows fits its shared memory (about 160 rows per SM), else
+ * block by block.  CT_ERR_UNSUPPORTED for an FP64 factor; k may be 0. */
+ct_status ct_apply_qt_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k,
+                          void* stream);
+
 /* B <- Q^T B exactly like ct_apply_qt, for callers that cannot let a library
  * allocate device memory: applications whose framework has already reserved
  * the GPU's memory for its own caching allocator (an allocation here would
@@ -259,9 +269,10 @@ ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k,
  * CT_PREC_F32 / CT_PREC_TF32 factor; B is an FP32 device matrix, ldb >= n.
  * The paper's factor is FP64 and has no counterpart; the operation is the
  * back substitution of Sec. II-C-4 at lower precision.  For k <= 64 one
- * persistent launch walks the 64-row block rows in dependency order; wider B
- * uses recursive halving with one product per split.  CT_ERR_UNSUPPORTED for
- * an FP64 factor. */
+ * persistent launch per 32 columns walks the 128-row block rows in
+ * dependency order, each block row finished by a product with its inverted
+ * diagonal block; wider B uses recursive halving with one product per split.
+ * CT_ERR_UNSUPPORTED for an FP64 factor. */
 ct_status ct_trsm_solve_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k, int transpose,
                             void* stream);
 

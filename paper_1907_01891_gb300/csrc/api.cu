@@ -60,6 +60,7 @@ void free_factor(ct_factor* f) {
   if (f->barrier) cudaFree(f->barrier);
   if (f->partials) cudaFree(f->partials);
   if (f->Gblk) cudaFree(f->Gblk);
+  if (f->Tblk) cudaFree(f->Tblk);
   delete f;
 }
 
@@ -127,20 +128,31 @@ class Refiner {
     // lambda*I rows make the system inconsistent: go to CGLS after X_0.
     const bool classical_only = method == 1;
     const bool cgls_now = method == 2 || (method == 0 && lam_ > 0.0);
-    bool go_cgls = false;
+    bool go_cgls = false, have_residual = false;
     for (; it <= max_iter; ++it) {
       double worst = 0.0;
-      if ((st = classical_step(it > 0, &worst)) != CT_OK) return st;
+      // The residual of X_0 tells whether B is consistent: a residual well
+      // above rounding level means noisy data, where only CGLS reaches the
+      // least-squares solution, so it goes there without a classical step.
+      int mode = it == 0 ? 0 : 1;
+      if (it == 1 && method == 0) {
+        if ((st = residual_norm()) != CT_OK) return st;
+        if (resid_ > 1e-6) {
+          if (trace_) fprintf(stderr, "ctqr residual of X_0 %.3e: to CGLS (%.2f ms)\n", resid_, since_start());
+          go_cgls = true;
+          have_residual = true;
+          break;
+        }
+        mode = 2;
+      }
+      if ((st = classical_step(mode, &worst)) != CT_OK) return st;
       if (it == 0) {
+        if (trace_) fprintf(stderr, "ctqr X_0 = R^-1 (Q^T B) (%.2f ms)\n", since_start());
         if (cgls_now) { go_cgls = true; break; }
         continue;
       }
-      // The first residual tells whether B is consistent: a residual well
-      // above rounding level means noisy data, where only CGLS can reach the
-      // least-squares solution.
-      if (it == 1 && method == 0 && resid_ > 1e-6) { go_cgls = true; break; }
       last_ = worst;
-      if (trace_) fprintf(stderr, "ctqr classical %d: max |dx|/|x| = %.3e\n", it, worst);
+      if (trace_) fprintf(stderr, "ctqr classical %d: max |dx|/|x| = %.3e (%.2f ms)\n", it, worst, since_start());
       if (worst <= tol_) { result = CT_OK; break; }
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
       if (!classical_only && it >= 2 && worst > 0.25 * prev) { go_cgls = true; break; }
@@ -148,7 +160,7 @@ class Refiner {
     }
     if (go_cgls) {
       int used = 0;
-      result = cgls(max_iter - it, &used);
+      result = cgls(max_iter - it, &used, have_residual);
       it += used;
     }
     if (rep) {
@@ -205,6 +217,11 @@ class Refiner {
   // Diagnostics: CTQR_TRACE=1 prints every step's update size to stderr;
   // CTQR_PRECOND_F64=1 runs the preconditioner solves in FP64 arithmetic.
   bool trace_ = getenv("CTQR_TRACE") != nullptr;
+  std::chrono::steady_clock::time_point t0_ = std::chrono::steady_clock::now();
+  // host milliseconds since the refinement started (trace output only)
+  double since_start() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
+  }
   bool precond_f64_ = getenv("CTQR_PRECOND_F64") != nullptr;
 
   ct_status alloc() {
@@ -267,14 +284,33 @@ class Refiner {
     return CT_OK;
   }
 
-  // One classical step; with_residual = false is the first solve (X = 0).
-  ct_status classical_step(bool with_residual, double* worst) {
+  // Res = B - [A; lambda I] X into Yd, its column norms into n1 and
+  // resid_ = ||Res||_F / ||B||_F.
+  ct_status residual_norm() {
     ct_status st;
-    if (with_residual) {
+    if ((st = residual()) != CT_OK) return st;
+    if ((st = launch_col_norms2(Yd_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;
+    if ((st = fetch(bn2_, 2)) != CT_OK) return st;
+    double rr = 0.0, bb = 0.0;
+    for (int64_t c = 0; c < k_; ++c) {
+      bb += h_[c];
+      rr += h_[k_ + c];
+    }
+    resid_ = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    return CT_OK;
+  }
+
+  // One classical step: mode 0 is the first solve (X = 0), mode 1 forms the
+  // residual of X first, mode 2 takes the residual (and its norms) that
+  // residual_norm() left in Yd.
+  ct_status classical_step(int mode, double* worst) {
+    ct_status st;
+    const bool with_residual = mode != 0;
+    if (mode == 1) {
       if ((st = residual()) != CT_OK) return st;
       if ((st = launch_col_norms2(Yd_, ldw_, m_, k_, n1_, s_)) != CT_OK) return st;
-    } else if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) {
-      return st;
+    } else if (mode == 0) {
+      if ((st = launch_copy_matrix(B_, CT_F64, ldb_, Yd_, CT_F64, ldw_, m_, k_, s_)) != CT_OK) return st;
     }
     if (f32()) {
       float* D = (float*)D_.p;
@@ -374,7 +410,7 @@ class Refiner {
   // <r, A t> / ||A t||^2 and beta the Polak-Ribiere ratio, so rounding in the
   // preconditioner solves slows the iteration but cannot move its fixed
   // point, A^T r = 0.
-  ct_status cgls(int budget, int* used) {
+  ct_status cgls(int budget, int* used, bool have_residual) {
     ct_status st;
     *used = 0;
     if ((st = cg_.alloc(((size_t)5 * n_ * k_ + (size_t)ldw_ * k_) * sizeof(double), s_)) != CT_OK) return st;
@@ -385,7 +421,7 @@ class Refiner {
     double* G = T_ + n_ * k_;  // scratch n x k
     Q_ = G + n_ * k_;
     (void)G;
-    if ((st = residual()) != CT_OK) return st;              // r = B - A X
+    if (!have_residual && (st = residual()) != CT_OK) return st;  // r = B - A X
     if ((st = precond_grad(S_)) != CT_OK) return st;        // s = R^-T A^T r
     if ((st = launch_copy_matrix(S_, CT_F64, n_, P_, CT_F64, n_, n_, k_, s_)) != CT_OK) return st;
     if ((st = launch_col_norms2(S_, n_, n_, k_, n1_, s_)) != CT_OK) return st;
@@ -414,7 +450,7 @@ class Refiner {
       if ((st = launch_colwise(0, 1.0, a_, T_, n_, X_, ldx_, n_, k_, s_)) != CT_OK) return st;    // x += a t
       if ((st = launch_colwise(0, -1.0, a_, Q_, ldw_, Yd_, ldw_, m_, k_, s_)) != CT_OK) return st;  // r -= a q
       last_ = worst;
-      if (trace_) fprintf(stderr, "ctqr cgls %d: max |dx|/|x| = %.3e\n", it, worst);
+      if (trace_) fprintf(stderr, "ctqr cgls %d: max |dx|/|x| = %.3e (%.2f ms)\n", it, worst, since_start());
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
       if (worst <= tol_) {
         CT_CUDA_TRY(cudaStreamSynchronize(s_));
@@ -455,6 +491,15 @@ ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int
   // the per-panel application.
   int64_t jblk = 0;
   if (f->Gblk && max_splits == 0) {
+    // FP32 right-hand sides: all outer blocks in one persistent launch when it fits
+    if (!c_f64 && fp32_math) {
+      int nblk = 0;
+      while ((int64_t)(nblk + 1) * 128 < f->n) ++nblk;
+      ct_status st = nblk > 0 ? apply_qt_outer_persist(f, (float*)C, ldc, k, nblk, work, work_elems, sms, s)
+                              : CT_ERR_UNSUPPORTED;
+      if (st == CT_OK) jblk = (int64_t)nblk * 128;
+      else if (st != CT_ERR_UNSUPPORTED) return st;
+    }
     for (; jblk + 128 < f->n; jblk += 128) {
       ct_status st = apply_outer_reflector(f, jblk, (char*)C + (size_t)jblk * cs, c_f64, ldc, k, fp32_math, work,
                                            work_elems, sms, s);
@@ -567,7 +612,8 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       (st = dev_alloc(&f->status, 1)) != CT_OK ||
       (st = dev_alloc(&f->barrier, 2)) != CT_OK ||
       (st = dev_alloc(&f->partials, f->partials_elems)) != CT_OK ||
-      (tc && (st = dev_alloc(&f->Gblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK)) {
+      (tc && (st = dev_alloc(&f->Gblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK) ||
+      (tc && (st = dev_alloc(&f->Tblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK)) {
     free_factor(f);
     return st;
   }
@@ -720,6 +766,21 @@ ct_status ct_apply_qt(const ct_factor* f, double* B, int64_t ldb, int64_t k, voi
   Scratch work;
   if ((st = work.alloc(work_elems * sizeof(double), s)) != CT_OK) return st;
   return apply_qt_all(f, B, true, ldb, k, false, (double*)work.p, work_elems, di.sms, s);
+}
+
+ct_status ct_apply_qt_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k, void* stream) {
+  if (!f || k < 0) return CT_ERR_INVALID;
+  if (f->store != CT_F32) return CT_ERR_UNSUPPORTED;
+  if (k == 0) return CT_OK;
+  if (!B || !aligned16(B) || ldb < f->m) return CT_ERR_INVALID;
+  cudaStream_t s = as_stream(stream);
+  DeviceInfo di;
+  ct_status st = device_info(&di);
+  if (st != CT_OK) return st;
+  const size_t work_elems = reflector_work_elems(di.sms, f->nb, k);
+  Scratch work;
+  if ((st = work.alloc(work_elems * sizeof(double), s)) != CT_OK) return st;
+  return apply_qt_all(f, B, false, ldb, k, true, (double*)work.p, work_elems, di.sms, s);
 }
 
 ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k, void* stream) {

@@ -76,6 +76,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, unsign
 
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 
+// 4-byte asynchronous copy global -> shared; an invalid element is filled
+// with zero (source size 0: nothing is read).
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Launch accounting (profile.cu).  Construct a LaunchScope right before a
 // kernel launch and let it go out of scope right after: it counts the launch,
@@ -84,7 +95,8 @@ constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s per wait
 // ---------------------------------------------------------------------------
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
-  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_TC_UPDATE, K_COUNT
+  K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_TC_UPDATE,
+  K_QT_OUTER, K_COUNT
 };
 
 // Graph capture: launches made between begin and end are recorded into
@@ -142,6 +154,8 @@ struct ct_factor {
   float* Gblk = nullptr;        // two-level factors: V^T V of every 128-column outer
                                 // block (128 x 128, strict upper part; blocks whose
                                 // update ran, i.e. all but the last)
+  float* Tblk = nullptr;        // the same blocks' compact-WY T = S^{-1} (128 x 128,
+                                // column-major, upper)
   int device = 0;
 };
 
@@ -182,6 +196,11 @@ ct_status apply_block_reflector(const ReflectorArgs& a, double* work, size_t wor
 // two-level factor, T given through its UT-transform form S = T^{-1} =
 // diag(1/tau) + striu(G), G = V^T V (gemm_simt.cu); work as for
 // apply_block_reflector.
+// Q^T C (FP32 C and arithmetic, 1 <= k <= 32) for the outer blocks [0, nblk)
+// of a two-level factor in one cooperative launch; CT_ERR_UNSUPPORTED when
+// the factor or the shape does not allow it (nothing launched).
+ct_status apply_qt_outer_persist(const ct_factor* f, float* C, int64_t ldc, int64_t k, int nblk, double* work,
+                                 size_t work_elems, int sms, cudaStream_t s);
 ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f64, int64_t ldc, int64_t k,
                                 bool fp32_math, double* work, size_t work_elems, int sms, cudaStream_t s);
 

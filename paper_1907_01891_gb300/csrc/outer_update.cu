@@ -208,6 +208,177 @@ __global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Q^T C for the first nblk 128-column outer blocks of a two-level factor in
+// one cooperative launch (the solve's Q^T B, FP32 C and arithmetic, k <= 32).
+//
+// Applying the blocks one by one takes three launches per block whose work
+// is a few microseconds each.  Here every CTA owns a fixed range of at most
+// kQRC rows of C and keeps them in shared memory for the whole application;
+// for block J (reflectors V_J = the unit lower trapezoid of F[J:m, J:J+128],
+// compact-WY factor T_J):
+//   A. P_c = V_J^T C over the CTA's rows >= J        (partial, to global)
+//   -- grid barrier --
+//   B. P = sum_c P_c, split over the CTAs, each summing its entries over the
+//      partials in a fixed order
+//   -- grid barrier --
+//   C. W' = T_J^T P (every CTA, from the reduced P), then C -= V_J W' on the
+//      CTA's rows.
+// The next block's phase A reads only the CTA's own rows, so no barrier is
+// needed between C and A.  Thread (a, h) = (tid % 128, tid / 128) forms entry
+// a of columns [h KC/2, (h+1) KC/2) in A and C's W' product.
+constexpr int kQRC = 160;       // most rows of C a CTA holds
+constexpr int kQVS = kQRC + 1;  // column stride of the V slab in shared memory
+
+template <int KC>
+constexpr size_t qt_outer_smem_floats() {
+  return (size_t)kNB * kQVS + (size_t)kNB * kGS + (size_t)kQRC * (KC + 4) + (size_t)2 * kNB * (KC + 4);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int KC>
+__global__ void __launch_bounds__(256, 1) k_qt_outer(const float* __restrict__ F, int64_t ld, int64_t m,
+                                                     const float* __restrict__ Tblk, int nblk,
+                                                     float* __restrict__ C, int64_t ldc, int k, int rows_per_cta,
+                                                     float* __restrict__ part, float* __restrict__ pred,
+                                                     unsigned long long* bar, int* status) {
+  constexpr int CS = KC + 4;  // row stride of the k-column tiles (16-byte rows)
+  constexpr int H = KC / 2;   // columns per thread in the 128-row products
+  constexpr int E = kNB * KC; // entries of P
+  extern __shared__ __align__(16) float sq[];
+  float* Vs = sq;                   // V_J(a_lo + rr, a) at a * kQVS + rr
+  float* Ts = Vs + kNB * kQVS;      // T_J(i, a) at a * kGS + i
+  float* Cs = Ts + kNB * kGS;       // the CTA's rows of C, [rr][c]
+  float* Ps = Cs + kQRC * CS;       // reduced V^T C, [a][c]
+  float* Ws = Ps + kNB * CS;        // W', [a][c]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x;
+  const int64_t r_lo = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_hi = r_lo + rows_per_cta < m ? r_lo + rows_per_cta : m;
+  const int nrow = r_hi > r_lo ? (int)(r_hi - r_lo) : 0;
+  const int c1 = (int)((m + rows_per_cta - 1) / rows_per_cta);  // CTAs that own rows
+  for (int e = tid; e < kQRC * KC; e += 256) {
+    const int rr = e % kQRC, c = e / kQRC;
+    Cs[rr * CS + c] = (rr < nrow && c < k) ? C[r_lo + rr + (int64_t)c * ldc] : 0.f;
+  }
+  const int a = tid % kNB, h = tid / kNB;
+  for (int b = 0; b < nblk; ++b) {
+    const int64_t J = (int64_t)b * kNB;
+    const int64_t a_lo = r_lo > J ? r_lo : J;
+    const int na = r_hi > a_lo ? (int)(r_hi - a_lo) : 0;  // active rows
+    const int off = (int)(a_lo - r_lo);
+    const int c0 = (int)(J / rows_per_cta);                // first CTA with active rows
+    // T_J and the V slab of the active rows (zero above the unit diagonal)
+    for (int e = tid; e < kNB * kNB; e += 256)
+      cp_async_f32(Ts + (e / kNB) * kGS + (e % kNB), Tblk + (size_t)b * kNB * kNB + e, true);
+    for (int e = tid; e < na * kNB; e += 256) {
+      const int rr = e % na, col = e / na;
+      const int64_t r = a_lo + rr;
+      const bool v = r - J > col;
+      cp_async_f32(Vs + col * kQVS + rr, v ? F + r + (J + col) * ld : F, v);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid < kNB && J + tid >= a_lo && J + tid < r_hi) Vs[tid * kQVS + (int)(J + tid - a_lo)] = 1.f;
+    __syncthreads();
+    // A. this CTA's V_J^T C
+    if (na > 0) {
+      float acc[H];
+#pragma unroll
+      for (int j = 0; j < H; ++j) acc[j] = 0.f;
+      for (int rr = 0; rr < na; ++rr) {
+        const float v = Vs[a * kQVS + rr];
+        const float4* cr = reinterpret_cast<const float4*>(Cs + (off + rr) * CS + h * H);
+#pragma unroll
+        for (int q = 0; q < H / 4; ++q) {
+          const float4 c4 = cr[q];
+          acc[4 * q + 0] = fmaf(v, c4.x, acc[4 * q + 0]);
+          acc[4 * q + 1] = fmaf(v, c4.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(v, c4.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(v, c4.w, acc[4 * q + 3]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < H; ++j) part[((size_t)blockIdx.x * KC + h * H + j) * kNB + a] = acc[j];
+    }
+    if (!grid_barrier(bar, (unsigned)G, status, kBarrierLimitNs)) return;
+    // B. entries [e0, e1) of P summed over the active CTAs' partials
+    {
+      const int e0 = (int)((int64_t)blockIdx.x * E / G), e1 = (int)((int64_t)(blockIdx.x + 1) * E / G);
+      for (int e = e0 + warp; e < e1; e += 8) {
+        float s = 0.f;
+        for (int z = c0 + lane; z < c1; z += 32) s += __ldcg(part + (size_t)z * E + e);
+        s = warp_sum_f(s);
+        if (lane == 0) pred[e] = s;
+      }
+    }
+    if (!grid_barrier(bar, (unsigned)G, status, kBarrierLimitNs)) return;
+    if (na > 0) {
+      for (int e = tid; e < E; e += 256) Ps[(e % kNB) * CS + e / kNB] = __ldcg(pred + e);
+      __syncthreads();
+      // W'(a, c) = sum_i T(i, a) P(i, c); T is upper triangular, so the sum
+      // stops at the warp's last row a
+      {
+        float acc[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) acc[j] = 0.f;
+        const int imax = a | 31;
+        for (int i = 0; i <= imax; ++i) {
+          const float t = Ts[a * kGS + i];
+          const float4* pr = reinterpret_cast<const float4*>(Ps + i * CS + h * H);
+#pragma unroll
+          for (int q = 0; q < H / 4; ++q) {
+            const float4 p4 = pr[q];
+            acc[4 * q + 0] = fmaf(t, p4.x, acc[4 * q + 0]);
+            acc[4 * q + 1] = fmaf(t, p4.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fmaf(t, p4.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fmaf(t, p4.w, acc[4 * q + 3]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < H; ++j) Ws[a * CS + h * H + j] = acc[j];
+      }
+      __syncthreads();
+      // C. C -= V_J W' on the active rows, eight columns per item
+      const int items = na * (KC / 8);
+      for (int e = tid; e < items; e += 256) {
+        const int rr = e % na, g8 = e / na;
+        float acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+        for (int col = 0; col < kNB; ++col) {
+          const float v = Vs[col * kQVS + rr];
+          const float4* wr = reinterpret_cast<const float4*>(Ws + col * CS + g8 * 8);
+          const float4 w0 = wr[0], w1 = wr[1];
+          acc[0] = fmaf(v, w0.x, acc[0]);
+          acc[1] = fmaf(v, w0.y, acc[1]);
+          acc[2] = fmaf(v, w0.z, acc[2]);
+          acc[3] = fmaf(v, w0.w, acc[3]);
+          acc[4] = fmaf(v, w1.x, acc[4]);
+          acc[5] = fmaf(v, w1.y, acc[5]);
+          acc[6] = fmaf(v, w1.z, acc[6]);
+          acc[7] = fmaf(v, w1.w, acc[7]);
+        }
+        float* cr = Cs + (off + rr) * CS + g8 * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cr[j] -= acc[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nrow * KC; e += 256) {
+    const int rr = e % nrow, c = e / nrow;
+    if (c < k) C[r_lo + rr + (int64_t)c * ldc] = Cs[rr * CS + c];
+  }
+}
+
 }  // namespace
 
 size_t outer_work_floats(int sms, int64_t m, int64_t n) {
@@ -285,7 +456,8 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     CT_LAUNCH_CHECK();
   }
   // W' = T^T W: T = S^{-1} once for the block, then one product per 64 columns.
-  float* Tb = Gp + (size_t)(2 * sms + 1) * kNB * kNB;
+  // (kept in the factor's per-block store, next to G, when there is one)
+  float* Tb = f->Tblk ? f->Tblk + (size_t)(J / kNB) * kNB * kNB : Gp + (size_t)(2 * sms + 1) * kNB * kNB;
   {
     LaunchScope ls(K_TW, s, (double)kNB * kNB * kNB / 3.0, 8.0 * kNB * kNB);
     static bool attr = false;
@@ -321,6 +493,44 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     return CT_OK;
   }
   return tc_update_presplit(Vr, Vrl, kNB, Wq, Wql, kNB, mr, nc, kNB, C, ld, split3, sms, f->status, s);
+}
+
+// Q^T C for the outer blocks [0, nblk) in one cooperative launch; returns
+// CT_ERR_UNSUPPORTED (nothing launched) when the factor keeps no T blocks,
+// k is outside 1..32, or the rows do not fit kQRC per CTA on this GPU.
+ct_status apply_qt_outer_persist(const ct_factor* f, float* C, int64_t ldc, int64_t k, int nblk, double* work,
+                                 size_t work_elems, int sms, cudaStream_t s) {
+  if (!f->Tblk || f->store != CT_F32 || k < 1 || k > 32 || nblk < 1 || (int64_t)nblk * kNB >= f->n)
+    return CT_ERR_UNSUPPORTED;
+  const int KC = k <= 16 ? 16 : 32;
+  const void* fn = KC == 16 ? (const void*)k_qt_outer<16> : (const void*)k_qt_outer<32>;
+  const size_t smem = (KC == 16 ? qt_outer_smem_floats<16>() : qt_outer_smem_floats<32>()) * sizeof(float);
+  CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
+  if (per_sm < 1) return CT_ERR_UNSUPPORTED;
+  const int grid = sms * per_sm;
+  const int64_t rows = (f->m + grid - 1) / grid;
+  if (rows > kQRC) return CT_ERR_UNSUPPORTED;
+  // work: partials [grid][KC][128], reduced P [KC][128], barrier counter
+  const size_t pfl = (size_t)grid * KC * kNB, rfl = (size_t)KC * kNB;
+  const size_t need_bytes = (pfl + rfl) * sizeof(float) + 2 * sizeof(unsigned long long) + 16;
+  if (need_bytes > work_elems * sizeof(double)) return CT_ERR_UNSUPPORTED;
+  float* part = (float*)work;
+  float* pred = part + pfl;
+  unsigned long long* bar = (unsigned long long*)(((uintptr_t)(pred + rfl) + 15) & ~(uintptr_t)15);
+  CT_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned long long), s));
+  const float* F = (const float*)f->F;
+  int64_t ld = f->ld, m = f->m, ldc_ = ldc;
+  const float* T = f->Tblk;
+  int nb_ = nblk, k_ = (int)k, rpc = (int)rows;
+  int* status = f->status;
+  void* args[] = {(void*)&F, (void*)&ld, (void*)&m, (void*)&T, (void*)&nb_, (void*)&C, (void*)&ldc_, (void*)&k_,
+                  (void*)&rpc, (void*)&part, (void*)&pred, (void*)&bar, (void*)&status};
+  LaunchScope ls(K_QT_OUTER, s, 4.0 * (double)nblk * kNB * (double)f->m * k,
+                 2.0 * (double)nblk * kNB * (double)f->m * 4.0);
+  CT_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
+  return CT_OK;
 }
 
 }  // namespace ctqr

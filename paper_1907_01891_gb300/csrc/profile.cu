@@ -68,7 +68,8 @@ const char* kNames[K_COUNT] = {"zero_fill",   "system_matrix", "panel_qr",  "ref
                                "reflector_tw", "block_update",  "trsm_diag", "copy",
                                "rank_check",  "col_norms",     "col_add",   "gemm_tn",
                                "col_axpy",    "tc_gemm",       "spmm",      "tile_runtime",
-                               "conv",        "gate",          "tc_update"};
+                               "conv",        "gate",          "tc_update",
+                               "qt_outer"};
 
 }  // namespace
 

@@ -136,15 +136,34 @@ __global__ void __launch_bounds__(1024) k_rank_check(const S* __restrict__ F, in
 //
 // The recursive scheme above issues about two launches per 64-row block; for
 // a few right-hand sides each launch is tiny and the solve is a chain of
-// launch latencies.  Here one persistent launch walks the block rows in
+// launch latencies.  Here one persistent launch walks 128-row blocks in
 // dependency order: a CTA takes the next block row i from a ticket counter
-// (bottom-up for R X = B, top-down for R^T Z = B), subtracts the products
-// with every finished block X_j as soon as that block's flag is set, solves
-// its 64 x 64 diagonal block and publishes X_i with a release store of flag i.
-// A CTA only waits for blocks whose tickets were taken earlier, by CTAs that
-// are running, so the launch always progresses; every wait is bounded (2 s,
-// then CT_ERR_TIMEOUT in the status word and the CTA leaves).
-constexpr int kPB = 64;  // block rows and the most right-hand sides per launch
+// (bottom-up for R X = B, top-down for R^T Z = B), inverts its diagonal
+// block R_ii while the blocks it depends on are still being solved,
+// subtracts the product with every finished block X_j as soon as that
+// block's flag is set, and forms X_i = R_ii^{-1} Y_i as one more product, so
+// that one block of the chain costs two 128 x 128 x k products rather than a
+// 128-step substitution.  (Multiplying by the inverted diagonal block trades
+// a little accuracy, bounded through the diagonal block's condition number,
+// for that parallelism.)  A CTA only waits for blocks whose tickets were
+// taken earlier, by CTAs that are running, so the launch always progresses;
+// every wait is bounded (2 s, then CT_ERR_TIMEOUT in the status word and the
+// CTA leaves).
+//
+// Work split of a product: thread (r, g) = (tid % 128, tid / 128) holds row
+// r of the 128 x 128 block operand for columns [32 g, 32 g + 32) in
+// registers and multiplies it with the matching 32 rows of the right-hand
+// sides, read from shared memory as broadcasts; the four partial rows are
+// then summed in a fixed order.
+constexpr int kPB = 64;          // most right-hand sides for the persistent solve
+constexpr int kQB = 128;         // block rows
+constexpr int kQT = 512;         // threads per CTA
+constexpr int kQK = 32;          // right-hand sides per launch
+constexpr int kQG = kQT / kQB;   // column groups of the block operand (4)
+constexpr int kQL = kQB / kQG;   // columns per group (32)
+constexpr int kQS = kQB + 1;     // stride of the 128 x 128 shared tiles
+constexpr int kXS = kQK + 4;     // stride of the right-hand-side tiles (16-byte rows)
+constexpr size_t kQSmemFloats = (size_t)2 * kQB * kQS + (size_t)2 * kQB * kXS;
 
 __device__ __forceinline__ int ld_acquire_i32(const int* p) {
   int v;
@@ -156,46 +175,87 @@ __device__ __forceinline__ void st_release_i32(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-template <int NC>
-__device__ __forceinline__ void block_product(float (*Rs)[kPB + 1], float (*Xs)[kPB + 1], float (*Ys)[kPB + 1],
-                                              int k, int tid) {
-  const int r4 = (tid % 16) * 4, cgp = tid / 16;
-  float acc[4][NC];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int w = 0; w < NC; ++w) acc[a][w] = 0.f;
-#pragma unroll 8
-  for (int l = 0; l < kPB; ++l) {
-    float rv[4], xv[NC];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) rv[a] = Rs[r4 + a][l];
-#pragma unroll
-    for (int w = 0; w < NC; ++w) xv[w] = Xs[l][cgp + 16 * w];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int w = 0; w < NC; ++w) acc[a][w] = fmaf(rv[a], xv[w], acc[a][w]);
+// X = U^{-1} for the upper triangular 128 x 128 U, both column-major with
+// stride kQS in shared memory, by block doubling: the diagonal reciprocals,
+// then for s = 1, 2, 4, ... and every pair of diagonal blocks A = [p, p+s),
+// C = [p+s, p+2s): X_AC = -X_A (U_AC X_C).  tmp: 4096 floats.
+__device__ void tri_inv_f32(const float* __restrict__ U, float* __restrict__ X, float* __restrict__ tmp,
+                            int tid) {
+  for (int e = tid; e < kQB * kQB; e += kQT) {
+    const int rr = e % kQB, cc = e / kQB;
+    X[cc * kQS + rr] = rr == cc ? 1.f / U[cc * kQS + cc] : 0.f;
   }
-#pragma unroll
-  for (int w = 0; w < NC; ++w)
-    if (cgp + 16 * w < k)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) Ys[r4 + a][cgp + 16 * w] -= acc[a][w];
+  __syncthreads();
+  for (int s = 1; s < kQB; s *= 2) {
+    const int ss = s * s, ent = (kQB / (2 * s)) * ss;
+    for (int e = tid; e < ent; e += kQT) {
+      const int pr = e / ss, rc = e % ss, rr = rc % s, c = rc / s;
+      const int p0 = pr * 2 * s, gi = p0 + rr, gc = p0 + s + c;
+      float acc = 0.f;
+      for (int kk = 0; kk <= c; ++kk)  // X_C is upper triangular
+        acc = fmaf(U[(p0 + s + kk) * kQS + gi], X[gc * kQS + p0 + s + kk], acc);
+      tmp[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ent; e += kQT) {
+      const int pr = e / ss, rc = e % ss, rr = rc % s, c = rc / s;
+      const int p0 = pr * 2 * s, gi = p0 + rr, gc = p0 + s + c;
+      float acc = 0.f;
+      for (int kk = rr; kk < s; ++kk)  // X_A is upper triangular
+        acc = fmaf(X[(p0 + kk) * kQS + gi], tmp[pr * ss + c * s + kk], acc);
+      X[gc * kQS + gi] = -acc;
+    }
+    __syncthreads();
+  }
 }
 
-template <bool TRANS>
-__global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ F, int64_t ld, int64_t n,
-                                                      float* __restrict__ B, int64_t ldb, int k,
-                                                      int* __restrict__ flags, int* __restrict__ ticket,
-                                                      int* __restrict__ status) {
-  extern __shared__ float psm[];
-  float (*Rs)[kPB + 1] = (float (*)[kPB + 1])psm;                       // an off-diagonal block, then R_ii
-  float (*Xs)[kPB + 1] = (float (*)[kPB + 1])(psm + kPB * (kPB + 1));   // X_j [row][column]
-  float (*Ys)[kPB + 1] = (float (*)[kPB + 1])(psm + 2 * kPB * (kPB + 1));  // B_i minus the products so far
+// Ps[g][c][r] = sum_u a[u] Y[32 g + u][c] for c < 4 NC4 (zero when the
+// thread's operand row is known to be zero).
+template <int NC4>
+__device__ __forceinline__ void row_partials(const float (&a)[kQL], const float* __restrict__ Y,
+                                             float* __restrict__ Ps, int r, int g, bool live) {
+  float acc[4 * NC4];
+#pragma unroll
+  for (int c = 0; c < 4 * NC4; ++c) acc[c] = 0.f;
+  if (live) {
+#pragma unroll
+    for (int u = 0; u < kQL; ++u) {
+      const float4* y = reinterpret_cast<const float4*>(Y + (kQL * g + u) * kXS);
+#pragma unroll
+      for (int q = 0; q < NC4; ++q) {
+        const float4 v = y[q];
+        acc[4 * q + 0] = fmaf(a[u], v.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(a[u], v.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(a[u], v.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(a[u], v.w, acc[4 * q + 3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4 * NC4; ++c) Ps[(g * kQK + c) * kQB + r] = acc[c];
+}
+
+// The four partials of entry (r, c), summed in a fixed order.
+__device__ __forceinline__ float sum_parts(const float* __restrict__ Ps, int r, int c) {
+  return ((Ps[c * kQB + r] + Ps[(kQK + c) * kQB + r]) + Ps[(2 * kQK + c) * kQB + r]) +
+         Ps[(3 * kQK + c) * kQB + r];
+}
+
+template <bool TRANS, int NC4>
+__global__ void __launch_bounds__(kQT, 1) k_trsm_persist(const float* __restrict__ F, int64_t ld, int64_t n,
+                                                         float* __restrict__ B, int64_t ldb, int k,
+                                                         int* __restrict__ flags, int* __restrict__ ticket,
+                                                         int* __restrict__ status) {
+  extern __shared__ __align__(16) float psm[];
+  float* St = psm;               // a staged 128 x 128 block: op(R)_ij(r, l) at St[l * kQS + r]
+  float* Dm = St + kQB * kQS;    // R_ii^{-1} (column-major), then the partial products Ps[g][c][r]
+  float* Ps = Dm;
+  float* Xs = Dm + kQB * kQS;    // X_j [row][column]
+  float* Ys = Xs + kQB * kXS;    // Y_i minus the products so far
   __shared__ int s_t, s_fail;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nb = (int)((n + kPB - 1) / kPB);
+  const int tid = threadIdx.x, r = tid % kQB, g = tid / kQB;
+  const int nb = (int)((n + kQB - 1) / kQB);
+  constexpr int kc4 = 4 * NC4;   // columns carried (>= k)
   for (;;) {
     if (tid == 0) {
       s_t = atomicAdd(ticket, 1);
@@ -205,39 +265,58 @@ __global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ 
     const int t = s_t;
     if (t >= nb) return;
     const int i = TRANS ? t : nb - 1 - t;
-    const int64_t i0 = (int64_t)i * kPB;
-    const int ni = (int)(n - i0 < kPB ? n - i0 : kPB);
-    // B_i, and the diagonal block R_ii (upper part) held in registers until
-    // the end so that loading it is off the dependency chain
-    float dreg[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int e = tid + 256 * u, r = e % kPB, c = e / kPB;
-      Ys[r][c] = (r < ni && c < k) ? __ldcg(B + i0 + r + c * ldb) : 0.f;
-      dreg[u] = (r < ni && c < ni && r <= c) ? F[i0 + r + (i0 + c) * ld] : 0.f;
-    }
+    const int64_t i0 = (int64_t)i * kQB;
+    const int ni = (int)(n - i0 < kQB ? n - i0 : kQB);
     const int deps = TRANS ? i : nb - 1 - i;
-    // the 64 x 64 block op(R)_{ij} for contribution q, 16 elements per
-    // thread held in registers so its loads overlap the previous product:
-    // element u is (r, c) = (e % 64, e / 64) of the stored block, e = tid + 256 u
-    float rreg[16];
-    auto load_r = [&](int q) {
-      const int j = TRANS ? q : nb - 1 - q;
-      const int64_t j0 = (int64_t)j * kPB;
-      const int nj = (int)(n - j0 < kPB ? n - j0 : kPB);
+
+    // R_ii: upper part (the rows below the diagonal hold reflectors), the
+    // identity past ni; then its inverse
+    for (int e = tid; e < kQB * kQB; e += kQT) {
+      const int rr = e % kQB, cc = e / kQB;
+      const bool v = rr <= cc && cc < ni;
+      cp_async_f32(St + cc * kQS + rr, v ? F + i0 + rr + (i0 + cc) * ld : F, v);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid >= ni && tid < kQB) St[tid * kQS + tid] = 1.f;
+    __syncthreads();
+    tri_inv_f32(St, Dm, Xs, tid);
+    // this thread's row of op(R_ii)^{-1}: R_ii^{-1} (upper) or R_ii^{-T} (lower)
+    float d[kQL];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = tid + 256 * u, a = e % kPB, b = e / kPB;
-        // !TRANS: R(i0 + a, j0 + b); TRANS: R(j0 + a, i0 + b) (contiguous along a)
-        const bool ok = TRANS ? (a < nj && b < ni) : (a < ni && b < nj);
-        rreg[u] = ok ? __ldcg(TRANS ? F + j0 + a + (i0 + b) * ld : F + i0 + a + (j0 + b) * ld) : 0.f;
+    for (int u = 0; u < kQL; ++u) d[u] = TRANS ? Dm[r * kQS + kQL * g + u] : Dm[(kQL * g + u) * kQS + r];
+    const bool live = TRANS ? (kQL * g <= r) : (kQL * g + kQL - 1 >= r);  // warp-uniform
+    __syncthreads();  // Dm and St free
+    for (int e = tid; e < kQB * kc4; e += kQT) {
+      const int rr = e % kQB, c = e / kQB;
+      Ys[rr * kXS + c] = (rr < ni && c < k) ? __ldcg(B + i0 + rr + (int64_t)c * ldb) : 0.f;
+    }
+    // op(R)_ij for dependency q into St: !TRANS R(i0 + a, j0 + b) = (r, l) = (a, b);
+    // TRANS R(j0 + a, i0 + b) = (r, l) = (b, a); a runs along memory
+    auto stage = [&](int q) {
+      const int j = TRANS ? q : nb - 1 - q;
+      const int64_t j0 = (int64_t)j * kQB;
+      const int nj = (int)(n - j0 < kQB ? n - j0 : kQB);
+      for (int e = tid; e < kQB * kQB; e += kQT) {
+        const int a = e % kQB, b = e / kQB;
+        const int rr = TRANS ? b : a, l = TRANS ? a : b;
+        const bool v = rr < ni && l < nj;
+        const float* src = TRANS ? F + j0 + a + (i0 + b) * ld : F + i0 + a + (j0 + b) * ld;
+        cp_async_f32(St + l * kQS + rr, v ? src : F, v);
       }
+      cp_async_commit();
     };
-    if (deps > 0) load_r(0);
+    if (deps > 0) stage(0);
     for (int q = 0; q < deps; ++q) {
       const int j = TRANS ? q : nb - 1 - q;  // finished blocks first
-      const int64_t j0 = (int64_t)j * kPB;
-      const int nj = (int)(n - j0 < kPB ? n - j0 : kPB);
+      const int64_t j0 = (int64_t)j * kQB;
+      const int nj = (int)(n - j0 < kQB ? n - j0 : kQB);
+      cp_async_wait_all();
+      __syncthreads();
+      float a[kQL];
+#pragma unroll
+      for (int u = 0; u < kQL; ++u) a[u] = St[(kQL * g + u) * kQS + r];
       if (tid == 0) {
         const uint64_t start = globaltimer_ns();
         while (ld_acquire_i32(flags + j) == 0) {
@@ -250,96 +329,36 @@ __global__ void __launch_bounds__(256) k_trsm_persist(const float* __restrict__ 
           __nanosleep(32);
         }
       }
+      __syncthreads();  // X_j published; St read
+      if (s_fail) {
+        cp_async_wait_all();
+        return;
+      }
+      for (int e = tid; e < kQB * kc4; e += kQT) {
+        const int l = e % kQB, c = e / kQB;
+        Xs[l * kXS + c] = (l < nj && c < k) ? __ldcg(B + j0 + l + (int64_t)c * ldb) : 0.f;
+      }
+      if (q + 1 < deps) stage(q + 1);
       __syncthreads();
-      if (s_fail) return;
-      float xreg[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = tid + 256 * u, r = e % kPB, c = e / kPB;
-        xreg[u] = (r < nj && c < k) ? __ldcg(B + j0 + r + c * ldb) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = tid + 256 * u, a = e % kPB, b = e / kPB;
-        // Rs[r][c] = op(R)_{ij}(r, c)
-        if (TRANS) Rs[b][a] = rreg[u];
-        else Rs[a][b] = rreg[u];
-        Xs[a][b] = xreg[u];
-      }
+      row_partials<NC4>(a, Xs, Ps, r, g, true);
       __syncthreads();
-      if (q + 1 < deps) load_r(q + 1);
-      // Ys -= Rs Xs with a 4 x NC register tile per thread: rows
-      // 4 * (tid % 16) + 0..3, columns tid / 16 + 16 * w (w < NC, c < k);
-      // NC = ceil(k / 16) so that a few right-hand sides cost few products
-      switch ((k + 15) / 16) {
-        case 1: block_product<1>(Rs, Xs, Ys, k, tid); break;
-        case 2: block_product<2>(Rs, Xs, Ys, k, tid); break;
-        case 3: block_product<3>(Rs, Xs, Ys, k, tid); break;
-        default: block_product<4>(Rs, Xs, Ys, k, tid); break;
-      }
-      __syncthreads();
-    }
-    // diagonal block: X_i = R_ii^{-1} Ys (or R_ii^{-T}); one warp per column,
-    // with the reciprocals of the diagonal computed once
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int e = tid + 256 * u, r = e % kPB, c = e / kPB;
-      Rs[r][c] = dreg[u];
-    }
-    __syncthreads();
-    float* rdiag = &Xs[0][0];  // free now
-    if (tid < ni) rdiag[tid] = 1.f / Rs[tid][tid];
-    __syncthreads();
-    // warp w solves columns w and w + 8 (then w + 16, w + 24, ...) in pairs,
-    // interleaving the two dependency chains
-    for (int c = warp; c < k; c += 16) {
-      const bool two = c + 8 < k;
-      const int c2 = two ? c + 8 : c;
-      float y0 = lane < ni ? Ys[lane][c] : 0.f;
-      float y1 = lane + 32 < ni ? Ys[lane + 32][c] : 0.f;
-      float u0 = lane < ni ? Ys[lane][c2] : 0.f;
-      float u1 = lane + 32 < ni ? Ys[lane + 32][c2] : 0.f;
-      if (!TRANS) {
-        for (int q = ni - 1; q >= 0; --q) {
-          const float rq = rdiag[q];
-          const float xq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31) * rq;
-          const float zq = __shfl_sync(0xffffffffu, q < 32 ? u0 : u1, q & 31) * rq;
-          if (q < 32) {
-            if (lane == q) { y0 = xq; u0 = zq; }
-          } else if (lane == q - 32) {
-            y1 = xq;
-            u1 = zq;
-          }
-          const float ra = Rs[lane][q], rb = Rs[lane + 32][q];
-          if (lane < q) { y0 -= ra * xq; u0 -= ra * zq; }
-          if (lane + 32 < q) { y1 -= rb * xq; u1 -= rb * zq; }
-        }
-      } else {
-        for (int q = 0; q < ni; ++q) {
-          const float rq = rdiag[q];
-          const float xq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31) * rq;
-          const float zq = __shfl_sync(0xffffffffu, q < 32 ? u0 : u1, q & 31) * rq;
-          if (q < 32) {
-            if (lane == q) { y0 = xq; u0 = zq; }
-          } else if (lane == q - 32) {
-            y1 = xq;
-            u1 = zq;
-          }
-          const float ra = Rs[q][lane], rb = Rs[q][lane + 32];
-          if (lane > q && lane < ni) { y0 -= ra * xq; u0 -= ra * zq; }
-          if (lane + 32 > q && lane + 32 < ni) { y1 -= rb * xq; u1 -= rb * zq; }
-        }
-      }
-      if (lane < ni) B[i0 + lane + c * ldb] = y0;
-      if (lane + 32 < ni) B[i0 + lane + 32 + c * ldb] = y1;
-      if (two) {
-        if (lane < ni) B[i0 + lane + c2 * ldb] = u0;
-        if (lane + 32 < ni) B[i0 + lane + 32 + c2 * ldb] = u1;
+      for (int e = tid; e < kQB * kc4; e += kQT) {
+        const int rr = e % kQB, c = e / kQB;
+        Ys[rr * kXS + c] -= sum_parts(Ps, rr, c);
       }
     }
-    __threadfence();
+    __syncthreads();  // Y_i complete
+    row_partials<NC4>(d, Ys, Ps, r, g, live);
     __syncthreads();
-    if (tid == 0) st_release_i32(flags + i, 1);
+    for (int e = tid; e < kQB * kc4; e += kQT) {
+      const int rr = e % kQB, c = e / kQB;
+      if (rr < ni && c < k) B[i0 + rr + (int64_t)c * ldb] = sum_parts(Ps, rr, c);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release_i32(flags + i, 1);
+    }
   }
 }
 
@@ -430,34 +449,44 @@ bool persist_enabled() {
   return on;
 }
 
-// One persistent launch per group of up to 64 columns (FP32 R and B).
+// One persistent launch per group of up to 32 columns (FP32 R and B).
+template <bool TRANS>
+const void* persist_kernel(int kc) {
+  if (kc <= 8) return (const void*)k_trsm_persist<TRANS, 2>;
+  if (kc <= 16) return (const void*)k_trsm_persist<TRANS, 4>;
+  return (const void*)k_trsm_persist<TRANS, 8>;
+}
+
 ct_status trsm_persist(const ct_factor* f, float* B, int64_t ldb, int64_t k, bool transpose, cudaStream_t s) {
   DeviceInfo di;
   ct_status st = device_info(&di);
   if (st != CT_OK) return st;
-  const int nb = (int)((f->n + kPB - 1) / kPB);
+  const int nb = (int)((f->n + kQB - 1) / kQB);
   int* flags = nullptr;
   const size_t words = (size_t)nb + 4;
   CT_CUDA_TRY(cudaMallocAsync((void**)&flags, words * sizeof(int), s));
   struct Free { int* p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{flags, s};
-  const size_t smem = (size_t)3 * kPB * (kPB + 1) * sizeof(float);
-  const void* fn = transpose ? (const void*)k_trsm_persist<true> : (const void*)k_trsm_persist<false>;
-  CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
-  int grid = di.sms * (per_sm > 0 ? per_sm : 1);
-  if (grid > nb) grid = nb;
-  for (int64_t c0 = 0; c0 < k; c0 += kPB) {
-    const int kc = (int)(k - c0 < kPB ? k - c0 : kPB);
+  const size_t smem = kQSmemFloats * sizeof(float);
+  for (int64_t c0 = 0; c0 < k; c0 += kQK) {
+    const int kc = (int)(k - c0 < kQK ? k - c0 : kQK);
+    const void* fn = transpose ? persist_kernel<true>(kc) : persist_kernel<false>(kc);
+    CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kQT, smem));
+    if (per_sm < 1) return CT_ERR_UNSUPPORTED;
+    int grid = di.sms * per_sm;
+    if (grid > nb) grid = nb;
     CT_CUDA_TRY(cudaMemsetAsync(flags, 0, words * sizeof(int), s));
     LaunchScope ls(K_TRSM_DIAG, s, (double)f->n * f->n * kc, (double)f->n * f->n * 2.0 + 8.0 * f->n * kc);
-    if (transpose)
-      k_trsm_persist<true><<<grid, 256, smem, s>>>((const float*)f->F, f->ld, f->n, B + c0 * ldb, ldb, kc, flags,
-                                                flags + nb, f->status);
-    else
-      k_trsm_persist<false><<<grid, 256, smem, s>>>((const float*)f->F, f->ld, f->n, B + c0 * ldb, ldb, kc, flags,
-                                                 flags + nb, f->status);
-    CT_LAUNCH_CHECK();
+    const float* F = (const float*)f->F;
+    int64_t ld = f->ld, n = f->n, ldb_ = ldb;
+    float* Bc = B + c0 * ldb;
+    int kc_ = kc;
+    int* ticket = flags + nb;
+    int* status = f->status;
+    void* args[] = {(void*)&F, (void*)&ld, (void*)&n, (void*)&Bc, (void*)&ldb_, (void*)&kc_,
+                    (void*)&flags, (void*)&ticket, (void*)&status};
+    CT_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kQT), args, smem, s));
   }
   return CT_OK;
 }

@@ -110,6 +110,7 @@ SIGNATURES = {
     "ct_factor_status": ([_VP, _VP], _I),
     "ct_factor_copy": ([_VP, _VP, _I64, _VP, _VP], _I),
     "ct_apply_qt": ([_VP, _VP, _I64, _I64, _VP], _I),
+    "ct_apply_qt_f32": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_apply_qt_noalloc": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_trsm_solve": ([_VP, _VP, _I64, _I64, _VP], _I),
     "ct_trsm_solve_f32": ([_VP, _VP, _I64, _I64, _I, _VP], _I),
@@ -318,6 +319,12 @@ def apply_qt_noalloc(f: Factor, B: torch.Tensor) -> torch.Tensor:
     """B <- Q^T B in place without any device allocation (k <= 64 columns)."""
     _check(load().ct_apply_qt_noalloc(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()),
            "ct_apply_qt_noalloc")
+    return B
+
+
+def apply_qt_f32(f: Factor, B: torch.Tensor) -> torch.Tensor:
+    """B <- Q^T B in place in FP32 (m x k FP32 column-major) with a mixed-precision factor."""
+    _check(load().ct_apply_qt_f32(f.handle, B.data_ptr(), _ld(B), B.shape[1], _stream()), "ct_apply_qt_f32")
     return B
 
 

@@ -59,5 +59,6 @@ def test_null_arguments_rejected_without_gpu():
     out = ctypes.c_void_p()
     assert lib.ct_qr_factor(None, 0, 10, 5, 10, 0, None, ctypes.byref(out), None) == ctqr.CT_ERR_INVALID
     assert lib.ct_apply_qt(None, None, 1, 1, None) == ctqr.CT_ERR_INVALID
+    assert lib.ct_apply_qt_f32(None, None, 1, 1, None) == ctqr.CT_ERR_INVALID
     assert lib.ct_trsm_solve(None, None, 1, 1, None) == ctqr.CT_ERR_INVALID
     lib.ct_factor_destroy(None)

@@ -396,6 +396,37 @@ def test_tf32_factor_qt_by_outer_blocks(shape, k):
     assert abs(np.linalg.norm(Y) - np.linalg.norm(B)) <= 1e-5 * np.linalg.norm(B)  # orthogonal invariance
 
 
+@pytest.mark.parametrize("prec,shape,k", [(ctqr.Prec.TF32, (1200, 520), 17), (ctqr.Prec.TF32, (700, 300), 3),
+                                          (ctqr.Prec.TF32, (700, 300), 40), (ctqr.Prec.TF32, (24500, 260), 5),
+                                          (ctqr.Prec.F32, (500, 200), 4)])
+def test_fp32_qt_matches_oracle_with_the_factors_reflectors(prec, shape, k):
+    """ct_apply_qt_f32 (Q^T B in FP32, the refinement's first solve) against
+    the oracle's reflector-by-reflector Q^T built from the factor's own V and
+    tau, i.e. the same orthogonal matrix in FP64.  TF32 factors with k <= 32
+    whose rows fit 160 per SM take the one-launch path over all 128-column
+    outer blocks (one qt_outer launch); k > 32, taller matrices and one-level
+    factors take the block-by-block path (none)."""
+    m, n = shape
+    A = I.random_matrix(m, n, seed=30 + n)
+    B = I.random_matrix(m, k, seed=31 + n).astype(np.float32)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A, dtype=torch.float32), prec=prec)
+    F, tau = ctqr.factor_matrix(f)
+    Yo = O.apply_qt(_np(F).astype(np.float64), _np(tau), B.astype(np.float64))
+    Bg = ctqr.to_colmajor(B, dtype=torch.float32)
+    torch.cuda.synchronize()
+    ctqr.profile_reset()
+    ctqr.profile_enable(True)
+    ctqr.apply_qt_f32(f, Bg)
+    torch.cuda.synchronize()
+    ctqr.profile_enable(False)
+    launches = {p_["name"]: p_["launches"] for p_ in ctqr.profile_kernels()}
+    Y = _np(Bg).astype(np.float64)
+    assert np.linalg.norm(Y - Yo) <= 2e-5 * np.linalg.norm(B), np.linalg.norm(Y - Yo) / np.linalg.norm(B)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    one_launch = prec == ctqr.Prec.TF32 and k <= 32 and -(-m // sms) <= 160 and n > 128
+    assert launches.get("qt_outer", 0) == (1 if one_launch else 0), launches
+
+
 def test_tf32_factor_with_lookahead_refines_to_fp64(monkeypatch):
     """The opt-in look-ahead (deferred outer-block updates on a second stream
     while the next panels run on reserved SMs) gives the same solution."""
