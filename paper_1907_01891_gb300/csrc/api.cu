@@ -610,7 +610,7 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   if ((st = dev_alloc(&f->tau, (size_t)n)) != CT_OK ||
       (st = dev_alloc(&f->T, (size_t)np * f->nb * f->nb)) != CT_OK ||
       (st = dev_alloc(&f->status, 1)) != CT_OK ||
-      (st = dev_alloc(&f->barrier, 2)) != CT_OK ||
+      (st = dev_alloc(&f->barrier, 3)) != CT_OK ||
       (st = dev_alloc(&f->partials, f->partials_elems)) != CT_OK ||
       (tc && (st = dev_alloc(&f->Gblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK) ||
       (tc && (st = dev_alloc(&f->Tblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK)) {
@@ -645,6 +645,11 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
     a.mr = m - j0;
     a.nc = cend - j0 - nbp;
     a.fp32_math = store == CT_F32;
+    // two-level factors: the inner panels' updates in one launch when they fit
+    if (tc && f->panel_cap == 0) {
+      const ct_status u = inner_update_persist(f, j0, nbp, cend, Tp, (double*)work.p, work_elems, di.sms, s);
+      if (u != CT_ERR_UNSUPPORTED) return u;
+    }
     return apply_block_reflector(a, (double*)work.p, work_elems, di.sms, s);
   };
   if (!tc) {

@@ -96,7 +96,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
   K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_TC_UPDATE,
-  K_QT_OUTER, K_COUNT
+  K_QT_OUTER, K_INNER, K_COUNT
 };
 
 // Graph capture: launches made between begin and end are recorded into
@@ -196,6 +196,11 @@ ct_status apply_block_reflector(const ReflectorArgs& a, double* work, size_t wor
 // two-level factor, T given through its UT-transform form S = T^{-1} =
 // diag(1/tau) + striu(G), G = V^T V (gemm_simt.cu); work as for
 // apply_block_reflector.
+// One inner panel's block reflector (columns [j0, j0+nbp), T at Tp) applied to
+// the columns [j0+nbp, cend) of an FP32-stored factor in one cooperative
+// launch; CT_ERR_UNSUPPORTED (nothing launched) when the shape does not fit.
+ct_status inner_update_persist(ct_factor* f, int64_t j0, int nbp, int64_t cend, const double* Tp, double* work,
+                               size_t work_elems, int sms, cudaStream_t s);
 // Q^T C (FP32 C and arithmetic, 1 <= k <= 32) for the outer blocks [0, nblk)
 // of a two-level factor in one cooperative launch; CT_ERR_UNSUPPORTED when
 // the factor or the shape does not allow it (nothing launched).

@@ -89,14 +89,16 @@ __global__ void __launch_bounds__(256) k_reduce_gram(const float* __restrict__ G
 constexpr int kGS = kNB + 1;  // leading dimension of the 128 x 128 matrices in shared memory
 constexpr size_t kTinvSmem = (size_t)3 * kNB * kGS * sizeof(float);
 
-__global__ void __launch_bounds__(256) k_tinv(const float* __restrict__ Gred, const double* __restrict__ tau, int nbo,
-                                              float* __restrict__ Tout) {
+constexpr int kTinvThreads = 1024;
+
+__global__ void __launch_bounds__(kTinvThreads) k_tinv(const float* __restrict__ Gred, const double* __restrict__ tau,
+                                                       int nbo, float* __restrict__ Tout) {
   extern __shared__ float sm[];
   float* S = sm;              // S(i, j) = G(i, j) for i < j
   float* X = S + kNB * kGS;   // T
   float* Y = X + kNB * kGS;   // S_AC T_C
   const int tid = threadIdx.x;
-  for (int e = tid; e < kNB * kNB; e += 256) {
+  for (int e = tid; e < kNB * kNB; e += kTinvThreads) {
     const int i = e % kNB, j = e / kNB;
     S[i + j * kGS] = __ldcg(Gred + e);
     X[i + j * kGS] = (i == j && i < nbo) ? (float)tau[i] : 0.f;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(256) k_tinv(const float* __restrict__ Gred, co
   __syncthreads();
   for (int s = 1; s < kNB; s *= 2) {
     const int ent = (kNB / (2 * s)) * s * s;
-    for (int e = tid; e < ent; e += 256) {
+    for (int e = tid; e < ent; e += kTinvThreads) {
       const int pr = e / (s * s), rr = e % (s * s), r = rr % s, c = rr / s;
       const int p0 = pr * 2 * s, gi = p0 + r, gc = p0 + s + c;
       float acc = 0.f;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(256) k_tinv(const float* __restrict__ Gred, co
       Y[gi + gc * kGS] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < ent; e += 256) {
+    for (int e = tid; e < ent; e += kTinvThreads) {
       const int pr = e / (s * s), rr = e % (s * s), r = rr % s, c = rr / s;
       const int p0 = pr * 2 * s, gi = p0 + r, gc = p0 + s + c;
       float acc = 0.f;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(256) k_tinv(const float* __restrict__ Gred, co
     }
     __syncthreads();
   }
-  for (int e = tid; e < kNB * kNB; e += 256) {
+  for (int e = tid; e < kNB * kNB; e += kTinvThreads) {
     const int i = e % kNB, j = e / kNB;
     Tout[e] = X[i + j * kGS];
   }
@@ -142,31 +144,47 @@ __global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, 
   float* Ws = Ts + kNB * kNB;   // Ws[k * kTC + c] = W(k, c0 + c)
   const int tid = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * kTC;
-  for (int e0 = tid; e0 < kNB * kNB; e0 += 256 * 8) {
-    float v[8];
+  // T: 64 elements per thread, 16 loads in flight at a time
+  for (int e0 = tid; e0 < kNB * kNB; e0 += 256 * 16) {
+    float v[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldcg(T + e0 + 256 * u);  // T(k, r) at k + r * kNB
+    for (int u = 0; u < 16; ++u) v[u] = __ldcg(T + e0 + 256 * u);  // T(k, r) at k + r * kNB
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 16; ++u) {
       const int e = e0 + 256 * u, k = e % kNB, r = e / kNB;
       Ts[k * kNB + r] = v[u];
     }
   }
-  for (int e0 = tid; e0 < kNB * kTC; e0 += 256 * 4) {
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int z = 0; z < wsplits; ++z) {
-      float w[4];
+  // the W tile summed over the splits in order: 32 elements per thread in two
+  // halves, the loads of two splits in flight at a time
+#pragma unroll 1
+  for (int hv = 0; hv < 2; ++hv) {
+    float v[16];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = e0 + 256 * u, k = e % kNB, c = e / kNB;
-        w[u] = c0 + c < nc ? __ldcg(Wp + z * wstride + k + (c0 + c) * kNB) : 0.f;
+    for (int u = 0; u < 16; ++u) v[u] = 0.f;
+    int z = 0;
+    for (; z + 2 <= wsplits; z += 2) {
+      float w0[16], w1[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
+        const bool ok = c0 + c < nc;
+        w0[u] = ok ? __ldcg(Wp + z * wstride + k + (c0 + c) * kNB) : 0.f;
+        w1[u] = ok ? __ldcg(Wp + (z + 1) * wstride + k + (c0 + c) * kNB) : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] += w[u];
+      for (int u = 0; u < 16; ++u) v[u] = (v[u] + w0[u]) + w1[u];
+    }
+    for (; z < wsplits; ++z) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
+        v[u] += c0 + c < nc ? __ldcg(Wp + z * wstride + k + (c0 + c) * kNB) : 0.f;
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + 256 * u, k = e % kNB, c = e / kNB;
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
       Ws[k * kTC + c] = v[u];
     }
   }
@@ -466,7 +484,7 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
       CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplyTtSmem));
       attr = true;
     }
-    k_tinv<<<1, 256, kTinvSmem, s>>>(Gred, f->tau + J, nbo, Tb);
+    k_tinv<<<1, kTinvThreads, kTinvSmem, s>>>(Gred, f->tau + J, nbo, Tb);
     CT_LAUNCH_CHECK();
   }
   {

@@ -703,7 +703,8 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   a.gram_part = f->partials + (size_t)2 * (di.sms + 1) * 2 * kMaxNb;
   a.bar = f->barrier;
   a.status = f->status;
-  CT_CUDA_TRY(cudaMemsetAsync(f->barrier, 0, 2 * sizeof(unsigned long long), s));
+  // the panel's two words and the third, used by the inner update that follows
+  CT_CUDA_TRY(cudaMemsetAsync(f->barrier, 0, 3 * sizeof(unsigned long long), s));
   void* args[] = {&a};
   LaunchScope ls(K_PANEL, s, 3.0 * (double)mr * nbp * nbp, 2.0 * (double)mr * nbp * sizeof(S));
   CT_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPT), args, smem, s));

@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // latency is paid once per tile, not once per column.
 // ---------------------------------------------------------------------------
 constexpr int kUpdThreads = 384;
+constexpr size_t kUpdCbufBytes = (size_t)256 * 64 * sizeof(float);  // 64 columns per epilogue thread
 
 struct UpdArgs {
   int64_t M, N, K;
@@ -432,6 +433,23 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     }
   } else if (warp >= 4) {
     const int lg = warp & 3, half = (warp - 4) >> 2;
+    // this thread's slice of the next tile's C (row, 64 columns) is copied
+    // into its own part of cbuf (element j at j * 256 + et) while the current
+    // tile waits for its accumulator and is stored
+    const int et = threadIdx.x - 128;
+    float* cbuf = (float*)(smem + STAGES * STAGE_BYTES + 256);
+    auto prefetch = [&](int64_t t) {
+      const int64_t m0 = (t % args.mtiles) * kBM, n0 = (t / args.mtiles) * kBM;
+      const int64_t row = m0 + lg * 32 + lane, c0 = n0 + half * 64;
+      const bool rok = row < args.M;
+#pragma unroll 16
+      for (int j = 0; j < 64; ++j) {
+        const bool v = rok && c0 + j < args.N;
+        cp_async_f32(cbuf + j * 256 + et, v ? args.C + row + (c0 + j) * args.ldc : args.C, v);
+      }
+      cp_async_commit();
+    };
+    if ((int64_t)blockIdx.x < ntile) prefetch(blockIdx.x);
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
       const int acc = it & 1, ua = it >> 1;
@@ -440,10 +458,14 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
       const int64_t c0 = n0 + half * 64;
       const bool rok = row < args.M;
       float c[64];
+      cp_async_wait_all();
 #pragma unroll
-      for (int j = 0; j < 64; ++j)
-        c[j] = (rok && c0 + j < args.N) ? args.C[row + (c0 + j) * args.ldc] : 0.f;
-      if (!mbar_wait(&tfull[acc], (uint32_t)(ua & 1), args.status)) break;
+      for (int j = 0; j < 64; ++j) c[j] = cbuf[j * 256 + et];
+      if (t + gridDim.x < ntile) prefetch(t + gridDim.x);
+      if (!mbar_wait(&tfull[acc], (uint32_t)(ua & 1), args.status)) {
+        cp_async_wait_all();
+        break;
+      }
       tc_fence_after();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -524,7 +546,8 @@ ct_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& 
 template <bool SPLIT3, int STAGES>
 ct_status launch_upd(const CUtensorMap* maps, const UpdArgs& a, int sms, cudaStream_t s) {
   constexpr size_t STAGE_BYTES = (size_t)kBM * kBK * 4 * (SPLIT3 ? 4 : 2);
-  const size_t smem = STAGES * STAGE_BYTES + 1024 + 256;
+  // operand stages, alignment slack, barriers, and the epilogue's C buffer
+  const size_t smem = STAGES * STAGE_BYTES + 1024 + 256 + kUpdCbufBytes;
   static bool attr_done = false;
   if (!attr_done) {
     CT_CUDA_TRY(cudaFuncSetAttribute(k_tc_update<SPLIT3, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -571,8 +594,8 @@ ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, cons
   a.ntiles = (N + kBM - 1) / kBM;
   a.status = status;
   LaunchScope ls(K_TC_UPDATE, s, 2.0 * M * N * K, 4.0 * ((double)K * (M + N) * (split3 ? 2 : 1) + 2.0 * M * N));
-  if (split3) return launch_upd<true, 3>(maps, a, sms, s);
-  return launch_upd<false, 6>(maps, a, sms, s);
+  if (split3) return launch_upd<true, 2>(maps, a, sms, s);
+  return launch_upd<false, 4>(maps, a, sms, s);
 }
 
 // C (M x N) = / -= A^T B on the tensor cores; see the file comment.

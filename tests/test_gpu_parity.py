@@ -280,14 +280,28 @@ def test_reconstruct_scan_host_and_device_buffers_agree():
 
 
 # ---------------------------------------------------------------- tensor-core factor
-@pytest.mark.parametrize("shape", [(300, 200), (700, 300), (1000, 513)])
+@pytest.mark.parametrize("shape", [(300, 200), (700, 300), (1000, 513), (49000, 150)])
 def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape):
     """3xTF32 outer updates give an FP32-quality factor (R within ~1e-4 of the
-    oracle's, relative to max |R|); refinement then reaches the 1e-10 target."""
+    oracle's, relative to max |R|); refinement then reaches the 1e-10 target.
+    The inner panels' updates run as one cooperative launch each while every
+    SM's share of the rows fits 320 (the 49000-row case takes the
+    three-kernel form)."""
     m, n = shape
     A = I.random_matrix(m, n, seed=31 + m)
     At = ctqr.to_colmajor(A)
-    f = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32)
+    Af = At.to(torch.float32)
+    torch.cuda.synchronize()
+    ctqr.profile_reset()
+    ctqr.profile_enable(True)
+    f = ctqr.qr_factor(Af, prec=ctqr.Prec.TF32)
+    torch.cuda.synchronize()
+    ctqr.profile_enable(False)
+    launches = {p_["name"]: p_["launches"] for p_ in ctqr.profile_kernels()}
+    inner = sum(-(-min(128, n - J) // 32) - 1 for J in range(0, n, 128))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fits = -(-m // sms) <= 320
+    assert launches.get("inner_update", 0) == (inner if fits else 0), launches
     assert f.status() == ctqr.CT_OK
     F, tau = ctqr.factor_matrix(f)
     Fo, tauo = O.qr(A)
