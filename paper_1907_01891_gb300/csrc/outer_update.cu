@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256, 1) k_qt_outer(const float* __restrict__ F
 
 size_t outer_work_floats(int sms, int64_t m, int64_t n) {
   const int64_t mp = (m + 3) / 4 * 4;
-  const int64_t wcols = n > (int64_t)4 * sms * 128 ? n : (int64_t)4 * sms * 128;
+  const int64_t wcols = 8 * n > (int64_t)4 * sms * 128 ? 8 * n : (int64_t)4 * sms * 128;
   return (size_t)mp * kNB          // Vc
          + (size_t)2 * m * kNB     // Vr (high, low)
          + (size_t)kNB * wcols     // W partials
@@ -422,7 +422,7 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
   float* F = (float*)f->F;
   const int64_t ld = f->ld;
   const int64_t ldvc = (m + 3) / 4 * 4;
-  const int64_t wcols = n > (int64_t)4 * sms * 128 ? n : (int64_t)4 * sms * 128;
+  const int64_t wcols = 8 * n > (int64_t)4 * sms * 128 ? 8 * n : (int64_t)4 * sms * 128;
   float* Vc = work;
   float* Vr = Vc + (size_t)ldvc * kNB;
   float* Vrl = Vr + (size_t)m * kNB;
@@ -445,13 +445,33 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
   if ((st = tc_gemm_tn(Vc, ldvc, Vc, ldvc, kNB, kNB, mr, Gp, kNB, (int64_t)kNB * kNB, 0, gs, split3,
                        f->status, s)) != CT_OK)
     return st;
-  // W = V^T C, split over rows when there are too few column tiles.
+  // W = V^T C, split over rows when there are too few column tiles: at least
+  // two waves of CTAs, and among the split counts up to three times that the
+  // one whose last wave is fullest (one CTA per SM; a half-empty last wave
+  // costs a whole wave).
   const int64_t tiles = (nc + 127) / 128;
-  int64_t ws = (2 * sms + tiles - 1) / tiles;
-  const int64_t wsmax = (mr + 1023) / 1024;
-  if (ws > wsmax) ws = wsmax;
-  if (ws * nc > wcols) ws = wcols / nc;
-  if (ws < 1) ws = 1;
+  int64_t wsmax = (mr + 1023) / 1024;
+  if (wsmax * nc > wcols) wsmax = wcols / nc;
+  if (wsmax < 1) wsmax = 1;
+  int64_t ws0 = (2 * sms + tiles - 1) / tiles;
+  if (ws0 > wsmax) ws0 = wsmax;
+  if (ws0 < 1) ws0 = 1;
+  int64_t ws = ws0;
+  {
+    double best = -1.0;
+    for (int64_t w = ws0; w <= 3 * ws0 && w <= wsmax; ++w) {
+      // the splits tc_gemm_tn makes of w (chunks rounded up to 32 rows)
+      int64_t chunk = (mr + w - 1) / w;
+      chunk = (chunk + 31) / 32 * 32;
+      const int64_t made = (mr + chunk - 1) / chunk;
+      const int64_t ctas = made * tiles;
+      const double eff = (double)ctas / (double)(sms * ((ctas + sms - 1) / sms));
+      if (eff > best + 0.02) {
+        best = eff;
+        ws = w;
+      }
+    }
+  }
   float* C = F + J + (J + nbo) * ld;
   if ((st = tc_gemm_tn(Vc, ldvc, C, ld, kNB, nc, mr, Wp, kNB, (int64_t)kNB * nc, 0, (int)ws, split3,
                        f->status, s)) != CT_OK)

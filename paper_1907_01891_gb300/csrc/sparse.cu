@@ -132,6 +132,45 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ ptr, c
   }
 }
 
+// The same product for k <= 16: the two half-warps take the even and the odd
+// nonzeros of the row (lane c = lane % 16 the column) and are added at the
+// end, so every lane of the FP64 pipe's warp instructions does work (on GB300
+// an FP64 warp instruction costs its full issue time whatever its mask).
+__global__ void __launch_bounds__(256) k_spmm16(const int64_t* __restrict__ ptr, const int* __restrict__ idx,
+                                                const double* __restrict__ val, int64_t rows,
+                                                const double* __restrict__ Xr, int k, double* __restrict__ Yr) {
+  const int lane = threadIdx.x & 31, h = lane >> 4, c = lane & 15;
+  const bool act = c < k;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < rows; i += nwarps) {
+    const int64_t b = ptr[i], e = ptr[i + 1];
+    double acc = 0.0;
+    int64_t q = b + h;
+    for (; q + 6 < e; q += 8) {  // four nonzeros per half-warp in flight
+      int j[4];
+      double a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        j[u] = __ldg(idx + q + 2 * u);
+        a[u] = __ldg(val + q + 2 * u);
+      }
+      double x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = act ? Xr[(int64_t)j[u] * k + c] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += a[u] * x[u];
+    }
+    for (; q < e; q += 2) {
+      const int j = __ldg(idx + q);
+      const double a = __ldg(val + q);
+      if (act) acc += a * Xr[(int64_t)j * k + c];
+    }
+    acc += __shfl_down_sync(0xffffffffu, acc, 16);
+    if (h == 0 && act) Yr[i * k + c] = acc;
+  }
+}
+
 // Column-major <-> row-major for rows x k FP64 blocks through 32 x 32 tiles.
 // mode 0: dst = src, 1: dst -= src, 2: dst = -src (row-major -> column-major only).
 __global__ void __launch_bounds__(256) k_to_rows(const double* __restrict__ src, int64_t ld, int64_t rows, int k,
@@ -253,7 +292,9 @@ ct_status SparseSystem::apply(const double* X, int64_t ldx, int64_t k, double* Y
   }
   {
     LaunchScope ls(K_SPMM, s, 2.0 * nnz * k, 12.0 * nnz + 8.0 * (m + n) * k);
-    k_spmm<<<(unsigned)((m + 7) / 8 < 65535 ? (m + 7) / 8 : 65535), tb, 0, s>>>(row_ptr, col, val, m, Xr, (int)k, Yr);
+    const unsigned g = (unsigned)((m + 7) / 8 < 65535 ? (m + 7) / 8 : 65535);
+    if (k <= 16) k_spmm16<<<g, tb, 0, s>>>(row_ptr, col, val, m, Xr, (int)k, Yr);
+    else k_spmm<<<g, tb, 0, s>>>(row_ptr, col, val, m, Xr, (int)k, Yr);
     CT_LAUNCH_CHECK();
   }
   {
@@ -279,7 +320,9 @@ ct_status SparseSystem::apply_t(const double* R, int64_t ldr, int64_t k, double*
   }
   {
     LaunchScope ls(K_SPMM, s, 2.0 * nnz * k, 12.0 * nnz + 8.0 * (m + n) * k);
-    k_spmm<<<(unsigned)((n + 7) / 8 < 65535 ? (n + 7) / 8 : 65535), tb, 0, s>>>(col_ptr, crow, cval, n, Rr, (int)k, Sr);
+    const unsigned g = (unsigned)((n + 7) / 8 < 65535 ? (n + 7) / 8 : 65535);
+    if (k <= 16) k_spmm16<<<g, tb, 0, s>>>(col_ptr, crow, cval, n, Rr, (int)k, Sr);
+    else k_spmm<<<g, tb, 0, s>>>(col_ptr, crow, cval, n, Rr, (int)k, Sr);
     CT_LAUNCH_CHECK();
   }
   {
