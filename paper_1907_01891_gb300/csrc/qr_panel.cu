@@ -54,6 +54,8 @@ struct PanelArgs {
   int* status;
   int row0;              // rows held by CTA 0 (the panel's top nbp rows), the
                          // others rp each after them; 0: rp rows per CTA from row 0
+  int dot2;              // Cholesky-QR: Gram and row solves as compensated FP32
+                         // products on an FP32 copy of the rows (else FP64)
 };
 
 // First panel row and row count of CTA b.
@@ -371,6 +373,29 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return y;
 }
 
+// Compensated dot product on the FP32 pipes: Dot2 of Ogita, Rump and Oishi
+// (2005), built from the error-free transformations TwoProduct (by FMA) and
+// TwoSum (Knuth).  s + c carries the sum of products with about twice FP32's
+// precision; every operation is an explicitly rounded intrinsic so the
+// compiler cannot contract the transformations.  On GB300 this costs ten
+// FP32 instructions per term against one FP64 FMA, and the FP32 pipes issue
+// 64 times as many lanes per clock.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(pe, e));
+  }
+  // a term far below s (the low part of a split factor): into c directly
+  __device__ __forceinline__ void add_small(float x, float y) { c = __fmaf_rn(x, y, c); }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <typename S>
 __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   extern __shared__ double smem[];
@@ -385,6 +410,12 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   double* X = M + nn;                         // scratch / U^{-1} / (L1^T)^{-1}
   double* sv = X + nn;                        // [P] s_i
   double* dv = sv + P;                        // [P] column sums
+  // with a.dot2: the same rows in FP32 (exact: the data is FP32) and M^{-1}
+  // split into FP32 high and low parts
+  const bool dot2 = a.dot2 != 0;
+  float* slabf = (float*)(dv + P);            // [nbp][rp]
+  float* Mh = slabf + (size_t)nbp * rp;
+  float* Ml = Mh + nn;
   __shared__ int s_ok;
   int64_t rb;
   int nr;
@@ -400,9 +431,16 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = src[(int64_t)(c + u) * a.ld];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) slab[(size_t)(c + u) * rp + r] = (double)v[u];
+      for (int u = 0; u < 8; ++u) {
+        slab[(size_t)(c + u) * rp + r] = (double)v[u];
+        if (dot2) slabf[(size_t)(c + u) * rp + r] = (float)v[u];
+      }
     }
-    for (; c < nbp; ++c) slab[(size_t)c * rp + r] = (double)src[(int64_t)c * a.ld];
+    for (; c < nbp; ++c) {
+      const S v = src[(int64_t)c * a.ld];
+      slab[(size_t)c * rp + r] = (double)v;
+      if (dot2) slabf[(size_t)c * rp + r] = (float)v;
+    }
   }
   // the top nbp rows of the panel (held by CTA 0, read by all before CTA 0
   // can overwrite them, i.e. before the second barrier)
@@ -425,16 +463,29 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   for (int e = tid; e < split_from; e += kPT) {
     int i, j;
     tri_index(e, i, j);
-    const double* ci = slab + (size_t)i * rp;
-    const double* cj = slab + (size_t)j * rp;
-    double s0 = 0.0, s1 = 0.0;
-    int r = 0;
-    for (; r + 1 < nr; r += 2) {
-      s0 += ci[r] * cj[r];
-      s1 += ci[r + 1] * cj[r + 1];
+    if (dot2) {
+      const float* ci = slabf + (size_t)i * rp;
+      const float* cj = slabf + (size_t)j * rp;
+      Dot2 d0, d1;
+      int r = 0;
+      for (; r + 1 < nr; r += 2) {
+        d0.add(ci[r], cj[r]);
+        d1.add(ci[r + 1], cj[r + 1]);
+      }
+      if (r < nr) d0.add(ci[r], cj[r]);
+      gp[e] = d0.value() + d1.value();
+    } else {
+      const double* ci = slab + (size_t)i * rp;
+      const double* cj = slab + (size_t)j * rp;
+      double s0 = 0.0, s1 = 0.0;
+      int r = 0;
+      for (; r + 1 < nr; r += 2) {
+        s0 += ci[r] * cj[r];
+        s1 += ci[r + 1] * cj[r + 1];
+      }
+      if (r < nr) s0 += ci[r] * cj[r];
+      gp[e] = s0 + s1;
     }
-    if (r < nr) s0 += ci[r] * cj[r];
-    gp[e] = s0 + s1;
   }
   // rem * g <= kPT; g is a power of two <= 32, so the groups of g lanes never
   // straddle a warp; whole warps take part in the shuffles
@@ -445,9 +496,17 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
     if (act) {
       int i, j;
       tri_index(e, i, j);
-      const double* ci = slab + (size_t)i * rp;
-      const double* cj = slab + (size_t)j * rp;
-      for (int r = part; r < nr; r += g) s += ci[r] * cj[r];
+      if (dot2) {
+        const float* ci = slabf + (size_t)i * rp;
+        const float* cj = slabf + (size_t)j * rp;
+        Dot2 d;
+        for (int r = part; r < nr; r += g) d.add(ci[r], cj[r]);
+        s = d.value();
+      } else {
+        const double* ci = slab + (size_t)i * rp;
+        const double* cj = slab + (size_t)j * rp;
+        for (int r = part; r < nr; r += g) s += ci[r] * cj[r];
+      }
     }
     for (int o = g / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
     if (act && part == 0) gp[e] = s;
@@ -576,6 +635,15 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
     M[i + j * P] = s;
   }
   __syncthreads();
+  if (dot2) {
+    for (int e = tid; e < nn; e += kPT) {
+      const double mv = M[e];
+      const float h = (float)mv;
+      Mh[e] = h;
+      Ml[e] = (float)(mv - (double)h);
+    }
+    __syncthreads();
+  }
 
   // 4. This CTA's rows: V2 = P2 M^{-1} (rows with panel index >= nbp, columns
   //    from the last so that each row is updated in place); the top nbp rows
@@ -583,10 +651,24 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   for (int r = tid; r < nr; r += kPT) {
     const int64_t gr = rb + r;
     if (gr >= nbp) {
-      for (int j = nbp - 1; j >= 0; --j) {
-        double s = 0.0;
-        for (int i = 0; i <= j; ++i) s += slab[(size_t)i * rp + r] * M[i + j * P];
-        slab[(size_t)j * rp + r] = s;
+      // FP32 result (the factor's storage type) of a compensated product
+      // with the split M^{-1}; the inputs are the unmodified FP32 copy
+      if (dot2) {
+        for (int j = nbp - 1; j >= 0; --j) {
+          Dot2 d;
+          for (int i = 0; i <= j; ++i) {
+            const float x = slabf[(size_t)i * rp + r];
+            d.add(x, Mh[i + j * P]);
+            d.add_small(x, Ml[i + j * P]);
+          }
+          slab[(size_t)j * rp + r] = (double)__fadd_rn(d.s, d.c);
+        }
+      } else {
+        for (int j = nbp - 1; j >= 0; --j) {
+          double acc = 0.0;
+          for (int i = 0; i <= j; ++i) acc += slab[(size_t)i * rp + r] * M[i + j * P];
+          slab[(size_t)j * rp + r] = acc;
+        }
       }
     } else {
       const int i = (int)gr;
@@ -630,9 +712,10 @@ int panel_grid(int64_t mr, const DeviceInfo& di, size_t mth) {
   return grid;
 }
 
-size_t panel_cqr_smem_bytes(int nbp, int rp) {
+size_t panel_cqr_smem_bytes(int nbp, int rp, bool dot2) {
   const size_t P = (size_t)pow2_at_least(nbp);
-  size_t bytes = ((size_t)nbp * rp + 5 * P * P + 2 * P) * sizeof(double);
+  size_t bytes = ((size_t)nbp * rp + 5 * P * P + 2 * P) * sizeof(double) +
+                 (dot2 ? ((size_t)nbp * rp + 2 * P * P) * sizeof(float) : 0);  // FP32 slab copy, split M^{-1}
   // the Householder fallback: its buffers in place of G.., T at the start
   const size_t fb = ((size_t)nbp * rp + kSmallDoubles + kMaxNb) * sizeof(double);
   const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
@@ -674,13 +757,15 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
     rp_c = (int)((mr - nbp + grid - 2) / (grid - 1));
     if (rp_c < nbp) rp_c = nbp;
   }
-  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp && panel_cqr_smem_bytes(nbp, rp_c) <= limit;
+  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp && panel_cqr_smem_bytes(nbp, rp_c, false) <= limit;
+  // compensated FP32 Gram and row solves when their FP32 copy of the rows fits
+  const bool dot2 = cqr && panel_cqr_smem_bytes(nbp, rp_c, true) <= limit;
   if (cqr) {
     if (grid >= 2 && mr > nbp) row0 = nbp;
     rp = rp_c;
   }
   const void* fn = cqr ? (const void*)k_panel_cqr<S> : (const void*)k_panel<S, Mth>;
-  const size_t smem = cqr ? panel_cqr_smem_bytes(nbp, rp) : panel_smem_bytes(nbp, rp, sizeof(Mth));
+  const size_t smem = cqr ? panel_cqr_smem_bytes(nbp, rp, dot2) : panel_smem_bytes(nbp, rp, sizeof(Mth));
   if (smem > limit) return CT_ERR_UNSUPPORTED;
   CT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -696,6 +781,7 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   a.rp = rp;
   a.grid = grid;
   a.row0 = row0;
+  a.dot2 = dot2 ? 1 : 0;
   a.tau = f->tau + j0;
   a.T = T;
   a.ldt = f->nb;
