@@ -679,11 +679,23 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       cudaStream_t s;
       ~LaGuard() {
         if (la->rest_pending) cudaStreamWaitEvent(s, la->ev_rest, 0);
+        if (la->ev_t) cudaStreamWaitEvent(s, la->ev_t, 0);  // the last T on the side stream
         if (la->ev_w) cudaEventDestroy(la->ev_w);
         if (la->ev_rest) cudaEventDestroy(la->ev_rest);
         if (la->s2) cudaStreamDestroy(la->s2);
+        if (la->ev_g) cudaEventDestroy(la->ev_g);
+        if (la->ev_t) cudaEventDestroy(la->ev_t);
+        if (la->s3) cudaStreamDestroy(la->s3);
       }
     } la_guard{&la, s};
+    // the side stream for each outer block's T (beside its V^T C product)
+    if (cudaStreamCreateWithFlags(&la.s3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&la.ev_g, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&la.ev_t, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      free_factor(f);
+      return CT_ERR_CUDA;
+    }
     const char* la_env = getenv("CTQR_LOOKAHEAD");
     const bool la_on = la_env && *la_env == '1' && di.sms > 2 * kReserve;
     if (la_on) {

@@ -96,7 +96,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 enum KernelClass {
   K_ZERO = 0, K_SIDDON, K_PANEL, K_VTC, K_TW, K_UPDATE, K_TRSM_DIAG, K_COPY, K_RANK,
   K_NORMS, K_ADD, K_GEMM_TN, K_AXPY, K_TC_GEMM, K_SPMM, K_TILE_RT, K_CONV, K_GATE, K_TC_UPDATE,
-  K_QT_OUTER, K_INNER, K_COUNT
+  K_QT_OUTER, K_INNER, K_TINV, K_COUNT
 };
 
 // Graph capture: launches made between begin and end are recorded into
@@ -229,6 +229,10 @@ size_t outer_work_floats(int sms, int64_t m, int64_t n);
 struct Lookahead {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_w = nullptr, ev_rest = nullptr;
+  // side stream for T = S^{-1}, which needs only V^T V and tau, so it runs
+  // beside the V^T C product (ev_g: V^T V reduced; ev_t: T written)
+  cudaStream_t s3 = nullptr;
+  cudaEvent_t ev_g = nullptr, ev_t = nullptr;
   bool defer = false;         // defer the rest of this block's update
   bool rest_pending = false;  // a deferred update is in flight (ev_rest recorded)
   int reserve = 0;

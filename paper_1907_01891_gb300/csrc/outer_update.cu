@@ -472,15 +472,8 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
       }
     }
   }
-  float* C = F + J + (J + nbo) * ld;
-  if ((st = tc_gemm_tn(Vc, ldvc, C, ld, kNB, nc, mr, Wp, kNB, (int64_t)kNB * nc, 0, (int)ws, split3,
-                       f->status, s)) != CT_OK)
-    return st;
-  // tc_gemm_tn may merge splits: recompute how many partial blocks it wrote.
+  // G: the splits tc_gemm_tn wrote (it may merge them)
   {
-    int64_t chunk = (mr + ws - 1) / ws;
-    chunk = (chunk + 31) / 32 * 32;
-    ws = (mr + chunk - 1) / chunk;
     int64_t gchunk = (mr + gs - 1) / gs;
     gchunk = (gchunk + 31) / 32 * 32;
     gs = (int)((mr + gchunk - 1) / gchunk);
@@ -493,20 +486,43 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     k_reduce_gram<<<kNB * kNB / 256, 256, 0, s>>>(Gp, gs, (int64_t)kNB * kNB, nbo, Gred);
     CT_LAUNCH_CHECK();
   }
-  // W' = T^T W: T = S^{-1} once for the block, then one product per 64 columns.
-  // (kept in the factor's per-block store, next to G, when there is one)
+  // T = S^{-1} once for the block (kept in the factor's per-block store, next
+  // to G, when there is one), on the side stream beside V^T C when there is one
   float* Tb = f->Tblk ? f->Tblk + (size_t)(J / kNB) * kNB * kNB : Gp + (size_t)(2 * sms + 1) * kNB * kNB;
+  const bool side = la && la->s3 && f->Gblk && f->Tblk;
   {
-    LaunchScope ls(K_TW, s, (double)kNB * kNB * kNB / 3.0, 8.0 * kNB * kNB);
     static bool attr = false;
     if (!attr) {
       CT_CUDA_TRY(cudaFuncSetAttribute(k_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem));
       CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplyTtSmem));
       attr = true;
     }
-    k_tinv<<<1, kTinvThreads, kTinvSmem, s>>>(Gred, f->tau + J, nbo, Tb);
+    cudaStream_t st_t = s;
+    if (side) {
+      CT_CUDA_TRY(cudaEventRecord(la->ev_g, s));
+      CT_CUDA_TRY(cudaStreamWaitEvent(la->s3, la->ev_g, 0));
+      st_t = la->s3;
+    }
+    // (on the side stream its event time includes the wait for a free SM)
+    LaunchScope ls(K_TINV, st_t, (double)kNB * kNB * kNB / 3.0, 8.0 * kNB * kNB);
+    k_tinv<<<1, kTinvThreads, kTinvSmem, st_t>>>(Gred, f->tau + J, nbo, Tb);
     CT_LAUNCH_CHECK();
+    if (side) CT_CUDA_TRY(cudaEventRecord(la->ev_t, la->s3));
   }
+  float* C = F + J + (J + nbo) * ld;
+  if ((st = tc_gemm_tn(Vc, ldvc, C, ld, kNB, nc, mr, Wp, kNB, (int64_t)kNB * nc, 0, (int)ws, split3,
+                       f->status, s)) != CT_OK) {
+    if (side) cudaStreamWaitEvent(s, la->ev_t, 0);
+    return st;
+  }
+  // tc_gemm_tn may merge splits: recompute how many partial blocks it wrote.
+  {
+    int64_t chunk = (mr + ws - 1) / ws;
+    chunk = (chunk + 31) / 32 * 32;
+    ws = (mr + chunk - 1) / chunk;
+  }
+  if (side) CT_CUDA_TRY(cudaStreamWaitEvent(s, la->ev_t, 0));
+  // W' = T^T W, one product per 64 columns.
   {
     LaunchScope ls(K_TW, s, 2.0 * kNB * kNB * nc, 4.0 * kNB * nc * (ws + 2));
     k_apply_tt<<<(unsigned)((nc + kTC - 1) / kTC), 256, kApplyTtSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Tb, nc,

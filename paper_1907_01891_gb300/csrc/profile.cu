@@ -69,7 +69,7 @@ const char* kNames[K_COUNT] = {"zero_fill",   "system_matrix", "panel_qr",  "ref
                                "rank_check",  "col_norms",     "col_add",   "gemm_tn",
                                "col_axpy",    "tc_gemm",       "spmm",      "tile_runtime",
                                "conv",        "gate",          "tc_update",
-                               "qt_outer",    "inner_update"};
+                               "qt_outer",    "inner_update",  "t_inverse"};
 
 }  // namespace
 
