@@ -336,6 +336,10 @@ def main():
                 "unit": "TFLOP/s",
                 "peak_source": "derived: 152 SMs x %s FMA/clk x 2 x %.2f GHz" % (
                     "2 FP64" if alu == fp64_peak else "128 FP32", sm_max_ghz)}
+        if dom["name"] == "panel_qr":
+            roof["note"] = ("algorithmic flops 3*mr*nbp^2 per panel against the FP64 peak; the Gram matrix and "
+                            "the row solves run as compensated FP32 products, the 32x32 Cholesky, inverses and "
+                            "modified LU in FP64 (dependent steps: latency-bound)")
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom["name"]
     roof["launches_per_step"] = dom["launches"]
