@@ -108,10 +108,15 @@ typedef struct {
   double lambda;   /* > 0: the factored system is [A_rays; lambda*I] and the A */
                    /* passed to ct_reconstruct_batch holds only its first     */
                    /* m - n rows (the lambda*I rows are applied implicitly)   */
-  double tol;      /* stop when every column has ||dx_c|| <= tol*||x_c||        */
-                   /* (default 1e-12)                                          */
-  int method;      /* 0 auto: classical refinement while its updates shrink     */
-                   /*   at least twofold per step, then preconditioned CGLS;    */
+  double tol;      /* stop when every column has ||dx_c|| <= tol*||x_c||, or   */
+                   /* (CGLS) when every column's error left after the step,    */
+                   /* estimated as ||dx_c|| rho/(1-rho) from the larger of the */
+                   /* last two contraction ratios rho < 1/2, is below          */
+                   /* tol*||x_c|| (default 1e-12)                              */
+  int method;      /* 0 auto: CGLS right after X_0 when the residual of X_0 is */
+                   /*   above 1e-6 ||B|| (noisy data) or lambda > 0, else      */
+                   /*   classical refinement while its updates shrink at least */
+                   /*   fourfold per step, then preconditioned CGLS;           */
                    /* 1 classical only; 2 CGLS only (after the first solve)     */
 } ct_refine_opts;
 

@@ -427,6 +427,7 @@ class Refiner {
     if ((st = launch_col_norms2(S_, n_, n_, k_, n1_, s_)) != CT_OK) return st;
     if ((st = fetch(n1_, 1)) != CT_OK) return st;
     std::vector<double> gamma(h_.begin(), h_.begin() + k_), alpha(k_), beta(k_);
+    std::vector<double> prel(k_, 0.0), pratio(k_, INFINITY);  // last step and contraction per column
     for (int it = 0; it < budget; ++it) {
       *used = it + 1;
       // t = R^{-1} p ; q = [A; lambda I] t
@@ -438,21 +439,37 @@ class Refiner {
       if ((st = launch_col_norms2(T_, n_, n_, k_, n3_, s_)) != CT_OK) return st;             // ||t||^2
       if ((st = launch_col_norms2(X_, ldx_, n_, k_, a_, s_)) != CT_OK) return st;            // ||x||^2
       if ((st = fetch(n1_, 4)) != CT_OK) return st;
-      double worst = 0.0;
+      // worst: max over columns of |dx|/|x|; est: max over columns of the
+      // error left after this step, |dx| rho / (1 - rho) with rho the larger
+      // of the last two contraction ratios |dx_t| / |dx_{t-1}| (the remaining
+      // steps of an iteration contracting by rho sum to that), once two
+      // ratios exist and both are below 1/2; otherwise the step itself.
+      double worst = 0.0, est = 0.0;
       for (int64_t c = 0; c < k_; ++c) {
         const double rq = h_[c], qq = h_[k_ + c], tt = h_[2 * k_ + c], xx = h_[3 * k_ + c];
         alpha[c] = qq > 0.0 ? rq / qq : 0.0;
         const double dx = fabs(alpha[c]) * sqrt(tt), xn = sqrt(xx + alpha[c] * alpha[c] * tt);
         const double rel = xn > 0.0 ? dx / xn : (dx > 0.0 ? INFINITY : 0.0);
         if (!(rel <= worst)) worst = rel;
+        double e = rel;
+        const double ratio = prel[c] > 0.0 ? rel / prel[c] : INFINITY;
+        if (it >= 2) {
+          const double rho = ratio > pratio[c] ? ratio : pratio[c];
+          if (rho < 0.5) e = rel * rho / (1.0 - rho);
+        }
+        pratio[c] = ratio;
+        prel[c] = rel;
+        if (!(e <= est)) est = e;
       }
       CT_CUDA_TRY(cudaMemcpyAsync(a_, alpha.data(), sizeof(double) * k_, cudaMemcpyHostToDevice, s_));
       if ((st = launch_colwise(0, 1.0, a_, T_, n_, X_, ldx_, n_, k_, s_)) != CT_OK) return st;    // x += a t
       if ((st = launch_colwise(0, -1.0, a_, Q_, ldw_, Yd_, ldw_, m_, k_, s_)) != CT_OK) return st;  // r -= a q
       last_ = worst;
-      if (trace_) fprintf(stderr, "ctqr cgls %d: max |dx|/|x| = %.3e (%.2f ms)\n", it, worst, since_start());
+      if (trace_)
+        fprintf(stderr, "ctqr cgls %d: max |dx|/|x| = %.3e, estimated error left %.3e (%.2f ms)\n", it, worst, est,
+                since_start());
       if (!isfinite(worst)) return CT_ERR_NONFINITE;
-      if (worst <= tol_) {
+      if (worst <= tol_ || est <= tol_) {
         CT_CUDA_TRY(cudaStreamSynchronize(s_));
         return CT_OK;
       }

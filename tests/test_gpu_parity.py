@@ -280,13 +280,15 @@ def test_reconstruct_scan_host_and_device_buffers_agree():
 
 
 # ---------------------------------------------------------------- tensor-core factor
-@pytest.mark.parametrize("shape", [(300, 200), (700, 300), (1000, 513), (49000, 150)])
+@pytest.mark.parametrize("shape", [(300, 200), (700, 300), (1000, 513), (49000, 150), (90000, 150)])
 def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape):
     """3xTF32 outer updates give an FP32-quality factor (R within ~1e-4 of the
     oracle's, relative to max |R|); refinement then reaches the 1e-10 target.
     The inner panels' updates run as one cooperative launch each while every
-    SM's share of the rows fits 320 (the 49000-row case takes the
-    three-kernel form)."""
+    SM's share of the rows fits 320 (the 49000- and 90000-row cases take the
+    three-kernel form); at 90000 rows the Cholesky-QR panel's FP32 copy of its
+    rows no longer fits beside the FP64 one, so its Gram matrix and row solves
+    run in FP64."""
     m, n = shape
     A = I.random_matrix(m, n, seed=31 + m)
     At = ctqr.to_colmajor(A)
