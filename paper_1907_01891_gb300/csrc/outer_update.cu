@@ -1,15 +1,17 @@
 // outer_update.cu -- the tensor-core trailing update of one 128-column outer
-// block of the mixed-precision factorization.
+// block of the mixed-precision factorization, and the one-launch Q^T of all
+// outer blocks for FP32 right-hand sides.
 //
 // After the inner 32-column panels of an outer block [J, J+nbo) are factored,
 // the rest of the matrix C = F[J:m, J+nbo:n] is updated once with the whole
 // block reflector Q_J = I - V T V^T of the nbo reflectors:
+//   G  = V^T V                  tcgen05 GEMM, reduced once and kept per block
+//   T  = S^{-1}                 the UT-transform S = diag(1/tau) + striu(G)
+//                               inverted by block doubling (T_ii = tau_i, so
+//                               tau_i = 0 gives H_i = I), kept per block; on a
+//                               side stream beside the next product
 //   W  = V^T C                  tcgen05 GEMM (split over rows, FP32 partials)
-//   W' = T^T W                  here, through the UT-transform form
-//                               T^{-1} = S = diag(1/tau) + striu(V^T V): W' solves
-//                               S^T W' = W (forward substitution, w'_i = tau_i w_i,
-//                               then w_r -= (V^T V)_{ir} w'_i for r > i), which
-//                               also covers tau_i = 0 (w'_i = 0);
+//   W' = T^T W                  a product per 64 columns (partials summed in order)
 //   C -= V W'                   tcgen05 GEMM.
 // This is the paper's Apply_left_Qt_of_dense_QR with its "S factor"
 // (Sec. II-C-3) applied to a 128-column block at once, so C is read and
