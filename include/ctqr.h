@@ -49,8 +49,13 @@ typedef enum {
 typedef enum { CT_F64 = 0, CT_F32 = 1 } ct_dtype;
 
 /* Arithmetic of the factorization's trailing updates (the dense contraction
- * C <- C - V T^T V^T C).  Panels, reflector norms and T factors are always
- * computed in FP64.  CT_PREC_F64: plain FP64 everywhere, factor stored in FP64.
+ * C <- C - V T^T V^T C).  Reflector scalars and T factors are always FP64;
+ * FP64-stored factors compute their panels column by column in FP64,
+ * FP32-stored ones by Cholesky-QR with Householder reconstruction (the 32 x 32
+ * algebra in FP64, the Gram matrix and the row solves as compensated FP32 dot
+ * products of about twice FP32's precision, or FP64 when their FP32 copy does
+ * not fit in shared memory; a panel with kappa_1(R1) > 3e3 falls back to the
+ * column-by-column FP64 panel).  CT_PREC_F64: plain FP64 everywhere, factor stored in FP64.
  * CT_PREC_F32: factor stored in FP32, updates in FP32 (CUDA cores).
  * CT_PREC_TF32: factor stored in FP32; 128-column outer blocks of 32-column
  * panels, the outer trailing updates on the tensor cores (tcgen05) in TF32 with
@@ -191,8 +196,8 @@ ct_status ct_build_system(const ct_geometry* geom, ct_dtype dtype, double lambda
                           void* A, int64_t lda, void* stream);
 
 /* Householder QR A = QR (Eq. (QR)) of the m x n (m >= n) matrix A, blocked in
- * panels of nb columns: per panel an FP64 panel factorization (reflector
- * generation, norms) and its T factor (the paper's "S factor" of
+ * panels of nb columns: per panel a panel factorization (reflector generation,
+ * norms; arithmetic as described for ct_prec) and its T factor (the paper's "S factor" of
  * Compute_dense_QR, Sec. II-C-3), then the trailing update of the rest
  * (Apply_left_Qt_of_dense_QR) in the arithmetic `prec` selects.
  * A has type `dtype` (CT_F64 or CT_F32), leading dimension lda.  On success
