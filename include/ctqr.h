@@ -109,7 +109,7 @@ typedef struct ct_factor ct_factor;
 
 /* Options of ct_reconstruct_batch's FP64 refinement.  NULL = defaults. */
 typedef struct {
-  int max_iter;    /* iteration cap, all phases together (default 60)          */
+  int max_iter;    /* iteration cap, all phases together (default 200)         */
   double lambda;   /* > 0: the factored system is [A_rays; lambda*I] and the A */
                    /* passed to ct_reconstruct_batch holds only its first     */
                    /* m - n rows (the lambda*I rows are applied implicitly)   */
