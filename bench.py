@@ -53,6 +53,20 @@ def parse():
     return p.parse_args()
 
 
+# DRAM bytes (read + write) of one Cholesky-QR panel launch of 22976 rows x 32
+# columns, from the ncu capture summarised in profiles/panel_qr_fan128.md
+PANEL_CAPTURE_BYTES, PANEL_CAPTURE_ROWS, PANEL_NB = 3.076e6, 22976, 32
+
+
+def panel_traffic_per_launch(m, n, nb=PANEL_NB):
+    """The captured panel's DRAM bytes scaled by rows to the average panel of
+    an m x n factorization (panel j0 has m - j0 rows)."""
+    if m <= 0 or n <= 0:
+        return None
+    rows = [m - j0 for j0 in range(0, n, nb)]
+    return PANEL_CAPTURE_BYTES * (sum(rows) / len(rows)) / PANEL_CAPTURE_ROWS
+
+
 def qr_flops(m, n):
     return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
 
@@ -346,6 +360,13 @@ def main():
     roof["share_of_step"] = dom["ms"] / (ms / args.steps)
     roof["timed_in"] = "one extra step with CUDA events around every launch of the class"
     roof["traffic"] = None
+    if dom["name"] == "panel_qr" and args.prec != "f64":
+        t = panel_traffic_per_launch(m_sys, n_sys)
+        if t is not None:
+            roof["traffic"] = t
+            roof["traffic_source"] = ("ncu capture of one 22976-row panel (dram read + write %.3g MB, "
+                                      "profiles/panel_qr_fan128.md) scaled by rows to this step's average panel"
+                                      % (PANEL_CAPTURE_BYTES / 1e6))
 
     # ---- end to end through the public API with host buffers
     Bh = B.cpu()
