@@ -8,6 +8,12 @@ HBM.  value = slices reconstructed per second (whole job, all ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec P]
   python bench.py --impl reference ...   # the plain CPU oracle on the host
+  python bench.py --probe M N [--rhs K]  # per-kernel launch list of one factorization
+
+The default workload is the 256 x 256 fan-beam system stacked over 1e-3 I
+(135232 x 65536, 64 slices) with the 3xTF32 tensor-core factor and FP64
+refinement; after the timed steps the plain FP64 QR path reconstructs the same
+scan once, for the relative error and the FP64 path's slices/s.
 
 Multi-GPU (torchrun): every rank reconstructs its own scan (independent
 replicas, weak scaling); there is no data-path collective.
@@ -42,29 +48,27 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="fan128")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="fan256")
     p.add_argument("--prec", choices=sorted(PREC), default="tf32")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--fp64-check", type=int, default=None,
-                   help="also run the FP64 QR path once for the relative-error column "
-                        "(default: on unless the workload is the 256x256 one, where it takes ~15 min)")
+    p.add_argument("--fp64-check", type=int, default=1,
+                   help="after the timed steps, reconstruct the scan once through the plain FP64 QR "
+                        "path (relative error and FP64 slices/s; about 15 min on the 256x256 system)")
+    p.add_argument("--probe", type=int, nargs=2, metavar=("M", "N"), default=None,
+                   help="factor one seeded M x N matrix and print its per-kernel launch list")
+    p.add_argument("--rhs", type=int, default=0, help="--probe: also time Q^T and R^-1, R^-T on K columns")
+    p.add_argument("--seed", type=int, default=5, help="--probe: seed of the matrix")
     return p.parse_args()
 
 
-# DRAM bytes (read + write) of one Cholesky-QR panel launch of 22976 rows x 32
-# columns, from the ncu capture summarised in profiles/panel_qr_fan128.md
-PANEL_CAPTURE_BYTES, PANEL_CAPTURE_ROWS, PANEL_NB = 3.076e6, 22976, 32
-
-
-def panel_traffic_per_launch(m, n, nb=PANEL_NB):
-    """The captured panel's DRAM bytes scaled by rows to the average panel of
-    an m x n factorization (panel j0 has m - j0 rows)."""
-    if m <= 0 or n <= 0:
-        return None
-    rows = [m - j0 for j0 in range(0, n, nb)]
-    return PANEL_CAPTURE_BYTES * (sum(rows) / len(rows)) / PANEL_CAPTURE_ROWS
+# ncu DRAM traffic (read + write) over algorithmic bytes, per kernel class,
+# each from one capture of that kernel on a smaller case of the same shape
+# family (launch, rows, columns in the value); None: not captured since the
+# kernel last changed.  The roofline's traffic is this ratio times the
+# dominant class's algorithmic bytes per launch.
+TRAFFIC_RATIO = {}
 
 
 def qr_flops(m, n):
@@ -159,77 +163,232 @@ def job_throughput(world: int, units_per_rank: int, steps: int, ms_max: float) -
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_sample(cfg, k: int, budget_s: float):
-    """Time the plain CPU oracle on a bounded sample of the workload and scale
-    it (by rays for the build, by flops for QR and solve) to one full step.
-    Returns (seconds per full step, cores, description)."""
-    from oracle import oracle as O
+class OracleSampler:
+    """Bounded samples of one step of the workload run by the plain CPU oracle
+    on the host cores: (1) the system matrix of a subset of the views (scaled
+    by rays to the whole scan) and (2) unblocked Householder QR, Q^T and
+    back-solve of the k slices on the first ns columns of a seeded m x ns
+    matrix at the system's full height (scaled by flops to n columns).  The
+    sample size is calibrated once so that one sample takes about `target_s`
+    seconds; every sample reports its measured time and the time a full step
+    would take at the measured rates (labelled as extrapolated)."""
 
-    g = cfg["geom"]
-    m, n = g.m, g.n
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    # (1) system matrix for a subset of the views, scaled by rays
-    views = max(1, min(g.n_views, int(g.n_views * min(1.0, 4096.0 / max(m, 1)))))
-    gs = O.Geometry(g.beam, g.nx, g.ny, g.pixel, views, g.n_bins, g.angle0,
-                    g.angle_span * views / g.n_views, g.src_iso, g.det_span)
-    t0 = time.perf_counter()
-    As = O.system_matrix(gs)
-    t_build = (time.perf_counter() - t0) * (m / gs.m)
-    del As
-    # (2) QR + Q^T + back-solve of k slices on the first ns columns, full height
-    rng = np.random.default_rng(0)
-    A = None
-    ns = 64
-    spent = 0.0
-    t_qr_rate = None
-    while True:
-        A = np.asfortranarray(rng.standard_normal((m, ns)))
-        B = np.asfortranarray(rng.standard_normal((m, k)))
+    def __init__(self, cfg, k: int, m: int, n: int, target_s: float):
+        from oracle import oracle as O
+        self.O, self.cfg, self.k, self.m, self.n = O, cfg, k, m, n
+        g = cfg["geom"]
+        self.views = max(1, min(g.n_views, int(g.n_views * min(1.0, 2048.0 / max(g.m, 1)))))
+        self.gs = O.Geometry(g.beam, g.nx, g.ny, g.pixel, self.views, g.n_bins, g.angle0,
+                             g.angle_span * self.views / g.n_views, g.src_iso, g.det_span)
+        self.cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        self.rng = np.random.default_rng(0)
+        # calibrate ns: grow until one QR + solve sample takes ~target_s / 2
+        ns, t = 32, 0.0
+        while True:
+            t = self._qr_solve(ns)
+            if t > target_s / 4 or ns >= n:
+                break
+            ns = min(n, int(ns * min(4.0, max(1.25, math.sqrt(target_s / 2 / max(t, 1e-3))))))
+        self.ns = ns
+
+    def _qr_solve(self, ns: int) -> float:
+        A = np.asfortranarray(self.rng.standard_normal((self.m, ns)))
+        B = np.asfortranarray(self.rng.standard_normal((self.m, self.k)))
         t0 = time.perf_counter()
-        F, tau = O.qr(A)
-        Y = O.apply_qt(F, tau, B)
-        O.backsolve(F, Y)
-        dt = time.perf_counter() - t0
-        spent += dt
-        t_qr_rate = (qr_flops(m, ns) + solve_flops(m, ns, k)) / dt
-        if dt > budget_s / 4 or ns >= n or spent > budget_s:
-            break
-        ns = min(n, int(ns * min(4.0, max(1.5, math.sqrt(budget_s / 3 / max(dt, 1e-3))))))
-    t_full = t_build + (qr_flops(m, n) + solve_flops(m, n, k)) / t_qr_rate
-    desc = (f"oracle system matrix for {views} of {g.n_views} views (measured, scaled by rays) + "
-            f"unblocked Householder QR, Q^T and back-solve of {k} slices on the first {ns} of {n} "
-            f"columns at full height m={m} (measured {dt:.1f} s, flop-scaled to n={n})")
-    return t_full, cores, desc
+        F, tau = self.O.qr(A)
+        Y = self.O.apply_qt(F, tau, B)
+        self.O.backsolve(F, Y)
+        return time.perf_counter() - t0
+
+    def sample(self):
+        """One sample: (measured seconds, extrapolated seconds of a full step)."""
+        g = self.cfg["geom"]
+        t0 = time.perf_counter()
+        self.O.system_matrix(self.gs)
+        t_build = time.perf_counter() - t0
+        t_qr = self._qr_solve(self.ns)
+        full = (t_build * g.m / self.gs.m +
+                t_qr * (qr_flops(self.m, self.n) + solve_flops(self.m, self.n, self.k)) /
+                (qr_flops(self.m, self.ns) + solve_flops(self.m, self.ns, self.k)))
+        return t_build + t_qr, full
+
+    def describe(self) -> str:
+        g = self.cfg["geom"]
+        return (f"oracle on {self.cores} host cores: system matrix for {self.views} of {g.n_views} views "
+                f"(scaled by rays) + unblocked Householder QR, Q^T and back-solve of {self.k} slices on the "
+                f"first {self.ns} of {self.n} columns at full height m={self.m} (scaled by flops); "
+                f"the full step is extrapolated from the measured rates")
+
+    def lapack(self):
+        """The strong CPU baseline: LAPACK's blocked QR least-squares solve
+        (torch.linalg.lstsq, driver gels, on the CPU) of the same m x ns
+        sample, flop-scaled to n columns.  Returns (extrapolated seconds of a
+        full step's QR + solve, threads, description)."""
+        import torch
+        ns = min(self.n, 4 * self.ns)
+        A = torch.randn(self.m, ns, dtype=torch.float64)
+        B = torch.randn(self.m, self.k, dtype=torch.float64)
+        t0 = time.perf_counter()
+        torch.linalg.lstsq(A, B, driver="gels")
+        t = time.perf_counter() - t0
+        full = t * (qr_flops(self.m, self.n) + solve_flops(self.m, self.n, self.k)) / (
+            qr_flops(self.m, ns) + solve_flops(self.m, ns, self.k))
+        return full, torch.get_num_threads(), (
+            f"LAPACK gels (torch.linalg.lstsq on the CPU, {torch.get_num_threads()} threads) on the first {ns} "
+            f"of {self.n} columns at full height, measured {t:.2f} s, flop-scaled (QR + solve only)")
+
+
+def reference_main(args, cfg, k, m_sys, n_sys, world, rank):
+    """The reference arm: the plain CPU oracle on the host cores, W warm-up
+    and K timed steps, each step one bounded sample of the workload (see
+    OracleSampler); value = slices per second extrapolated from the samples'
+    measured rates.  Only rank 0 runs."""
+    if rank != 0:
+        return 0
+    g = cfg["geom"]
+    sampler = OracleSampler(cfg, k, m_sys, n_sys, target_s=args.cpu_seconds / 3)
+    for _ in range(args.warmup):
+        sampler.sample()
+    meas, full = [], []
+    for _ in range(args.steps):
+        t, f = sampler.sample()
+        meas.append(t)
+        full.append(f)
+    value = k * len(full) / sum(full)
+    ms = 1e3 * sum(meas) / len(meas)
+    line = {"metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: seeded ellipse phantoms", "impl": "reference",
+            "config": {"workload": f"{cfg['name']} ({m_sys}x{n_sys}, {k} slices)", "prec": "f64",
+                       "parallelism": "host cores"},
+            "step_is_sample": {"measured_ms_per_sample": ms,
+                               "extrapolated_ms_per_full_step": 1e3 * sum(full) / len(full)},
+            "cpu_baseline": {"value": value, "unit": "slices/s", "cores": sampler.cores, "kind": "oracle",
+                             "sample": sampler.describe()},
+            "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def probe_main(args):
+    """Factor one seeded random M x N matrix twice and print the second
+    factorization's per-kernel launch counts and device times; with --rhs K
+    (FP32 / TF32 factors) also Q^T of K columns in FP32 and the R^-1 and R^-T
+    solves, twice, the second round reported.  Used for the ncu captures."""
+    import torch
+    from paper_1907_01891_gb300 import ctqr
+    ctqr.load()
+    m, n = args.probe
+    prec = ctqr.Prec(PREC[args.prec])
+    dtype = torch.float64 if prec == ctqr.Prec.F64 else torch.float32
+    A = ctqr.to_colmajor(I.random_matrix(m, n, seed=args.seed), dtype=dtype)
+
+    def stats():
+        return {k["name"]: {"launches": k["launches"], "ms": round(k["ms"], 4),
+                            "us_per_launch": round(1e3 * k["ms"] / k["launches"], 2)}
+                for k in ctqr.profile_kernels() if k["launches"]}
+
+    ctqr.qr_factor(A, prec)
+    torch.cuda.synchronize()
+    ctqr.profile_reset()
+    ctqr.profile_enable(True)
+    f = ctqr.qr_factor(A, prec)
+    torch.cuda.synchronize()
+    ctqr.profile_enable(False)
+    out = {"m": m, "n": n, "prec": args.prec, "status": f.status(), "kernels": stats()}
+    if args.rhs > 0 and prec != ctqr.Prec.F64:
+        B = ctqr.to_colmajor(I.random_matrix(m, args.rhs, seed=args.seed + 1), dtype=torch.float32)
+        Y = ctqr.to_colmajor(I.random_matrix(n, args.rhs, seed=args.seed + 2), dtype=torch.float32)
+        for rnd in range(2):
+            torch.cuda.synchronize()
+            ctqr.profile_reset()
+            ctqr.profile_enable(rnd == 1)
+            ctqr.apply_qt_f32(f, B)
+            ctqr.trsm_solve_f32(f, Y)
+            ctqr.trsm_solve_f32(f, Y, transpose=True)
+            torch.cuda.synchronize()
+        ctqr.profile_enable(False)
+        out["solve_kernels"] = stats()
+    print(json.dumps(out))
+    return 0
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def roofline(dom, prec, ms_step, peaks):
+    """Roofline object of the dominant kernel class (the one with the most
+    device time in the profiled step)."""
+    sm_max_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    fp64_peak = 152 * 2 * 2 * sm_max_ghz * 1e9 / 1e12      # 2 DFMA/clk/SM (measured 1.204 TF/s)
+    fp32_peak = 152 * 128 * 2 * sm_max_ghz * 1e9 / 1e12    # 128 FFMA/clk/SM
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800 GB/s"
+    hbm = hbm or 6800.0
+    # TF32 tensor peak: cuBLAS TF32 8192^3 measured on this pool's GB300 (1040
+    # TFLOP/s), above the BF16-derived figure (sustained BF16 x 1.1/2.25)
+    tf32_peak = TF32_MEASURED_TFLOPS
+    name = dom["name"]
+    if name in ("zero_fill", "copy", "system_matrix", "tc_update", "tc_fused"):
+        roof = {"bound": "hbm", "achieved": dom["bytes"] / (dom["ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_source": hbm_src}
+        if name in ("tc_update", "tc_fused"):
+            roof["tensor_rate"] = {"achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": tf32_peak,
+                                   "unit": "TFLOP/s", "issued_x": 3,
+                                   "peak_source": "measured cuBLAS TF32 (8192^3) on a GB300 of this pool",
+                                   "note": "algorithmic flops 2MNK; 3xTF32 issues three MMAs per product"}
+    elif name == "tc_gemm":
+        roof = {"bound": "tensor", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": tf32_peak,
+                "unit": "TFLOP/s", "peak_source": "measured cuBLAS TF32 (8192^3) on a GB300 of this pool",
+                "note": "achieved counts algorithmic flops 2MNK; 3xTF32 issues 3 MMAs per product"}
+    else:
+        alu = fp64_peak if prec == "f64" or name == "panel_qr" else fp32_peak
+        roof = {"bound": "alu", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": alu,
+                "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x %s FMA/clk x 2 x %.2f GHz" % (
+                    "2 FP64" if alu == fp64_peak else "128 FP32", sm_max_ghz)}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = name
+    roof["launches_per_step"] = dom["launches"]
+    roof["share_of_step"] = dom["ms"] / ms_step
+    roof["timed_in"] = "one extra step with CUDA events around every launch of the class"
+    ratio = TRAFFIC_RATIO.get(name)
+    if ratio is not None and dom["launches"]:
+        roof["traffic"] = ratio["ratio"] * dom["bytes"] / dom["launches"]
+        roof["traffic_source"] = ("ncu dram read + write of " + ratio["capture"] +
+                                  " over its algorithmic bytes (%.3f), times this step's algorithmic "
+                                  "bytes per launch" % ratio["ratio"])
+    else:
+        roof["traffic"] = None
+    return roof
+
+
+# cuBLAS TF32 GEMM (8192^3) measured on a GB300 of this pool, TFLOP/s.
+TF32_MEASURED_TFLOPS = 1040.0
 
 
 # ---------------------------------------------------------------- main
 def main():
     args = parse()
+    if args.probe:
+        return probe_main(args)
     world, rank, local = dist_setup(args)
     cfg = WORKLOADS[args.workload]
     if args.workload == "batch64":
         return main_batch(args, world, rank, local, cfg)
-    if args.fp64_check is None:
-        args.fp64_check = 0 if args.workload == "fan256" else 1
     g = cfg["geom"]
     k = len(cfg["seeds"])
+    lam = cfg.get("lam", 0.0)
+    m_sys = g.m + (g.n if lam > 0 else 0)
+    n_sys = g.n
 
     if args.impl == "reference":
-        if rank != 0:
-            return 0
-        t_step, cores, desc = oracle_sample(cfg, k, args.cpu_seconds)
-        value = k / t_step
-        line = {"metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic: seeded ellipse phantoms", "impl": "reference",
-                "config": {"workload": f"{cfg['name']} ({g.m}x{g.n}, {k} slices)", "prec": "f64",
-                           "parallelism": "host cores"},
-                "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores, "kind": "oracle",
-                                 "sample": desc},
-                "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return 0
+        return reference_main(args, cfg, k, m_sys, n_sys, world, rank)
 
     import torch
     if world > 1:
@@ -239,10 +398,9 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1907_01891_gb300 import ctqr
     ctqr.load()
+    assert ctqr.system_size(g, lam) == (m_sys, n_sys)
 
     # ---- inputs (outside the timed region): phantoms, sinograms B = A x (+ noise)
-    lam = cfg.get("lam", 0.0)
-    m_sys, n_sys = ctqr.system_size(g, lam)
     seeds = replica_seeds(cfg["seeds"], rank)
     Xtrue = I.phantoms(g, seeds)
     A = ctqr.build_system(g, torch.float64)  # rays only, for the inputs and the checks
@@ -262,24 +420,12 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # Accuracy: optimality of the (regularized) least-squares solution,
-    # ||A^T (b - A x) - lam^2 x|| / (||A||_F^2 ||x||), a property that holds at any
-    # size; and, where the FP64 QR path is affordable, the relative error vs it.
+    # Accuracy at any size: optimality of the (regularized) least-squares
+    # solution, ||A^T (b - A x) - lam^2 x|| / (||A||_F^2 ||x||).
     r = B[:g.m] - A @ X
     gres = A.t() @ r - (lam * lam) * X
     normal_eq = float(torch.linalg.norm(gres) / (torch.linalg.norm(A) ** 2 * torch.linalg.norm(X)))
-    del r, gres
-    rel_err, fp64_qr_tflops = None, None
-    if args.fp64_check:
-        del A
-        torch.cuda.empty_cache()
-        X64, rep64 = ctqr.reconstruct_scan(g, B, prec=ctqr.Prec.F64, lam=lam)
-        torch.cuda.synchronize()
-        rel_err = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
-        fp64_qr_tflops = qr_flops(m_sys, n_sys) / (rep64.ms_factor / 1e3) / 1e12
-        del X64
-    else:
-        del A
+    del r, gres, A
     torch.cuda.empty_cache()
 
     gpu_id = None
@@ -305,6 +451,10 @@ def main():
     barrier(world)
     clk = clocks.stop()
     launches = ctqr.kernel_launches()  # launches of the timed steps (counted, not timed)
+    ms = e0.elapsed_time(e1)
+    ms_max = reduce_max(ms, world, dev)
+    value = job_throughput(world, k, args.steps, ms_max)
+    X_mixed = X.clone()
     # Per-kernel device times come from one more step with CUDA events around
     # every launch (outside the timed region: the events add host work).
     ctqr.profile_reset()
@@ -313,60 +463,12 @@ def main():
     torch.cuda.synchronize()
     ctqr.profile_enable(False)
     kstats = ctqr.profile_kernels()
-    ms = e0.elapsed_time(e1)
-    ms_max = reduce_max(ms, world, dev)
-    value = job_throughput(world, k, args.steps, ms_max)
     ms_factor = statistics.median(r.ms_factor for r in reps)
     ms_solve = statistics.median(r.ms_solve for r in reps)
     ms_build = statistics.median(r.ms_build for r in reps)
-
-    # ---- roofline of the dominant kernel class
-    dom = max(kstats, key=lambda s: s["ms"])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    sm_max_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
-    fp64_peak = 152 * 2 * 2 * sm_max_ghz * 1e9 / 1e12      # 2 DFMA/clk/SM (measured 1.204 TF/s)
-    fp32_peak = 152 * 128 * 2 * sm_max_ghz * 1e9 / 1e12    # 128 FFMA/clk/SM
-    bf16 = peaks.get("bf16_tflops_sustained") or 1705.3
-    tf32_peak = bf16 * 1.1 / 2.25
-    if dom["name"] in ("zero_fill", "copy", "system_matrix", "tc_update"):
-        roof = {"bound": "hbm", "achieved": dom["bytes"] / (dom["ms"] / 1e3) / 1e9,
-                "peak": peaks.get("hbm_gbs") or 6809.3, "unit": "GB/s"}
-        if dom["name"] == "tc_update":
-            roof["note"] = ("C -= V W' streams C (read + write) and the TF32 operands; achieved counts those "
-                            "algorithmic bytes; tensor rate %.1f TFLOP/s algorithmic" % (
-                                dom["flops"] / (dom["ms"] / 1e3) / 1e12))
-    elif dom["name"] == "tc_gemm":
-        roof = {"bound": "tensor", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12,
-                "peak": tf32_peak, "unit": "TFLOP/s",
-                "peak_source": "measured bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
-                "note": "achieved counts algorithmic flops 2MNK; 3xTF32 issues 3 MMAs per product"}
-    else:
-        alu = fp64_peak if args.prec == "f64" or dom["name"] == "panel_qr" else fp32_peak
-        roof = {"bound": "alu", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": alu,
-                "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x %s FMA/clk x 2 x %.2f GHz" % (
-                    "2 FP64" if alu == fp64_peak else "128 FP32", sm_max_ghz)}
-        if dom["name"] == "panel_qr":
-            roof["note"] = ("algorithmic flops 3*mr*nbp^2 per panel against the FP64 peak; the Gram matrix and "
-                            "the row solves run as compensated FP32 products, the 32x32 Cholesky, inverses and "
-                            "modified LU in FP64 (dependent steps: latency-bound)")
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom["name"]
-    roof["launches_per_step"] = dom["launches"]
-    roof["share_of_step"] = dom["ms"] / (ms / args.steps)
-    roof["timed_in"] = "one extra step with CUDA events around every launch of the class"
-    roof["traffic"] = None
-    if dom["name"] == "panel_qr" and args.prec != "f64":
-        t = panel_traffic_per_launch(m_sys, n_sys)
-        if t is not None:
-            roof["traffic"] = t
-            roof["traffic_source"] = ("ncu capture of one 22976-row panel (dram read + write %.3g MB, "
-                                      "profiles/panel_qr_fan128.md) scaled by rows to this step's average panel"
-                                      % (PANEL_CAPTURE_BYTES / 1e6))
+    peaks = load_peaks()
+    dom = max(kstats, key=lambda s_: s_["ms"])
+    roof = roofline(dom, args.prec, ms / args.steps, peaks)
 
     # ---- end to end through the public API with host buffers
     Bh = B.cpu()
@@ -382,6 +484,30 @@ def main():
     if args.e2e_steps > 0:
         e2e = {"value": world * k * args.e2e_steps / t_e2e, "unit": "slices/s",
                "h2d_bytes_per_step": m_sys * k * 8, "d2h_bytes_per_step": n_sys * k * 8}
+    del Bp, Xp
+
+    # ---- the plain FP64 QR path on the same scan, once (after the timed
+    # region): relative error of the mixed-precision result against it and
+    # its own slices/s
+    fp64 = None
+    if args.fp64_check and args.prec != "f64":
+        torch.cuda.empty_cache()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        X64, rep64 = ctqr.reconstruct_scan(g, B, prec=ctqr.Prec.F64, lam=lam)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        d = X_mixed - X64
+        fp64 = {"rel_err_vs_fp64_qr": float(torch.linalg.norm(d) / torch.linalg.norm(X64)),
+                "max_abs_err_vs_fp64_qr_rel": float(d.abs().max() / X64.abs().max()),
+                "fp64_qr_slices_per_s": k / (ms64 / 1e3), "fp64_ms_per_step": ms64,
+                "fp64_qr_tflops": qr_flops(m_sys, n_sys) / (rep64.ms_factor / 1e3) / 1e12,
+                "fp64_phase_ms": {"build": rep64.ms_build, "factor": rep64.ms_factor, "solve": rep64.ms_solve},
+                "speedup_mixed_vs_fp64": (ms64 / 1e3) / (ms_max / args.steps / 1e3),
+                "measured": "one FP64 reconstruct_scan of the same scan after the timed steps, CUDA events"}
+        del X64
 
     line = {"metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -395,17 +521,27 @@ def main():
             "qr_tflops": qr_flops(m_sys, n_sys) / (ms_factor / 1e3) / 1e12,
             "solve_slices_per_s": k / (ms_solve / 1e3),
             "phase_ms": {"build": ms_build, "factor": ms_factor, "solve": ms_solve},
-            "rel_err_vs_fp64_qr": rel_err,
+            "rel_err_vs_fp64_qr": fp64["rel_err_vs_fp64_qr"] if fp64 else None,
+            "fp64_qr": fp64,
             "normal_eq_residual": normal_eq,
             "refine_iterations": reps[-1].iterations,
-            "fp64_qr_tflops": fp64_qr_tflops,
+            "panel_arithmetic": ("FP32-stored factors: Cholesky-QR panels whose Gram matrix and row solves are "
+                                 "compensated FP32 (Dot2) products, the 32x32 algebra, tau and T in FP64"
+                                 if args.prec != "f64" else "FP64 per-column Householder panels"),
             "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "kernels": {s["name"]: {"launches": s["launches"], "ms": round(s["ms"], 3)}
-                        for s in kstats if s["launches"]}}
+            "kernels": {s_["name"]: {"launches": s_["launches"], "ms": round(s_["ms"], 3)}
+                        for s_ in kstats if s_["launches"]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_cpu, cores, desc = oracle_sample(cfg, k, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": k / t_cpu, "unit": "slices/s", "cores": cores, "kind": "oracle",
-                                "sample": desc}
+        sampler = OracleSampler(cfg, k, m_sys, n_sys, target_s=args.cpu_seconds)
+        t_meas, t_full = sampler.sample()
+        cpu = {"value": k / t_full, "unit": "slices/s", "cores": sampler.cores, "kind": "oracle",
+               "sample": sampler.describe() + f" (sample measured {t_meas:.1f} s)"}
+        try:
+            t_lp, thr, desc = sampler.lapack()
+            cpu["lapack"] = {"value": k / t_lp, "unit": "slices/s", "threads": thr, "sample": desc}
+        except Exception as exc:  # LAPACK timing is context only
+            cpu["lapack"] = {"unavailable": str(exc)[:200]}
+        line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -372,6 +372,39 @@ uint64_t ct_kernel_launches(void);
 ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const ct_batch_opts* opts,
                               ct_batch_report* report, void* stream);
 
+/* A factor kept beyond the process.  The paper computes the factorization
+ * once and stores it so that every later batch of slices reuses it (Sec.
+ * II-B; its factor is kept on disk as tile files).  ct_factor_save writes the
+ * factored matrix, tau, the panel T blocks and (CT_PREC_TF32) the per-block
+ * V^T V and T stores to one file: a 128-byte header (magic "CTQRFAC1",
+ * version, m, n, nb, prec, storage type, `tag`, payload size, FNV-1a-64
+ * checksum of the payload) followed by the arrays, column-major with
+ * leading dimension m.  `tag` is the caller's identifier of what was
+ * factored (e.g. ct_geometry_hash of the scan), 0 for none.  The copies go
+ * through a 64 MiB page-locked host buffer in chunks; synchronous on
+ * `stream`.  Errors: CT_ERR_INVALID for a NULL argument or a file that
+ * cannot be written; CT_ERR_CUDA / CT_ERR_NOMEM from the copies. */
+ct_status ct_factor_save(const ct_factor* f, const char* path, uint64_t tag, void* stream);
+
+/* Read a file written by ct_factor_save into a new factor on the current
+ * device (*out; release with ct_factor_destroy).  *tag (may be NULL)
+ * receives the stored tag.  Synchronous on `stream`.  CT_ERR_INVALID when
+ * the file is missing, its header is malformed or inconsistent, its size is
+ * not the header's, or the payload checksum does not match (nothing is
+ * returned then); CT_ERR_NOMEM when the factor does not fit. */
+ct_status ct_factor_load(const char* path, ct_factor** out, uint64_t* tag, void* stream);
+
+/* Shape, arithmetic and tag of a factor file, from its header alone (no GPU
+ * needed; any output may be NULL).  CT_ERR_INVALID as for ct_factor_load's
+ * header checks. */
+ct_status ct_factor_file_info(const char* path, int64_t* m, int64_t* n, int* nb, ct_prec* prec,
+                              uint64_t* tag);
+
+/* A 64-bit FNV-1a hash of a geometry and its lambda (every field, +0 and -0
+ * alike), never 0: a tag that ties a saved factor to the scan it factors.
+ * Returns 0 for NULL. */
+uint64_t ct_geometry_hash(const ct_geometry* geom, double lambda);
+
 /* Release a factor and its device memory (NULL is a no-op).  Waits for the
  * device to finish all queued work first, so a factor may be destroyed while
  * kernels that use it are still in flight. */

@@ -51,19 +51,6 @@ struct Scratch {
   }
 };
 
-void free_factor(ct_factor* f) {
-  if (!f) return;
-  if (f->owns_F && f->F) cudaFree(f->F);
-  if (f->tau) cudaFree(f->tau);
-  if (f->T) cudaFree(f->T);
-  if (f->status) cudaFree(f->status);
-  if (f->barrier) cudaFree(f->barrier);
-  if (f->partials) cudaFree(f->partials);
-  if (f->Gblk) cudaFree(f->Gblk);
-  if (f->Tblk) cudaFree(f->Tblk);
-  delete f;
-}
-
 template <typename T>
 ct_status dev_alloc(T** p, size_t elems) {
   if (getenv("CTQR_FAULT_NOMEM")) return CT_ERR_NOMEM;
@@ -497,6 +484,41 @@ class Refiner {
 namespace ctqr {
 int64_t npanels(const ct_factor* f) { return (f->n + f->nb - 1) / f->nb; }
 
+void free_factor(ct_factor* f) {
+  if (!f) return;
+  if (f->owns_F && f->F) cudaFree(f->F);
+  if (f->tau) cudaFree(f->tau);
+  if (f->T) cudaFree(f->T);
+  if (f->status) cudaFree(f->status);
+  if (f->barrier) cudaFree(f->barrier);
+  if (f->partials) cudaFree(f->partials);
+  if (f->Gblk) cudaFree(f->Gblk);
+  if (f->Tblk) cudaFree(f->Tblk);
+  delete f;
+}
+
+ct_status alloc_factor_aux(ct_factor* f, const DeviceInfo& di) {
+  const bool tc = f->prec == CT_PREC_TF32;
+  const int64_t n = f->n, np = npanels(f);
+  f->partials_elems = panel_partials_elems(di.sms, f->nb);
+  ct_status st;
+  if ((st = dev_alloc(&f->tau, (size_t)n)) != CT_OK ||
+      (st = dev_alloc(&f->T, (size_t)np * f->nb * f->nb)) != CT_OK ||
+      (st = dev_alloc(&f->status, 1)) != CT_OK ||
+      (st = dev_alloc(&f->barrier, 3)) != CT_OK ||
+      (st = dev_alloc(&f->partials, f->partials_elems)) != CT_OK ||
+      (tc && (st = dev_alloc(&f->Gblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK) ||
+      (tc && (st = dev_alloc(&f->Tblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK))
+    return st;
+  return CT_OK;
+}
+
+ct_status alloc_factor_matrix(ct_factor* f) {
+  f->owns_F = true;
+  f->ld = (f->m + 3) / 4 * 4;
+  return dev_alloc((char**)&f->F, (size_t)f->ld * f->n * (f->store == CT_F64 ? 8 : 4));
+}
+
 // Apply Q^T (all panels, factorization order) to the mr = m rows of C (k
 // columns, element type c_f64 ? FP64 : FP32).
 ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
@@ -623,14 +645,7 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
     if (st != CT_OK) { free_factor(f); return st; }
   }
   const int64_t np = ctqr::npanels(f);
-  f->partials_elems = panel_partials_elems(di.sms, f->nb);
-  if ((st = dev_alloc(&f->tau, (size_t)n)) != CT_OK ||
-      (st = dev_alloc(&f->T, (size_t)np * f->nb * f->nb)) != CT_OK ||
-      (st = dev_alloc(&f->status, 1)) != CT_OK ||
-      (st = dev_alloc(&f->barrier, 3)) != CT_OK ||
-      (st = dev_alloc(&f->partials, f->partials_elems)) != CT_OK ||
-      (tc && (st = dev_alloc(&f->Gblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK) ||
-      (tc && (st = dev_alloc(&f->Tblk, (size_t)((n + 127) / 128) * 128 * 128)) != CT_OK)) {
+  if ((st = alloc_factor_aux(f, di)) != CT_OK) {
     free_factor(f);
     return st;
   }

@@ -162,6 +162,14 @@ struct ct_factor {
 namespace ctqr {
 
 int64_t npanels(const ct_factor* f);
+// Release a factor and every buffer it owns (no synchronisation).
+void free_factor(ct_factor* f);
+// Allocate tau, the panel T blocks, the status word, the barrier counters,
+// the panel partials and (CT_PREC_TF32) the per-outer-block G and T stores
+// for a factor whose m, n, nb and prec are set (api.cu).
+ct_status alloc_factor_aux(ct_factor* f, const DeviceInfo& di);
+// Allocate an owned factored matrix (ld = m rounded up to 4 elements).
+ct_status alloc_factor_matrix(ct_factor* f);
 
 // ---- system matrix (siddon.cu) --------------------------------------------
 ct_status launch_build_system(const ct_geometry* g, ct_dtype dtype, double lambda, void* A,

@@ -54,8 +54,10 @@ struct PanelArgs {
   int* status;
   int row0;              // rows held by CTA 0 (the panel's top nbp rows), the
                          // others rp each after them; 0: rp rows per CTA from row 0
-  int dot2;              // Cholesky-QR: Gram and row solves as compensated FP32
-                         // products on an FP32 copy of the rows (else FP64)
+  int dot2;              // Cholesky-QR: 1 = Gram and row solves as compensated
+                         // FP32 products on an FP32 copy of the rows beside the
+                         // FP64 one; 2 = the same with the FP32 rows only (tall
+                         // panels whose FP64 rows do not fit); 0 = FP64
 };
 
 // First panel row and row count of CTA b.
@@ -402,19 +404,21 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   const int nbp = a.nbp, rp = a.rp, tid = threadIdx.x;
   const int P = pow2_at_least(nbp);           // leading dimension of the small matrices
   const int nn = P * P;
-  double* slab = smem;                        // [nbp][rp] this CTA's rows
-  double* G = slab + (size_t)nbp * rp;        // Gram, then R1 in its upper part
+  // with a.dot2: the rows in FP32 (exact: the data is FP32) and M^{-1} split
+  // into FP32 high and low parts; with a.dot2 == 2 only the FP32 rows are
+  // kept (they come first, the FP64 small matrices after them)
+  const bool dot2 = a.dot2 != 0, f32only = a.dot2 == 2;
+  double* slab = f32only ? nullptr : smem;    // [nbp][rp] this CTA's rows (FP64)
+  double* G = f32only ? (double*)((char*)smem + (((size_t)nbp * rp * sizeof(float) + 15) & ~(size_t)15))
+                      : slab + (size_t)nbp * rp;  // Gram, then R1 in its upper part
   double* Ri = G + nn;                        // R1^{-1} (upper), later T
   double* W = Ri + nn;                        // P1, then Q1 - S -> L1 (strict lower) / U (upper)
   double* M = W + nn;                         // scratch, then M^{-1} = R1^{-1} U^{-1}
   double* X = M + nn;                         // scratch / U^{-1} / (L1^T)^{-1}
   double* sv = X + nn;                        // [P] s_i
   double* dv = sv + P;                        // [P] column sums
-  // with a.dot2: the same rows in FP32 (exact: the data is FP32) and M^{-1}
-  // split into FP32 high and low parts
-  const bool dot2 = a.dot2 != 0;
-  float* slabf = (float*)(dv + P);            // [nbp][rp]
-  float* Mh = slabf + (size_t)nbp * rp;
+  float* slabf = f32only ? (float*)smem : (float*)(dv + P);  // [nbp][rp]
+  float* Mh = f32only ? (float*)(dv + P) : slabf + (size_t)nbp * rp;
   float* Ml = Mh + nn;
   __shared__ int s_ok;
   int64_t rb;
@@ -432,13 +436,13 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
       for (int u = 0; u < 8; ++u) v[u] = src[(int64_t)(c + u) * a.ld];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        slab[(size_t)(c + u) * rp + r] = (double)v[u];
+        if (!f32only) slab[(size_t)(c + u) * rp + r] = (double)v[u];
         if (dot2) slabf[(size_t)(c + u) * rp + r] = (float)v[u];
       }
     }
     for (; c < nbp; ++c) {
       const S v = src[(int64_t)c * a.ld];
-      slab[(size_t)c * rp + r] = (double)v;
+      if (!f32only) slab[(size_t)c * rp + r] = (double)v;
       if (dot2) slabf[(size_t)c * rp + r] = (float)v;
     }
   }
@@ -586,8 +590,10 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
   }
   __syncthreads();
   if (!s_ok) {
-    // per-column Householder on the same slab; G.. onward is free
-    panel_householder<S, double>(a, slab, G, smem);
+    // per-column Householder on the same slab; G.. onward is free (FP32
+    // rows only: the per-column panel in FP32 arithmetic on them)
+    if (f32only) panel_householder<S, float>(a, slabf, G, smem);
+    else panel_householder<S, double>(a, slab, G, smem);
     return;
   }
 
@@ -661,7 +667,9 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
             d.add(x, Mh[i + j * P]);
             d.add_small(x, Ml[i + j * P]);
           }
-          slab[(size_t)j * rp + r] = (double)__fadd_rn(d.s, d.c);
+          const float y = __fadd_rn(d.s, d.c);
+          if (f32only) slabf[(size_t)j * rp + r] = y;  // column j read above, before this write
+          else slab[(size_t)j * rp + r] = (double)y;
         }
       } else {
         for (int j = nbp - 1; j >= 0; --j) {
@@ -672,13 +680,17 @@ __global__ void __launch_bounds__(kPT, 1) k_panel_cqr(PanelArgs a) {
       }
     } else {
       const int i = (int)gr;
-      for (int j = 0; j < nbp; ++j)
-        slab[(size_t)j * rp + r] = j >= i ? sv[i] * G[i + j * P] : W[i + j * P];
+      for (int j = 0; j < nbp; ++j) {
+        const double y = j >= i ? sv[i] * G[i + j * P] : W[i + j * P];
+        if (f32only) slabf[(size_t)j * rp + r] = (float)y;
+        else slab[(size_t)j * rp + r] = y;
+      }
     }
   }
   __syncthreads();
   for (int c = 0; c < nbp; ++c)
-    for (int r = tid; r < nr; r += kPT) P_[rb + r + c * a.ld] = (S)slab[(size_t)c * rp + r];
+    for (int r = tid; r < nr; r += kPT)
+      P_[rb + r + c * a.ld] = f32only ? (S)slabf[(size_t)c * rp + r] : (S)slab[(size_t)c * rp + r];
 
   // 5. CTA 0 (which holds only the top rows, so it has no row solves):
   //    T = -U S L1^{-T} and tau = diag(T).  L1^{-T} is the inverse of the
@@ -712,12 +724,15 @@ int panel_grid(int64_t mr, const DeviceInfo& di, size_t mth) {
   return grid;
 }
 
-size_t panel_cqr_smem_bytes(int nbp, int rp, bool dot2) {
+// dot2: 0 FP64 rows, 1 FP64 and FP32 rows, 2 FP32 rows only.
+size_t panel_cqr_smem_bytes(int nbp, int rp, int dot2) {
   const size_t P = (size_t)pow2_at_least(nbp);
-  size_t bytes = ((size_t)nbp * rp + 5 * P * P + 2 * P) * sizeof(double) +
-                 (dot2 ? ((size_t)nbp * rp + 2 * P * P) * sizeof(float) : 0);  // FP32 slab copy, split M^{-1}
+  const size_t rows64 = dot2 == 2 ? 0 : (size_t)nbp * rp * sizeof(double);
+  const size_t rows32 = dot2 == 0 ? 0 : (((size_t)nbp * rp * sizeof(float) + 15) & ~(size_t)15);
+  size_t bytes = rows64 + rows32 + (5 * P * P + 2 * P) * sizeof(double) +
+                 (dot2 ? 2 * P * P * sizeof(float) : 0);  // split M^{-1}
   // the Householder fallback: its buffers in place of G.., T at the start
-  const size_t fb = ((size_t)nbp * rp + kSmallDoubles + kMaxNb) * sizeof(double);
+  const size_t fb = rows64 + rows32 + (kSmallDoubles + kMaxNb) * sizeof(double);
   const size_t t_need = ((size_t)nbp * (nbp - 1) / 2 + (size_t)nbp * nbp + nbp) * sizeof(double);
   bytes = bytes < fb ? fb : bytes;
   return bytes < t_need ? t_need : bytes;
@@ -757,9 +772,18 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
     rp_c = (int)((mr - nbp + grid - 2) / (grid - 1));
     if (rp_c < nbp) rp_c = nbp;
   }
-  bool cqr = sizeof(S) == 4 && cqr_enabled() && rp >= nbp && panel_cqr_smem_bytes(nbp, rp_c, false) <= limit;
-  // compensated FP32 Gram and row solves when their FP32 copy of the rows fits
-  const bool dot2 = cqr && panel_cqr_smem_bytes(nbp, rp_c, true) <= limit;
+  const bool cqr_ok = sizeof(S) == 4 && cqr_enabled() && rp >= nbp;
+  // compensated FP32 Gram and row solves beside the FP64 rows when both fit;
+  // for taller panels the FP32 rows alone (compensated products throughout)
+  int dot2 = 0;
+  bool cqr = false;
+  if (cqr_ok && panel_cqr_smem_bytes(nbp, rp_c, 0) <= limit) {
+    cqr = true;
+    dot2 = panel_cqr_smem_bytes(nbp, rp_c, 1) <= limit ? 1 : 0;
+  } else if (cqr_ok && panel_cqr_smem_bytes(nbp, rp_c, 2) <= limit) {
+    cqr = true;
+    dot2 = 2;
+  }
   if (cqr) {
     if (grid >= 2 && mr > nbp) row0 = nbp;
     rp = rp_c;
@@ -781,7 +805,7 @@ ct_status launch_panel_t(ct_factor* f, int64_t j0, int nbp, double* T, cudaStrea
   a.rp = rp;
   a.grid = grid;
   a.row0 = row0;
-  a.dot2 = dot2 ? 1 : 0;
+  a.dot2 = dot2;
   a.tau = f->tau + j0;
   a.T = T;
   a.ldt = f->nb;

@@ -15,14 +15,24 @@
 //                      expect_tx completion;
 //   warp 1 (one lane)  allocates TMEM and issues tcgen05.mma.kind::tf32
 //                      (M = 128, N = BN, K = 8 each, 4 per slice), committing
-//                      each stage back to the producer;
+//                      each stage back to the producer; the K range is cut
+//                      into chunks of CH slices accumulated alternately in two
+//                      TMEM buffers (see below);
 //   warps 2-5          split3: turn each landed slice x into a TF32-exact high
 //                      part hi = trunc_tf32(x) (in place) and a low part
 //                      lo = x - hi, so the three products hi*hi + hi*lo + lo*hi
 //                      recover FP32-level accuracy (error-compensated TF32);
-//                      afterwards they drain the FP32 accumulator from TMEM
-//                      with tcgen05.ld and apply the epilogue (coalesced
-//                      column-major stores, one row per thread).
+//                      as each chunk completes they add its TMEM buffer into
+//                      an FP32 register accumulator (tcgen05.ld, one row per
+//                      thread) and release the buffer; at the end they apply
+//                      the epilogue (column-major stores).
+// Why chunks: the tensor cores' FP32 accumulation rounds each MMA's sum
+// towards zero, so one accumulator over a long K (the V^T C product runs
+// over all rows of the trailing matrix, up to 135,232) drifts by about
+// K/8 * 3 truncations of its running value: relative errors near 1e-2 at
+// that height, which wrecked the preconditioner of the 256 x 256 system.
+// Restarting the TMEM accumulation every CH slices and summing the chunks on
+// the CUDA cores (round to nearest) bounds the drift by the chunk length.
 // Every wait is bounded (CT_ERR_TIMEOUT in the status word, then an orderly
 // exit that still waits for issued copies and MMAs and frees TMEM).
 #include <cuda.h>
@@ -35,11 +45,15 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 32;  // floats per K slice = one 128-byte swizzle row
 constexpr int kThreads = 192;
+// K slices (of kBK rows) per TMEM accumulation chunk: 256 rows, about 96
+// truncating accumulations of 3xTF32 MMAs per chunk.
+constexpr int kAccChunkSlices = 8;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 struct TcArgs {
   int64_t M, N, K;
-  int64_t k_chunk;
+  int64_t k_chunk;   // K rows per split (blockIdx.z)
+  int ch;            // K slices per TMEM accumulation chunk
   float* C;
   int64_t ldc;
   int64_t split_stride;
@@ -164,8 +178,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* conv = full + STAGES;
   uint64_t* empty = conv + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* tfull = empty + STAGES;   // [2] a chunk's MMAs are done in TMEM buffer b
+  uint64_t* tempty = tfull + 2;       // [2] the epilogue warps have read buffer b
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * kBM, n0 = (int64_t)blockIdx.y * BN;
@@ -173,6 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   int64_t kend = kbeg + args.k_chunk;
   if (kend > args.K) kend = args.K;
   const int nk = kend > kbeg ? (int)((kend - kbeg + kBK - 1) / kBK) : 0;
+  const int CH = args.ch > 0 ? args.ch : 1;
+  const int nch = (nk + CH - 1) / CH;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -180,13 +197,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&conv[s], 4);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -221,31 +241,59 @@ __global__ void __launch_bounds__(kThreads, 1)
                              ((uint32_t)(kBM >> 4) << 24);
       for (int kt = 0; kt < nk; ++kt) {
         const int s = kt % STAGES, u = kt / STAGES;
+        const int c = kt / CH, b = c & 1;
+        const bool first = kt % CH == 0;
+        // buffer b must have been read out for chunk c - 2
+        if (first && c >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((c >> 1) - 1) & 1), args.status)) break;
         if (!mbar_wait(SPLIT3 ? &conv[s] : &full[s], (uint32_t)(u & 1), args.status)) break;
         tc_fence_after();
         unsigned char* st = smem + s * STAGE_BYTES;
         const uint64_t da = sdesc_sw128(st), db = sdesc_sw128(st + A_BYTES);
+        const uint32_t d = tmem + (uint32_t)(b * BN);
 #pragma unroll
         for (int kk = 0; kk < kBK / 8; ++kk) {
           const uint64_t adv = (uint64_t)(kk * 2);  // 8 floats = 32 bytes = 2 x 16 B
-          mma_tf32(tmem, da + adv, db + adv, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(d, da + adv, db + adv, idesc, (!first || kk > 0) ? 1u : 0u);
           if (SPLIT3) {
             const uint64_t dal = sdesc_sw128(st + A_BYTES + B_BYTES);
             const uint64_t dbl = sdesc_sw128(st + 2 * A_BYTES + B_BYTES);
-            mma_tf32(tmem, dal + adv, db + adv, idesc, 1u);
-            mma_tf32(tmem, da + adv, dbl + adv, idesc, 1u);
+            mma_tf32(d, dal + adv, db + adv, idesc, 1u);
+            mma_tf32(d, da + adv, dbl + adv, idesc, 1u);
           }
         }
         mma_commit(&empty[s]);
+        if (kt % CH == CH - 1 || kt == nk - 1) mma_commit(&tfull[b]);
       }
-      mma_commit(done);
     }
   } else {
     // warps 2..5
     const int cw = warp - 2;  // 0..3
+    const int lg = warp & 3;  // TMEM lanes 32*lg .. +31 = tile rows
+    float acc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    int next = 0;  // next chunk to read out
+    bool ok = true;
+    // add chunk c's TMEM buffer into acc and release the buffer
+    auto drain = [&](int c) -> bool {
+      const int b = c & 1;
+      if (!mbar_wait(&tfull[b], (uint32_t)((c >> 1) & 1), args.status)) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int cc = 0; cc < BN; cc += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + cc), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[cc + j] += v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+      return true;
+    };
     if (SPLIT3) {
       const int t = cw * 32 + lane;
-      for (int kt = 0; kt < nk; ++kt) {
+      for (int kt = 0; kt < nk && ok; ++kt) {
         const int s = kt % STAGES, u = kt / STAGES;
         if (!mbar_wait(&full[s], (uint32_t)(u & 1), args.status)) break;
         unsigned char* st = smem + s * STAGE_BYTES;
@@ -268,30 +316,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&conv[s]);
+        // the chunk before the one this slice completes is long done
+        if (kt % CH == CH - 1)
+          while (next < kt / CH && ok) ok = drain(next++);
       }
     }
-    // Epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 = tile rows.
-    if (mbar_wait(done, 0u, args.status)) {
-      tc_fence_after();
-      const int lg = warp & 3;
+    while (next < nch && ok) ok = drain(next++);
+    // Epilogue (one row per thread).
+    if (ok) {
       const int64_t row = m0 + lg * 32 + lane;
       float* C = args.C + (args.mode == 0 ? (int64_t)blockIdx.z * args.split_stride : 0);
-      for (int c = 0; c < BN; c += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c, v);
-        if (nk == 0) {
+      if (row < args.M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0.f;
-        }
-        if (row < args.M) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t col = n0 + c + j;
-            if (col < args.N) {
-              float* p = C + row + col * args.ldc;
-              if (args.mode == 0) *p = v[j];
-              else *p -= v[j];
-            }
+        for (int j = 0; j < BN; ++j) {
+          const int64_t col = n0 + j;
+          if (col < args.N) {
+            float* p = C + row + col * args.ldc;
+            if (args.mode == 0) *p = acc[j];
+            else *p -= acc[j];
           }
         }
       }
@@ -301,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
                  : "memory");
   }
 }
@@ -624,6 +666,7 @@ ct_status tc_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, i
   a.N = N;
   a.K = K;
   a.k_chunk = chunk;
+  a.ch = kAccChunkSlices;
   a.C = C;
   a.ldc = ldc;
   a.split_stride = split_stride;

@@ -117,6 +117,11 @@ SIGNATURES = {
     "ct_reconstruct_batch": ([_VP, _VP, _I, _I64, _VP, _I64, _VP, _I64, _I64,
                               ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
     "ct_factor_destroy": ([_VP], None),
+    "ct_factor_save": ([_VP, ctypes.c_char_p, ctypes.c_uint64, _VP], _I),
+    "ct_factor_load": ([ctypes.c_char_p, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_uint64), _VP], _I),
+    "ct_factor_file_info": ([ctypes.c_char_p, _P64, _P64, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(ctypes.c_uint64)], _I),
+    "ct_geometry_hash": ([ctypes.POINTER(Geometry), _D], ctypes.c_uint64),
     "ct_reconstruct_scan": ([ctypes.POINTER(Geometry), _D, _I, _VP, _I64, _VP, _I64, _I64, _I,
                              ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
     "ct_gemm_tf32_tn": ([_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _I, _I, _VP], _I),
@@ -294,6 +299,31 @@ def qr_factor(A: torch.Tensor, prec: Prec = Prec.F64, nb: int = 0, in_place: boo
     _check(load().ct_qr_factor(A.data_ptr(), _dt(A), m, n, _ld(A), int(prec), ctypes.byref(opts),
                                ctypes.byref(h), _stream()), "ct_qr_factor")
     return Factor(h.value, keep=A if in_place else None)
+
+
+def factor_save(f: Factor, path: str, tag: int = 0) -> None:
+    """Write the factor to a file (ct_factor_save)."""
+    _check(load().ct_factor_save(f.handle, os.fsencode(path), tag, _stream()), "ct_factor_save")
+
+
+def factor_load(path: str) -> tuple[Factor, int]:
+    """Read a factor file into a new factor on the current device; returns (factor, tag)."""
+    h, tag = ctypes.c_void_p(), ctypes.c_uint64()
+    _check(load().ct_factor_load(os.fsencode(path), ctypes.byref(h), ctypes.byref(tag), _stream()),
+           "ct_factor_load")
+    return Factor(h.value), tag.value
+
+
+def factor_file_info(path: str) -> dict:
+    """Header of a factor file (no GPU needed)."""
+    m, n, nb, prec, tag = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()
+    _check(load().ct_factor_file_info(os.fsencode(path), ctypes.byref(m), ctypes.byref(n), ctypes.byref(nb),
+                                      ctypes.byref(prec), ctypes.byref(tag)), "ct_factor_file_info")
+    return dict(m=m.value, n=n.value, nb=nb.value, prec=Prec(prec.value), tag=tag.value)
+
+
+def geometry_hash(geom, lam: float = 0.0) -> int:
+    return int(load().ct_geometry_hash(ctypes.byref(geometry(geom)), lam))
 
 
 def factor_matrix(f: Factor) -> tuple[torch.Tensor, torch.Tensor]:

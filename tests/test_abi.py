@@ -62,3 +62,45 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.ct_apply_qt_f32(None, None, 1, 1, None) == ctqr.CT_ERR_INVALID
     assert lib.ct_trsm_solve(None, None, 1, 1, None) == ctqr.CT_ERR_INVALID
     lib.ct_factor_destroy(None)
+
+
+def test_factor_file_header_is_read_without_gpu(tmp_path):
+    """The factor file's header format (ct_factor_save): magic, version,
+    header size, m, n, nb, prec, storage type, block flag, tag, payload size,
+    checksum; ct_factor_file_info reads it without touching a GPU and refuses
+    a malformed one."""
+    import struct
+    from paper_1907_01891_gb300 import ctqr
+    m, n, nb = 10, 4, 2
+    payload = m * n * 8 + n * 8 + 2 * nb * nb * 8
+    hdr = struct.pack("<8sII qq iiii QQQ", b"CTQRFAC1", 1, 128, m, n, nb, 0, 0, 0, 77, payload, 0)
+    hdr += b"\0" * (128 - len(hdr))
+    good = tmp_path / "good.ctqr"
+    good.write_bytes(hdr + b"\0" * payload)
+    assert ctqr.factor_file_info(str(good)) == dict(m=m, n=n, nb=nb, prec=ctqr.Prec.F64, tag=77)
+    for name, blob in [("magic", b"CTQRFAC2" + hdr[8:]), ("short", hdr[:100]),
+                       ("m_lt_n", hdr[:16] + struct.pack("<qq", 3, 4) + hdr[32:]),
+                       ("store", hdr[:40] + struct.pack("<i", 1) + hdr[44:])]:
+        p = tmp_path / f"{name}.ctqr"
+        p.write_bytes(blob)
+        with pytest.raises(ctqr.CtError) as e:
+            ctqr.factor_file_info(str(p))
+        assert e.value.status == ctqr.CT_ERR_INVALID, name
+    out, tag = ctypes.c_void_p(), ctypes.c_uint64()
+    lib = ctqr.load()
+    assert lib.ct_factor_load(str(tmp_path / "missing.ctqr").encode(), ctypes.byref(out), ctypes.byref(tag),
+                              None) == ctqr.CT_ERR_INVALID
+    assert lib.ct_factor_load(str(tmp_path / "magic.ctqr").encode(), ctypes.byref(out), ctypes.byref(tag),
+                              None) == ctqr.CT_ERR_INVALID
+    assert not out.value
+
+
+def test_geometry_hash_distinguishes_scans_without_gpu():
+    from paper_1907_01891_gb300 import ctqr
+    from paper_1907_01891_gb300 import inputs as I
+    g = I.CONFIG2["geom"]
+    h = ctqr.geometry_hash(g)
+    assert h != 0 and h == ctqr.geometry_hash(g, 0.0) == ctqr.geometry_hash(g, -0.0)
+    assert h != ctqr.geometry_hash(g, 1e-3)
+    assert h != ctqr.geometry_hash(I.CONFIG3["geom"])
+    assert h != ctqr.geometry_hash(I.fan_geometry(128, 128, 183))
