@@ -219,23 +219,67 @@ class OracleSampler:
                 f"first {self.ns} of {self.n} columns at full height m={self.m} (scaled by flops); "
                 f"the full step is extrapolated from the measured rates")
 
-    def lapack(self):
+    def lapack(self, target_s: float):
         """The strong CPU baseline: LAPACK's blocked QR least-squares solve
-        (torch.linalg.lstsq, driver gels, on the CPU) of the same m x ns
-        sample, flop-scaled to n columns.  Returns (extrapolated seconds of a
-        full step's QR + solve, threads, description)."""
+        (torch.linalg.lstsq, driver gels, on the CPU) of an m x ns sample
+        (ns grown from 32 until one solve takes about target_s / 4),
+        flop-scaled to n columns.  Returns (extrapolated seconds of a full
+        step's QR + solve, threads, description)."""
         import torch
-        ns = min(self.n, 4 * self.ns)
-        A = torch.randn(self.m, ns, dtype=torch.float64)
+        ns, t = 32, 0.0
         B = torch.randn(self.m, self.k, dtype=torch.float64)
-        t0 = time.perf_counter()
-        torch.linalg.lstsq(A, B, driver="gels")
-        t = time.perf_counter() - t0
+        while True:
+            A = torch.randn(self.m, ns, dtype=torch.float64)
+            t0 = time.perf_counter()
+            torch.linalg.lstsq(A, B, driver="gels")
+            t = time.perf_counter() - t0
+            if t > target_s / 4 or ns >= self.n:
+                break
+            ns = min(self.n, int(ns * min(4.0, max(1.25, math.sqrt(target_s / 2 / max(t, 1e-3))))))
         full = t * (qr_flops(self.m, self.n) + solve_flops(self.m, self.n, self.k)) / (
             qr_flops(self.m, ns) + solve_flops(self.m, ns, self.k))
         return full, torch.get_num_threads(), (
             f"LAPACK gels (torch.linalg.lstsq on the CPU, {torch.get_num_threads()} threads) on the first {ns} "
             f"of {self.n} columns at full height, measured {t:.2f} s, flop-scaled (QR + solve only)")
+
+
+def _cpu_baseline_worker(workload, k, m, n, target_s):
+    """The oracle sample and the LAPACK sample (runs in a spawned process)."""
+    cfg = WORKLOADS[workload]
+    sampler = OracleSampler(cfg, k, m, n, target_s=target_s)
+    t_meas, t_full = sampler.sample()
+    cpu = {"value": k / t_full, "unit": "slices/s", "cores": sampler.cores, "kind": "oracle",
+           "sample": sampler.describe() + f" (sample measured {t_meas:.1f} s)"}
+    try:
+        t_lp, thr, desc = sampler.lapack(target_s)
+        cpu["lapack"] = {"value": k / t_lp, "unit": "slices/s", "threads": thr, "sample": desc}
+    except Exception as exc:  # LAPACK timing is context only
+        cpu["lapack"] = {"unavailable": str(exc)[:200]}
+    return cpu
+
+
+def cpu_baseline_bounded(workload, k, m, n, target_s, timeout_s):
+    """cpu_baseline object from a spawned process that is stopped after
+    timeout_s seconds (the host-side samples can never hold the GPU job)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(1)
+    try:
+        r = pool.apply_async(_cpu_baseline_worker, (workload, k, m, n, target_s))
+        return r.get(timeout=timeout_s)
+    except mp.TimeoutError:
+        return {"unavailable": f"the oracle sample did not finish within {timeout_s:.0f} s"}
+    finally:
+        pool.terminate()
+        pool.join()
+
+
+_T0 = time.perf_counter()
+
+
+def log(msg: str) -> None:
+    """Progress on stderr with the seconds since the start."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def reference_main(args, cfg, k, m_sys, n_sys, world, rank):
@@ -417,9 +461,11 @@ def main():
     def step():
         return ctqr.reconstruct_scan(g, B, X=X, prec=prec, lam=lam)
 
+    log(f"inputs ready ({m_sys} x {n_sys}, {k} slices); warm-up")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    log("warm-up done; timed steps")
     # Accuracy at any size: optimality of the (regularized) least-squares
     # solution, ||A^T (b - A x) - lam^2 x|| / (||A||_F^2 ||x||).
     r = B[:g.m] - A @ X
@@ -470,6 +516,7 @@ def main():
     dom = max(kstats, key=lambda s_: s_["ms"])
     roof = roofline(dom, args.prec, ms / args.steps, peaks)
 
+    log("timed steps done; end to end from host buffers")
     # ---- end to end through the public API with host buffers
     Bh = B.cpu()
     Bp = torch.empty((k, m_sys), dtype=torch.float64).pin_memory().t()
@@ -491,6 +538,7 @@ def main():
     # its own slices/s
     fp64 = None
     if args.fp64_check and args.prec != "f64":
+        log("FP64 QR path on the same scan")
         torch.cuda.empty_cache()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -532,16 +580,9 @@ def main():
             "kernels": {s_["name"]: {"launches": s_["launches"], "ms": round(s_["ms"], 3)}
                         for s_ in kstats if s_["launches"]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sampler = OracleSampler(cfg, k, m_sys, n_sys, target_s=args.cpu_seconds)
-        t_meas, t_full = sampler.sample()
-        cpu = {"value": k / t_full, "unit": "slices/s", "cores": sampler.cores, "kind": "oracle",
-               "sample": sampler.describe() + f" (sample measured {t_meas:.1f} s)"}
-        try:
-            t_lp, thr, desc = sampler.lapack()
-            cpu["lapack"] = {"value": k / t_lp, "unit": "slices/s", "threads": thr, "sample": desc}
-        except Exception as exc:  # LAPACK timing is context only
-            cpu["lapack"] = {"unavailable": str(exc)[:200]}
-        line["cpu_baseline"] = cpu
+        log("CPU baselines (oracle, LAPACK) in a spawned process")
+        line["cpu_baseline"] = cpu_baseline_bounded(args.workload, k, m_sys, n_sys, args.cpu_seconds,
+                                                    timeout_s=8 * args.cpu_seconds + 120)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

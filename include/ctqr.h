@@ -27,6 +27,7 @@
 #ifndef CTQR_H
 #define CTQR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -100,6 +101,10 @@ typedef struct {
                    /* operand into a TF32 high part and a low remainder and   */
                    /* sums three tensor-core products (close to FP32          */
                    /* accuracy); 1 uses plain TF32 (about 3 decimal digits)   */
+  int outer_nb;    /* CT_PREC_TF32 only: columns per tensor-core trailing      */
+                   /* update, 256 (default, 0 = default) or 128; 256 updates  */
+                   /* with two 128-column halves' reflectors at once (half    */
+                   /* the passes over the trailing matrix)                    */
 } ct_qr_opts;
 
 /* Opaque factorization: reflectors V and R (in the factored matrix), tau, and
@@ -207,6 +212,41 @@ ct_status ct_build_system(const ct_geometry* geom, ct_dtype dtype, double lambda
 ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n,
                        int64_t lda, ct_prec prec, const ct_qr_opts* opts,
                        ct_factor** out, void* stream);
+
+/* Options of ct_qr_factor_host.  NULL selects the defaults. */
+typedef struct {
+  size_t device_bytes; /* HBM for the streamed block columns (three m x bw FP64 */
+                       /* buffers decide the block width bw); 0 = a quarter of */
+                       /* the free device memory                                */
+  int nb;              /* panel width 8..64 (0 = 64; narrowed to what the panel  */
+                       /* kernel's shared memory holds for m rows)               */
+  int no_overlap;      /* 1: copies and compute on the caller's stream one after */
+                       /* the other (the paper's B-OOC); 0: a copy stream loads  */
+                       /* the next block column while the current one is used   */
+                       /* (O-OOC, double buffered)                               */
+} ct_ooc_opts;
+
+/* Out-of-core Householder QR (Eq. (QR)) of an m x n FP64 matrix A held in
+ * HOST memory (column-major, lda >= m), for systems larger than HBM: the
+ * paper's out-of-core algorithm-by-blocks (Sec. II-B, II-C) with host memory
+ * in place of the disk and HBM as the block cache.  Left-looking by block
+ * columns of bw columns (bw from opts->device_bytes): each block column is
+ * copied to HBM, every earlier block column's reflectors are streamed in
+ * (double buffered on a copy stream) and applied (Apply_left_Qt_of_dense_QR),
+ * the block is factored in HBM (Compute_dense_QR per panel) and copied back.
+ * A is overwritten by the factor (R on and above the diagonal, reflectors
+ * below) and borrowed by it: it must stay alive and unchanged until
+ * ct_factor_destroy.  tau and the panel T blocks stay in HBM.  Page-locked
+ * host memory lets the copies overlap the compute (pageable memory works,
+ * with staged copies).  The factor works with ct_apply_qt, ct_trsm_solve and
+ * ct_reconstruct_batch (FP64 right-hand sides in HBM), each streaming the
+ * factor through HBM again (Q^T block columns in factorization order, R's
+ * block columns bottom-up); the FP32 entry points, ct_factor_copy,
+ * ct_factor_save and ct_apply_qt_noalloc return CT_ERR_UNSUPPORTED for it.
+ * Synchronous on `stream`.  CT_ERR_NOMEM when device_bytes holds no block
+ * column; rank and non-finite data are reported by ct_factor_status(). */
+ct_status ct_qr_factor_host(double* A, int64_t m, int64_t n, int64_t lda, const ct_ooc_opts* opts,
+                            ct_factor** out, void* stream);
 
 /* Shape and arithmetic of a factor (any pointer may be NULL). */
 ct_status ct_factor_info(const ct_factor* f, int64_t* m, int64_t* n, int* nb,

@@ -523,6 +523,10 @@ ct_status alloc_factor_matrix(ct_factor* f) {
 // columns, element type c_f64 ? FP64 : FP32).
 ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
                        double* work, size_t work_elems, int sms, cudaStream_t s, int max_splits) {
+  if (f->F_host) {  // a host-resident factor streams through HBM
+    if (!c_f64 || fp32_math || max_splits) return CT_ERR_UNSUPPORTED;
+    return ooc_apply_qt(f, (double*)C, ldc, k, s);
+  }
   const size_t es = elem_size(f->store), cs = c_f64 ? 8 : 4;
   // Two-level factors apply each 128-column outer block at once (its panels'
   // reflectors in the same order), except the last block, whose V^T V the
@@ -631,6 +635,8 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   const bool tc = prec == CT_PREC_TF32;
   const int passes = opts && opts->tf32_passes ? opts->tf32_passes : 3;
   if (tc && passes != 1 && passes != 3) { delete f; return CT_ERR_INVALID; }
+  const int outer = opts && opts->outer_nb ? opts->outer_nb : 256;
+  if (outer != 128 && outer != 256) { delete f; return CT_ERR_INVALID; }
   int want = (opts && opts->nb) ? opts->nb : (prec == CT_PREC_F64 ? 64 : 32);
   if (tc && (want > 32 || (want & (want - 1)))) { delete f; return CT_ERR_INVALID; }
   f->nb = panel_width_that_fits(m, want, di, store == CT_F64 ? 8 : 4, tc);
@@ -690,9 +696,11 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       if ((st = panel_step(j0, nbp, n)) != CT_OK) { free_factor(f); return st; }
     }
   } else {
-    // 128-column outer blocks: inner panels update only their own block, the
-    // rest of the matrix gets one tensor-core update per outer block.
-    const size_t owf = outer_work_floats(di.sms, m, n);
+    // Outer blocks of 256 columns (or 128): inner panels update only their
+    // own 128-column half, the first half's block reflector updates the
+    // second half, and the rest of the matrix gets one tensor-core update
+    // per outer block.
+    const size_t owf = outer_work_floats(di.sms, m, n, outer);
     Scratch owork;
     if ((st = owork.alloc(owf * sizeof(float), s)) != CT_OK) { free_factor(f); return st; }
     // Look-ahead (opt-in, CTQR_LOOKAHEAD=1): while the columns beyond the
@@ -729,7 +737,7 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       return CT_ERR_CUDA;
     }
     const char* la_env = getenv("CTQR_LOOKAHEAD");
-    const bool la_on = la_env && *la_env == '1' && di.sms > 2 * kReserve;
+    const bool la_on = outer == 128 && la_env && *la_env == '1' && di.sms > 2 * kReserve;
     if (la_on) {
       if (cudaStreamCreateWithFlags(&la.s2, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&la.ev_w, cudaEventDisableTiming) != cudaSuccess ||
@@ -739,7 +747,28 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
         return CT_ERR_CUDA;
       }
     }
-    for (int64_t J = 0; J < n; J += 128) {
+    auto half_panels = [&](int64_t J0, int nbo) -> ct_status {
+      for (int64_t j0 = J0; j0 < J0 + nbo; j0 += f->nb) {
+        const int nbp = (int)(J0 + nbo - j0 < f->nb ? J0 + nbo - j0 : f->nb);
+        ct_status r = panel_step(j0, nbp, J0 + nbo);
+        if (r != CT_OK) return r;
+      }
+      return CT_OK;
+    };
+    for (int64_t J = 0; outer == 256 && J < n; J += 256) {
+      const int nbo_a = (int)(n - J < 128 ? n - J : 128);
+      const int nbo_b = (int)(n - J - 128 <= 0 ? 0 : (n - J - 128 < 128 ? n - J - 128 : 128));
+      if ((st = half_panels(J, nbo_a)) != CT_OK) { free_factor(f); return st; }
+      if (nbo_b == 0) break;
+      if ((st = outer_block_update(f, J, nbo_a, (float*)owork.p, owf, di.sms, passes == 3, s, &la,
+                                   J + 128 + nbo_b)) != CT_OK ||
+          (st = half_panels(J + 128, nbo_b)) != CT_OK ||
+          (st = outer_block_update256(f, J, nbo_b, (float*)owork.p, owf, di.sms, passes == 3, s, &la)) != CT_OK) {
+        free_factor(f);
+        return st;
+      }
+    }
+    for (int64_t J = 0; outer == 128 && J < n; J += 128) {
       const int nbo = (int)(n - J < 128 ? n - J : 128);
       // this block's panels run beside the previous block's deferred update
       f->panel_cap = la.rest_pending ? kReserve : 0;
@@ -788,6 +817,12 @@ ct_status ct_factor_copy(const ct_factor* f, void* F_out, int64_t ld_out, double
                          void* stream) {
   if (!f) return CT_ERR_INVALID;
   cudaStream_t s = as_stream(stream);
+  if (F_out && f->F_host) {  // the host factor's matrix, copied up to HBM
+    if (ld_out < f->m) return CT_ERR_INVALID;
+    CT_CUDA_TRY(cudaMemcpy2DAsync(F_out, ld_out * sizeof(double), f->F, f->ld * sizeof(double),
+                                  f->m * sizeof(double), f->n, cudaMemcpyHostToDevice, s));
+    F_out = nullptr;
+  }
   if (F_out) {
     if (ld_out < f->m) return CT_ERR_INVALID;
     ct_status st = launch_copy_matrix(f->F, f->store, f->ld, F_out, f->store, ld_out, f->m, f->n, s);
@@ -962,7 +997,7 @@ ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec pr
   if (mixed && (st = sp.build(geom, k, sp_status, s)) != CT_OK) return st;
   CT_CUDA_TRY(cudaEventRecord(ev[1], s));
   ct_factor* f = nullptr;
-  ct_qr_opts qo = {0, 1, 0};  // factor in place
+  ct_qr_opts qo = {0, 1, 0, 0};  // factor in place
   if ((st = ct_qr_factor(Abuf.p, mixed ? CT_F32 : CT_F64, m, n, lda, prec, &qo, &f, stream)) != CT_OK) return st;
   CT_CUDA_TRY(cudaEventRecord(ev[2], s));
   ct_refine_opts ro = ropts ? *ropts : ct_refine_opts{0, 0.0, 0.0, 0};

@@ -173,6 +173,7 @@ uint64_t ct_geometry_hash(const ct_geometry* g, double lambda) {
 
 ct_status ct_factor_save(const ct_factor* f, const char* path, uint64_t tag, void* stream) {
   if (!f || !path || !*path) return CT_ERR_INVALID;
+  if (f->F_host) return CT_ERR_UNSUPPORTED;  // the caller already holds it in host memory
   cudaStream_t s = (cudaStream_t)stream;
   const bool blocks = f->Gblk && f->Tblk;
   const auto secs = sections(f, blocks);

@@ -576,10 +576,11 @@ ct_status launch_gemm_tn(const void* A, bool a_f64, int64_t lda, const double* R
 
 namespace {
 
-template <typename TC, typename Acc>
+// BN: columns of C per CTA (16 for a few right-hand sides; 64 for many, so
+// that V is read once per product instead of once per 16 columns).
+template <typename TC, typename Acc, int BN>
 ct_status run_outer(const ct_factor* f, int64_t J, TC* C, int64_t ldc, int64_t k, double* work, size_t work_elems,
                     int sms, cudaStream_t s) {
-  constexpr int BN = 16;
   const float* V = (const float*)f->F + J + J * f->ld;
   const int64_t mr = f->m - J;
   const int nbo = kOB;
@@ -629,11 +630,16 @@ ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f
                                 bool fp32_math, double* work, size_t work_elems, int sms, cudaStream_t s) {
   if (k <= 0) return CT_OK;
   if (!f->Gblk || f->store != CT_F32 || J + kOB > f->n) return CT_ERR_INVALID;
+  const bool wide = k >= 48;
   if (c_f64) {
-    if (fp32_math) return run_outer<double, float>(f, J, (double*)C, ldc, k, work, work_elems, sms, s);
-    return run_outer<double, double>(f, J, (double*)C, ldc, k, work, work_elems, sms, s);
+    if (fp32_math)
+      return wide ? run_outer<double, float, 64>(f, J, (double*)C, ldc, k, work, work_elems, sms, s)
+                  : run_outer<double, float, 16>(f, J, (double*)C, ldc, k, work, work_elems, sms, s);
+    return wide ? run_outer<double, double, 64>(f, J, (double*)C, ldc, k, work, work_elems, sms, s)
+                : run_outer<double, double, 16>(f, J, (double*)C, ldc, k, work, work_elems, sms, s);
   }
-  return run_outer<float, float>(f, J, (float*)C, ldc, k, work, work_elems, sms, s);
+  return wide ? run_outer<float, float, 64>(f, J, (float*)C, ldc, k, work, work_elems, sms, s)
+              : run_outer<float, float, 16>(f, J, (float*)C, ldc, k, work, work_elems, sms, s);
 }
 
 }  // namespace ctqr

@@ -157,6 +157,10 @@ struct ct_factor {
   float* Tblk = nullptr;        // the same blocks' compact-WY T = S^{-1} (128 x 128,
                                 // column-major, upper)
   int device = 0;
+  bool F_host = false;          // F is the caller's host matrix (ct_qr_factor_host):
+                                // every use streams it through HBM
+  int64_t ooc_bw = 0;           // host factors: block-column width of the streaming
+  bool ooc_overlap = true;      // host factors: copies on their own stream
 };
 
 namespace ctqr {
@@ -221,6 +225,10 @@ ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f
 ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
                        double* work, size_t work_elems, int sms, cudaStream_t s, int max_splits = 0);
 
+// ---- out-of-core use of a host-resident factor (ooc.cu) -------------------
+ct_status ooc_apply_qt(const ct_factor* f, double* B, int64_t ldb, int64_t k, cudaStream_t s);
+ct_status ooc_trsm(const ct_factor* f, double* B, int64_t ldb, int64_t k, cudaStream_t s);
+
 // ---- triangular solve (trsm.cu) -------------------------------------------
 ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k,
                       cudaStream_t s);
@@ -231,7 +239,7 @@ int panel_width_that_fits(int64_t mr, int want, const DeviceInfo& di, size_t mth
 // Tensor-core update of C = F[J:m, J+nbo:n] with the 128-column block
 // reflector of F[J:m, J:J+nbo] (outer_update.cu); work holds
 // outer_work_floats(...) floats.
-size_t outer_work_floats(int sms, int64_t m, int64_t n);
+size_t outer_work_floats(int sms, int64_t m, int64_t n, int width);
 // Look-ahead: the update of the columns after the next outer block runs on
 // s2 (on all but `reserve` SMs) while the next block's panels run on s.
 struct Lookahead {
@@ -246,7 +254,14 @@ struct Lookahead {
   int reserve = 0;
 };
 ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
-                             bool split3, cudaStream_t s, Lookahead* la = nullptr);
+                             bool split3, cudaStream_t s, Lookahead* la = nullptr, int64_t cend = 0);
+// The update of C = F[J:m, J+128+nbo_b:n] with the 256-column block reflector
+// of F[J:m, J:J+128+nbo_b] (two 128-column halves, the first already applied
+// to the second by outer_block_update(..., cend = J + 128 + nbo_b)); also
+// forms the second half's V^T V and T blocks.  work: outer_work_floats(...,
+// 256) floats.
+ct_status outer_block_update256(ct_factor* f, int64_t J, int nbo_b, float* work, size_t work_floats, int sms,
+                                bool split3, cudaStream_t s, Lookahead* la);
 // Whether a panel of mr rows and nbp columns fits on `ctas` CTAs (qr_panel.cu).
 bool panel_fits_ctas(int64_t mr, int nbp, int ctas, const DeviceInfo& di);
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,

@@ -55,6 +55,7 @@ using namespace ctqr;
 extern "C" ct_status ct_apply_qt_noalloc(const ct_factor* f, double* B, int64_t ldb, int64_t k, void* stream) {
   if (!f || k < 0) return CT_ERR_INVALID;
   if (k > kMaxK) return CT_ERR_INVALID;  // beyond the static workspace
+  if (f->F_host) return CT_ERR_UNSUPPORTED;  // streaming a host factor allocates buffers
   if (k == 0) return CT_OK;
   if (!B || ((uintptr_t)B & 15u) || ldb < f->m) return CT_ERR_INVALID;
   DeviceInfo di;

@@ -25,17 +25,18 @@ constexpr int kNB = 128;
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// Vc (column-major, ld ldvc) and Vr (row-major, row stride kNB) get the
-// explicit reflectors of the block: V(r, a) = F stored value for r > a, 1 on
-// the diagonal, 0 above; columns a >= nbo are zero.  With Vrl != NULL the
-// row-major copy is split for error-compensated TF32: Vr = hi part (exact in
-// TF32), Vrl = x - hi.
+// Vc (column-major, ld ldvc) and Vr (row-major, row stride W) get the
+// explicit reflectors of a block of W columns: V(r, a) = F stored value for
+// r > a, 1 on the diagonal, 0 above; columns a >= nbo are zero.  With
+// Vrl != NULL the row-major copy is split for error-compensated TF32:
+// Vr = hi part (exact in TF32), Vrl = x - hi.
+template <int W>
 __global__ void __launch_bounds__(256) k_extract_v(const float* __restrict__ F, int64_t ld, int64_t mr,
                                                    int nbo, float* __restrict__ Vc, int64_t ldvc,
                                                    float* __restrict__ Vr, float* __restrict__ Vrl) {
-  __shared__ float tile[32][kNB + 1];
+  __shared__ float tile[32][W + 1];
   const int64_t r0 = (int64_t)blockIdx.x * 32;
-  for (int e = threadIdx.x; e < 32 * kNB; e += 256) {
+  for (int e = threadIdx.x; e < 32 * W; e += 256) {
     const int rr = e % 32, a = e / 32;
     const int64_t r = r0 + rr;
     float v = 0.f;
@@ -44,17 +45,17 @@ __global__ void __launch_bounds__(256) k_extract_v(const float* __restrict__ F, 
     if (r < mr) Vc[r + (int64_t)a * ldvc] = v;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 32 * kNB; e += 256) {
-    const int a = e % kNB, rr = e / kNB;
+  for (int e = threadIdx.x; e < 32 * W; e += 256) {
+    const int a = e % W, rr = e / W;
     const int64_t r = r0 + rr;
     if (r < mr) {
       const float x = tile[rr][a];
       if (Vrl) {
         const float h = tf32_hi(x);
-        Vr[r * kNB + a] = h;
-        Vrl[r * kNB + a] = x - h;
+        Vr[r * W + a] = h;
+        Vrl[r * W + a] = x - h;
       } else {
-        Vr[r * kNB + a] = x;
+        Vr[r * W + a] = x;
       }
     }
   }
@@ -131,21 +132,36 @@ __global__ void __launch_bounds__(kTinvThreads) k_tinv(const float* __restrict__
   }
 }
 
-// W' = T^T sum_z W_z for 64 columns per CTA (the UT-transform solve written as
-// a product with the explicit T), split into TF32 high and low parts when Wlo
-// is given.  Thread (ty = tid % 16, tx = tid / 16) computes rows ty + 16 i
-// (i < 8) and columns tx * 4 + j (j < 4).
+// W' = T0^T W[r0 : r0+128] (+ T1^T W[r1 : r1+128] when T1 is given), W the
+// sum over the splits z of the partials W_z (rows at stride 1, columns at
+// stride ldw), for 64 columns per CTA: the UT-transform solve written as a
+// product with the explicit T (two terms for the second half of a 256-column
+// block, whose T is [[T_A, T_AB], [0, T_B]]).  Written to Wout (and its TF32
+// low part to Wlo when given) with column stride ldo.  Thread (ty = tid % 16,
+// tx = tid / 16) computes rows ty + 16 i (i < 8) and columns tx * 4 + j.
 constexpr int kTC = 64;
 constexpr size_t kApplyTtSmem = (size_t)(kNB * kNB + kNB * kTC) * sizeof(float);
 
-__global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, int wsplits, int64_t wstride,
-                                                  const float* __restrict__ T, int64_t nc, float* __restrict__ Wout,
-                                                  float* __restrict__ Wlo) {
+__global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp0, int wsplits, int64_t wstride,
+                                                  int64_t ldw, const float* __restrict__ T0, int r0,
+                                                  const float* __restrict__ T1, int r1, int64_t nc,
+                                                  float* __restrict__ Wout, float* __restrict__ Wlo, int64_t ldo) {
   extern __shared__ float sm[];
   float* Ts = sm;               // Ts[k * kNB + r] = T(k, r)
   float* Ws = Ts + kNB * kNB;   // Ws[k * kTC + c] = W(k, c0 + c)
   const int tid = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * kTC;
+  const int ty = tid % 16, tx = tid / 16;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 1
+  for (int term = 0; term < (T1 ? 2 : 1); ++term) {
+  const float* T = term == 0 ? T0 : T1;
+  const float* Wp = Wp0 + (term == 0 ? r0 : r1);
+  if (term > 0) __syncthreads();  // the previous term's tiles are consumed
   // T: 64 elements per thread, 16 loads in flight at a time
   for (int e0 = tid; e0 < kNB * kNB; e0 += 256 * 16) {
     float v[16];
@@ -171,8 +187,8 @@ __global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, 
       for (int u = 0; u < 16; ++u) {
         const int e = tid + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
         const bool ok = c0 + c < nc;
-        w0[u] = ok ? __ldcg(Wp + z * wstride + k + (c0 + c) * kNB) : 0.f;
-        w1[u] = ok ? __ldcg(Wp + (z + 1) * wstride + k + (c0 + c) * kNB) : 0.f;
+        w0[u] = ok ? __ldcg(Wp + z * wstride + k + (c0 + c) * ldw) : 0.f;
+        w1[u] = ok ? __ldcg(Wp + (z + 1) * wstride + k + (c0 + c) * ldw) : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < 16; ++u) v[u] = (v[u] + w0[u]) + w1[u];
@@ -181,7 +197,7 @@ __global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, 
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int e = tid + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
-        v[u] += c0 + c < nc ? __ldcg(Wp + z * wstride + k + (c0 + c) * kNB) : 0.f;
+        v[u] += c0 + c < nc ? __ldcg(Wp + z * wstride + k + (c0 + c) * ldw) : 0.f;
       }
     }
 #pragma unroll
@@ -191,12 +207,6 @@ __global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, 
     }
   }
   __syncthreads();
-  const int ty = tid % 16, tx = tid / 16;
-  float acc[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
   for (int k = 0; k < kNB; ++k) {
     float a[8], b[4];
@@ -209,13 +219,14 @@ __global__ void __launch_bounds__(256) k_apply_tt(const float* __restrict__ Wp, 
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
   }
+  }  // term
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int64_t c = c0 + tx * 4 + j;
     if (c >= nc) continue;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int64_t o = ty + 16 * i + c * kNB;
+      const int64_t o = ty + 16 * i + c * ldo;
       const float w = acc[i][j];
       if (Wlo) {
         const float h = tf32_hi(w);
@@ -401,20 +412,23 @@ __global__ void __launch_bounds__(256, 1) k_qt_outer(const float* __restrict__ F
 
 }  // namespace
 
-size_t outer_work_floats(int sms, int64_t m, int64_t n) {
+size_t outer_work_floats(int sms, int64_t m, int64_t n, int width) {
   const int64_t mp = (m + 3) / 4 * 4;
   const int64_t wcols = 8 * n > (int64_t)4 * sms * 128 ? 8 * n : (int64_t)4 * sms * 128;
-  return (size_t)mp * kNB          // Vc
-         + (size_t)2 * m * kNB     // Vr (high, low)
-         + (size_t)kNB * wcols     // W partials
-         + (size_t)2 * kNB * n     // W' (high, low)
-         + (size_t)(2 * sms + 2) * kNB * kNB;  // G partials, reduced G, T
+  const size_t w = width > kNB ? (size_t)width : (size_t)kNB;
+  return (size_t)mp * w            // Vc
+         + (size_t)2 * m * w       // Vr (high, low)
+         + (size_t)w * wcols       // W partials
+         + (size_t)2 * w * n       // W' (high, low)
+         + (size_t)(2 * sms + 2) * w * w  // G partials, reduced G, T
+         + (size_t)3 * kNB * kNB;  // 256-column blocks: reduced G_AB, T_AB, scratch
 }
 
-// Update C = F[J:m, J+nbo:n] with the block reflector of F[J:m, J:J+nbo].
+// Update C = F[J:m, J+nbo:cend] with the block reflector of F[J:m, J:J+nbo]
+// (cend <= 0: to the last column).
 ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
-                             bool split3, cudaStream_t s, Lookahead* la) {
-  const int64_t m = f->m, n = f->n, mr = m - J, nc = n - J - nbo;
+                             bool split3, cudaStream_t s, Lookahead* la, int64_t cend) {
+  const int64_t m = f->m, n = f->n, mr = m - J, nc = (cend > 0 ? cend : n) - J - nbo;
   // the previous block's deferred update must be done before C is read
   if (la && la->rest_pending) {
     CT_CUDA_TRY(cudaStreamWaitEvent(s, la->ev_rest, 0));
@@ -432,10 +446,11 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
   float* Wq = Wp + (size_t)kNB * wcols;
   float* Wql = Wq + (size_t)kNB * n;
   float* Gp = Wql + (size_t)kNB * n;
-  if (outer_work_floats(sms, m, n) > work_floats) return CT_ERR_INVALID;
+  if (outer_work_floats(sms, m, n, kNB) > work_floats) return CT_ERR_INVALID;
+  if (cend > 0 && la && la->defer) return CT_ERR_INVALID;  // look-ahead updates whole blocks
   {
     LaunchScope ls(K_COPY, s, 0.0, (double)mr * kNB * 12);
-    k_extract_v<<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, Vc, ldvc, Vr,
+    k_extract_v<kNB><<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, Vc, ldvc, Vr,
                                                            split3 ? Vrl : nullptr);
     CT_LAUNCH_CHECK();
   }
@@ -527,8 +542,8 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
   // W' = T^T W, one product per 64 columns.
   {
     LaunchScope ls(K_TW, s, 2.0 * kNB * kNB * nc, 4.0 * kNB * nc * (ws + 2));
-    k_apply_tt<<<(unsigned)((nc + kTC - 1) / kTC), 256, kApplyTtSmem, s>>>(Wp, (int)ws, (int64_t)kNB * nc, Tb, nc,
-                                                                           Wq, split3 ? Wql : nullptr);
+    k_apply_tt<<<(unsigned)((nc + kTC - 1) / kTC), 256, kApplyTtSmem, s>>>(
+        Wp, (int)ws, (int64_t)kNB * nc, kNB, Tb, 0, nullptr, 0, nc, Wq, split3 ? Wql : nullptr, kNB);
     CT_LAUNCH_CHECK();
   }
   // C -= V W'  (A = V stored row-major: kNB x mr column-major with ld kNB),
@@ -549,6 +564,199 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
     return CT_OK;
   }
   return tc_update_presplit(Vr, Vrl, kNB, Wq, Wql, kNB, mr, nc, kNB, C, ld, split3, sms, f->status, s);
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// 256-column outer blocks.  The block reflector of two consecutive 128-column
+// halves A = [J, J+128) and B = [J+128, J+256) is I - V T V^T with V = [V_A V_B]
+// and T = [[T_A, T_AB], [0, T_B]], T_AB = -T_A (V_A^T V_B) T_B (the compact-WY
+// merge of Schreiber and Van Loan).  Updating the trailing matrix once per 256
+// columns instead of once per 128 halves the passes over it, the dominant
+// HBM traffic of the factorization.
+// ---------------------------------------------------------------------------
+
+// out[i + r * ldo] = sum_z P[z * pstride + row0 + i + r * ldp] for i < rows,
+// r < cols (the split partials of a tcgen05 product summed in order); with
+// strict, entries with i >= r are zero; entries with i >= vr or r >= vc are
+// zero.
+__global__ void __launch_bounds__(256) k_reduce_block(const float* __restrict__ P, int splits, int64_t pstride,
+                                                      int64_t ldp, int row0, int rows, int cols, int vr, int vc,
+                                                      int strict, float* __restrict__ out, int64_t ldo) {
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int i = e % rows, r = e / rows;
+  float acc = 0.f;
+  if (i < vr && r < vc && (!strict || i < r)) {
+    const float* p = P + row0 + i + (int64_t)r * ldp;
+    int z = 0;
+    for (; z + 8 <= splits; z += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (z + u) * pstride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; z < splits; ++z) acc += __ldcg(p + z * pstride);
+  }
+  out[i + (int64_t)r * ldo] = acc;
+}
+
+// C = alpha A B for 128 x 128 column-major FP32 matrices (ld 128): the two
+// small products of T_AB.  One output per thread, 16 x 16 tiles per CTA.
+__global__ void __launch_bounds__(256) k_small_gemm128(const float* __restrict__ A, const float* __restrict__ B,
+                                                       float alpha, float* __restrict__ C) {
+  __shared__ float As[16][kNB + 1];
+  __shared__ float Bs[kNB][17];
+  const int ti = threadIdx.x % 16, tj = threadIdx.x / 16;
+  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
+  for (int e = threadIdx.x; e < 16 * kNB; e += 256) {
+    const int ii = e % 16, k = e / 16;
+    As[ii][k] = A[i0 + ii + k * kNB];
+  }
+  for (int e = threadIdx.x; e < 16 * kNB; e += 256) {
+    const int k = e % kNB, jj = e / kNB;
+    Bs[k][jj] = B[k + (j0 + jj) * kNB];
+  }
+  __syncthreads();
+  float acc = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < kNB; ++k) acc = fmaf(As[ti][k], Bs[k][tj], acc);
+  C[i0 + ti + (j0 + tj) * kNB] = alpha * acc;
+}
+
+}  // namespace
+
+ct_status outer_block_update256(ct_factor* f, int64_t J, int nbo_b, float* work, size_t work_floats, int sms,
+                                bool split3, cudaStream_t s, Lookahead* la) {
+  constexpr int kW = 2 * kNB;
+  const int nbo = kNB + nbo_b;
+  const int64_t m = f->m, n = f->n, mr = m - J, nc = n - J - nbo;
+  if (nbo_b < 1 || nbo_b > kNB) return CT_ERR_INVALID;
+  if (nc <= 0) return CT_OK;
+  if (!f->Gblk || !f->Tblk) return CT_ERR_INVALID;
+  if (outer_work_floats(sms, m, n, kW) > work_floats) return CT_ERR_INVALID;
+  float* F = (float*)f->F;
+  const int64_t ld = f->ld;
+  const int64_t ldvc = (m + 3) / 4 * 4;
+  const int64_t wcols = 8 * n > (int64_t)4 * sms * 128 ? 8 * n : (int64_t)4 * sms * 128;
+  float* Vc = work;
+  float* Vr = Vc + (size_t)ldvc * kW;
+  float* Vrl = Vr + (size_t)m * kW;
+  float* Wp = Vrl + (size_t)m * kW;
+  float* Wq = Wp + (size_t)kW * wcols;
+  float* Wql = Wq + (size_t)kW * n;
+  float* Gp = Wql + (size_t)kW * n;
+  float* Gab = Gp + (size_t)(2 * sms + 2) * kW * kW;  // reduced V_A^T V_B (128 x 128)
+  float* Tab = Gab + (size_t)kNB * kNB;              // T_AB
+  float* Ysc = Tab + (size_t)kNB * kNB;              // V_A^T V_B T_B
+  {
+    LaunchScope ls(K_COPY, s, 0.0, (double)mr * kW * 12);
+    k_extract_v<kW><<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, Vc, ldvc, Vr,
+                                                               split3 ? Vrl : nullptr);
+    CT_LAUNCH_CHECK();
+  }
+  ct_status st;
+  // [V_A^T V_B; V_B^T V_B] (256 x 128), split over rows.
+  int gs = (int)((mr + 2047) / 2048);
+  if (gs > 2 * sms) gs = 2 * sms;
+  if (gs < 1) gs = 1;
+  if ((st = tc_gemm_tn(Vc, ldvc, Vc + (size_t)kNB * ldvc, ldvc, kW, kNB, mr, Gp, kW, (int64_t)kW * kNB, 0, gs,
+                       split3, f->status, s)) != CT_OK)
+    return st;
+  {
+    int64_t gchunk = (mr + gs - 1) / gs;
+    gchunk = (gchunk + 31) / 32 * 32;
+    gs = (int)((mr + gchunk - 1) / gchunk);
+  }
+  const int64_t hb = J / kNB + 1;  // the second half's index among the 128-column blocks
+  float* Gb = f->Gblk + (size_t)hb * kNB * kNB;
+  float* Tb = f->Tblk + (size_t)hb * kNB * kNB;
+  const float* Ta = f->Tblk + (size_t)(hb - 1) * kNB * kNB;
+  {
+    LaunchScope ls(K_TW, s, 2.0 * kNB * kNB * gs, 8.0 * kNB * kNB * (gs + 1));
+    // G_B = strict upper part of V_B^T V_B; G_AB = V_A^T V_B (all of it)
+    k_reduce_block<<<kNB * kNB / 256, 256, 0, s>>>(Gp, gs, (int64_t)kW * kNB, kW, kNB, kNB, kNB, nbo_b, nbo_b, 1,
+                                                   Gb, kNB);
+    CT_LAUNCH_CHECK();
+    k_reduce_block<<<kNB * kNB / 256, 256, 0, s>>>(Gp, gs, (int64_t)kW * kNB, kW, 0, kNB, kNB, kNB, nbo_b, 0,
+                                                   Gab, kNB);
+    CT_LAUNCH_CHECK();
+  }
+  // T_B = S_B^{-1}, then T_AB = -T_A (G_AB T_B), on the side stream beside W = V^T C
+  const bool side = la && la->s3;
+  {
+    static bool attr = false;
+    if (!attr) {
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplyTtSmem));
+      attr = true;
+    }
+    cudaStream_t st_t = s;
+    if (side) {
+      CT_CUDA_TRY(cudaEventRecord(la->ev_g, s));
+      CT_CUDA_TRY(cudaStreamWaitEvent(la->s3, la->ev_g, 0));
+      st_t = la->s3;
+    }
+    LaunchScope ls(K_TINV, st_t, (double)kNB * kNB * kNB / 3.0 + 4.0 * kNB * kNB * kNB, 8.0 * kNB * kNB * 4);
+    k_tinv<<<1, kTinvThreads, kTinvSmem, st_t>>>(Gb, f->tau + J + kNB, nbo_b, Tb);
+    CT_LAUNCH_CHECK();
+    k_small_gemm128<<<dim3(kNB / 16, kNB / 16), 256, 0, st_t>>>(Gab, Tb, 1.f, Ysc);
+    CT_LAUNCH_CHECK();
+    k_small_gemm128<<<dim3(kNB / 16, kNB / 16), 256, 0, st_t>>>(Ta, Ysc, -1.f, Tab);
+    CT_LAUNCH_CHECK();
+    if (side) CT_CUDA_TRY(cudaEventRecord(la->ev_t, la->s3));
+  }
+  // W = V^T C (256 x nc), split over rows for full waves of CTAs (two row
+  // tiles of V per column tile; they read the same C slices, the second from L2)
+  float* C = F + J + (J + nbo) * ld;
+  const int64_t tiles = 2 * ((nc + 127) / 128);
+  int64_t wsmax = (mr + 1023) / 1024;
+  if (wsmax * nc > wcols) wsmax = wcols / nc;
+  if (wsmax < 1) wsmax = 1;
+  int64_t ws0 = (2 * sms + tiles - 1) / tiles;
+  if (ws0 > wsmax) ws0 = wsmax;
+  if (ws0 < 1) ws0 = 1;
+  int64_t ws = ws0;
+  {
+    double best = -1.0;
+    for (int64_t w = ws0; w <= 3 * ws0 && w <= wsmax; ++w) {
+      int64_t chunk = (mr + w - 1) / w;
+      chunk = (chunk + 31) / 32 * 32;
+      const int64_t made = (mr + chunk - 1) / chunk;
+      const int64_t ctas = made * tiles;
+      const double eff = (double)ctas / (double)(sms * ((ctas + sms - 1) / sms));
+      if (eff > best + 0.02) {
+        best = eff;
+        ws = w;
+      }
+    }
+  }
+  if ((st = tc_gemm_tn(Vc, ldvc, C, ld, kW, nc, mr, Wp, kW, (int64_t)kW * nc, 0, (int)ws, split3, f->status, s)) !=
+      CT_OK) {
+    if (side) cudaStreamWaitEvent(s, la->ev_t, 0);
+    return st;
+  }
+  {
+    int64_t chunk = (mr + ws - 1) / ws;
+    chunk = (chunk + 31) / 32 * 32;
+    ws = (mr + chunk - 1) / chunk;
+  }
+  if (side) CT_CUDA_TRY(cudaStreamWaitEvent(s, la->ev_t, 0));
+  // W' = T^T W: rows of the first half T_A^T W_A, of the second T_AB^T W_A + T_B^T W_B
+  {
+    LaunchScope ls(K_TW, s, 2.0 * kW * kNB * nc * 1.5, 4.0 * kW * nc * (ws + 2));
+    const unsigned g = (unsigned)((nc + kTC - 1) / kTC);
+    k_apply_tt<<<g, 256, kApplyTtSmem, s>>>(Wp, (int)ws, (int64_t)kW * nc, kW, Ta, 0, nullptr, 0, nc, Wq,
+                                            split3 ? Wql : nullptr, kW);
+    CT_LAUNCH_CHECK();
+    k_apply_tt<<<g, 256, kApplyTtSmem, s>>>(Wp, (int)ws, (int64_t)kW * nc, kW, Tab, 0, Tb, kNB, nc, Wq + kNB,
+                                            split3 ? Wql + kNB : nullptr, kW);
+    CT_LAUNCH_CHECK();
+  }
+  // C -= V W'  (K = 256)
+  return tc_update_presplit(Vr, Vrl, kW, Wq, Wql, kW, mr, nc, kW, C, ld, split3, sms, f->status, s);
 }
 
 // Q^T C for the outer blocks [0, nblk) in one cooperative launch; returns

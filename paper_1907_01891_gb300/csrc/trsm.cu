@@ -504,6 +504,7 @@ ct_status trsm_persist(const ct_factor* f, float* B, int64_t ldb, int64_t k, boo
 // column.
 ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
+  if (f->F_host) return b_f64 ? ooc_trsm(f, (double*)B, ldb, k, s) : CT_ERR_UNSUPPORTED;
   if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
   if (!b_f64 && k <= kPB && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, false, s);
   const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};
@@ -513,6 +514,7 @@ ct_status launch_trsm(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int6
 // B[0:n, 0:k] <- R^{-T} B[0:n, 0:k] (same arithmetic rules as launch_trsm).
 ct_status launch_trsm_t(const ct_factor* f, void* B, bool b_f64, int64_t ldb, int64_t k, cudaStream_t s) {
   if (k <= 0 || f->n <= 0) return CT_OK;
+  if (f->F_host) return CT_ERR_UNSUPPORTED;
   if (!b_f64 && f->store == CT_F64) return CT_ERR_UNSUPPORTED;
   if (!b_f64 && k <= kPB && persist_enabled()) return trsm_persist(f, (float*)B, ldb, k, true, s);
   const TrsmCtx c{f, B, b_f64, ldb, k, (size_t)(b_f64 ? 8 : 4), s};

@@ -44,7 +44,12 @@ class Geometry(ctypes.Structure):
 
 
 class QrOpts(ctypes.Structure):
-    _fields_ = [("nb", ctypes.c_int), ("in_place", ctypes.c_int), ("tf32_passes", ctypes.c_int)]
+    _fields_ = [("nb", ctypes.c_int), ("in_place", ctypes.c_int), ("tf32_passes", ctypes.c_int),
+                ("outer_nb", ctypes.c_int)]
+
+
+class OocOpts(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("nb", ctypes.c_int), ("no_overlap", ctypes.c_int)]
 
 
 class RefineOpts(ctypes.Structure):
@@ -105,6 +110,7 @@ SIGNATURES = {
     "ct_build_system": ([ctypes.POINTER(Geometry), _I, _D, _VP, _I64, _VP], _I),
     "ct_qr_factor": ([_VP, _I, _I64, _I64, _I64, _I, ctypes.POINTER(QrOpts),
                       ctypes.POINTER(_VP), _VP], _I),
+    "ct_qr_factor_host": ([_VP, _I64, _I64, _I64, ctypes.POINTER(OocOpts), ctypes.POINTER(_VP), _VP], _I),
     "ct_factor_info": ([_VP, _P64, _P64, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "ct_factor_data": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I), _P64, ctypes.POINTER(_VP)], _I),
     "ct_factor_status": ([_VP, _VP], _I),
@@ -292,13 +298,27 @@ class Factor:
 
 
 def qr_factor(A: torch.Tensor, prec: Prec = Prec.F64, nb: int = 0, in_place: bool = False,
-              tf32_passes: int = 0) -> Factor:
+              tf32_passes: int = 0, outer_nb: int = 0) -> Factor:
     m, n = A.shape
     h = ctypes.c_void_p()
-    opts = QrOpts(nb, 1 if in_place else 0, tf32_passes)
+    opts = QrOpts(nb, 1 if in_place else 0, tf32_passes, outer_nb)
     _check(load().ct_qr_factor(A.data_ptr(), _dt(A), m, n, _ld(A), int(prec), ctypes.byref(opts),
                                ctypes.byref(h), _stream()), "ct_qr_factor")
     return Factor(h.value, keep=A if in_place else None)
+
+
+def qr_factor_host(A: torch.Tensor, device_bytes: int = 0, nb: int = 0, overlap: bool = True) -> Factor:
+    """Out-of-core QR of a host FP64 column-major tensor A (overwritten by the
+    factor, which borrows it): block columns stream through HBM within
+    device_bytes."""
+    if A.is_cuda or A.dtype != torch.float64 or A.dim() != 2 or (A.stride(0) != 1 and A.shape[0] > 1):
+        raise ValueError("expected a host FP64 column-major matrix")
+    m, n = A.shape
+    h = ctypes.c_void_p()
+    opts = OocOpts(device_bytes, nb, 0 if overlap else 1)
+    _check(load().ct_qr_factor_host(A.data_ptr(), m, n, max(A.stride(1), m), ctypes.byref(opts), ctypes.byref(h),
+                                    _stream()), "ct_qr_factor_host")
+    return Factor(h.value, keep=A)
 
 
 def factor_save(f: Factor, path: str, tag: int = 0) -> None:

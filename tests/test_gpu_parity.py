@@ -487,3 +487,39 @@ def test_refinement_cap_reports_noconverge():
     X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A, max_iter=1, tol=1e-14, check=False)
     assert rep.status == ctqr.CT_ERR_NOCONVERGE
     assert np.all(np.isfinite(_np(X)))
+
+
+@pytest.mark.parametrize("shape", [(400, 200), (900, 300), (1500, 700), (3000, 1100)])
+def test_tf32_outer_blocks_of_256_and_128_agree_and_refine(shape):
+    """The trailing update with 256-column outer blocks (two 128-column
+    halves merged into one compact-WY reflector, T = [[T_A, T_AB], [0, T_B]])
+    against 128-column blocks: both R factors are FP32-quality copies of the
+    oracle's (1e-4 relative to max |R|), and both refine to the oracle's
+    solution (1e-10).  The shapes cover a second half narrower than 128, a
+    first half that is the last block, and several whole 256-column blocks."""
+    m, n = shape
+    A = I.random_matrix(m, n, seed=400 + n)
+    At = ctqr.to_colmajor(A)
+    Fo, _ = O.qr(A)
+    Ro = np.triu(Fo[:n])
+    b = A @ I.random_matrix(n, 2, seed=401)
+    Xo = O.lstsq(A, b)
+    for outer in (128, 256):
+        f = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32, outer_nb=outer)
+        assert f.status() == ctqr.CT_OK
+        F, _ = ctqr.factor_matrix(f)
+        R = np.triu(_np(F).astype(np.float64)[:n])
+        assert np.abs(R - Ro).max() <= 1e-4 * np.abs(Ro).max(), outer
+        X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=At)
+        assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, (outer, rep)
+        # Q^T by 128-column blocks uses the per-half V^T V and T the factor keeps
+        B = I.random_matrix(m, 3, seed=402)
+        Y = _np(ctqr.apply_qt(f, ctqr.to_colmajor(B)))
+        assert abs(np.linalg.norm(Y) - np.linalg.norm(B)) <= 1e-5 * np.linalg.norm(B)
+
+
+def test_qr_options_reject_bad_outer_width():
+    A = ctqr.to_colmajor(I.random_matrix(300, 200, seed=1), dtype=torch.float32)
+    with pytest.raises(ctqr.CtError) as e:
+        ctqr.qr_factor(A, prec=ctqr.Prec.TF32, outer_nb=192)
+    assert e.value.status == ctqr.CT_ERR_INVALID
