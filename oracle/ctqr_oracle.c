@@ -38,18 +38,39 @@
 /*    (n_bins-1) (0 when n_bins == 1); direction (-cos(beta+g), -sin(beta+g)).*/
 /* The image has nx*ny square pixels of side `pixel`, centred on the origin; */
 /* pixel j = iy*nx + ix covers [x0+ix*p, x0+(ix+1)*p) x [y0+iy*p, ...).      */
+/* angle_rule 1: the views of Eq. (angulos), read as the uniform angles      */
+/* shifted per quarter of the views by 0, +0.5, -0.25 and -0.5 degrees       */
+/* (the equation's +0.5, -0.75, -0.25 taken relative to the previous         */
+/* quarter); view i (1-based) is in quarter q when q*v/4 < i <= (q+1)*v/4.   */
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int beam, nx, ny;
   double pixel;
   int n_views, n_bins;
   double angle0, angle_span, src_iso, det_span;
+  int angle_rule;
 } og_geometry;
+
+/* Angle (radians) of view v (0-based). */
+double oracle_view_angle(const og_geometry* g, int v) {
+  double ang = g->angle0 + (double)v * g->angle_span / (double)g->n_views;
+  if (g->angle_rule == 1) {
+    const double pi = 3.14159265358979323846;
+    const double i = (double)(v + 1), q4 = (double)g->n_views / 4.0;
+    double shift_deg = 0.0;
+    if (i <= q4) shift_deg = 0.0;
+    else if (i <= 2.0 * q4) shift_deg = 0.5;
+    else if (i <= 3.0 * q4) shift_deg = 0.5 - 0.75;
+    else shift_deg = 0.5 - 0.75 - 0.25;
+    ang += shift_deg * pi / 180.0;
+  }
+  return ang;
+}
 
 void oracle_ray(const og_geometry* g, int64_t ray, double* px, double* py,
                 double* dx, double* dy) {
   int v = (int)(ray / g->n_bins), b = (int)(ray % g->n_bins);
-  double ang = g->angle0 + (double)v * g->angle_span / (double)g->n_views;
+  double ang = oracle_view_angle(g, v);
   double c = (double)b - 0.5 * (double)(g->n_bins - 1);
   if (g->beam == 0) {
     double s = c * (g->det_span / (double)g->n_bins);

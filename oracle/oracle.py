@@ -35,7 +35,9 @@ class Geometry(ctypes.Structure):
     beam 0: parallel beam, det_span = detector width (image units).
     beam 1: equiangular fan beam, det_span = total fan angle (radians),
             src_iso = source-to-isocentre distance.
-    Views: angle0 + v * angle_span / n_views.  Rays: ray = view*n_bins + bin.
+    Views: angle0 + v * angle_span / n_views, with angle_rule 1 shifted per
+    quarter of the views as Eq. (angulos) reads (0, +0.5, -0.25, -0.5
+    degrees).  Rays: ray = view*n_bins + bin.
     """
 
     _fields_ = [
@@ -43,6 +45,7 @@ class Geometry(ctypes.Structure):
         ("pixel", ctypes.c_double), ("n_views", ctypes.c_int), ("n_bins", ctypes.c_int),
         ("angle0", ctypes.c_double), ("angle_span", ctypes.c_double),
         ("src_iso", ctypes.c_double), ("det_span", ctypes.c_double),
+        ("angle_rule", ctypes.c_int),
     ]
 
     @property
@@ -75,6 +78,8 @@ def _load():
         D = ctypes.POINTER(ctypes.c_double)
         I64 = ctypes.c_int64
         lib.oracle_ray.argtypes = [ctypes.POINTER(Geometry), I64, D, D, D, D]
+        lib.oracle_view_angle.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int]
+        lib.oracle_view_angle.restype = ctypes.c_double
         lib.oracle_system_matrix.argtypes = [ctypes.POINTER(Geometry), D, I64]
         lib.oracle_qr.argtypes = [D, I64, I64, I64, D]
         lib.oracle_apply_qt.argtypes = [D, I64, I64, I64, D, D, I64, I64]
@@ -106,6 +111,11 @@ def ray(g: Geometry, i: int):
     out = [ctypes.c_double() for _ in range(4)]
     _load().oracle_ray(ctypes.byref(g), i, *[ctypes.byref(o) for o in out])
     return tuple(o.value for o in out)
+
+
+def view_angle(g: Geometry, v: int) -> float:
+    """Angle (radians) of view v (0-based)."""
+    return _load().oracle_view_angle(ctypes.byref(g), v)
 
 
 def system_matrix(g: Geometry) -> np.ndarray:

@@ -42,6 +42,7 @@ class ScanGeometry:
     angle_span: float
     src_iso: float
     det_span: float
+    angle_rule: int = 0   # 1: views shifted per quarter as Eq. (angulos)
 
     @property
     def m(self) -> int:
@@ -75,6 +76,21 @@ def fan_geometry(npix: int, n_views: int, n_bins: int, pixel: float = 1.0,
     gmax = math.asin((fov * math.sqrt(2.0) / 2.0) / r_src)
     return ScanGeometry(FAN, npix, npix, pixel, n_views, n_bins, 0.0, 2.0 * math.pi,
                         r_src, 2.0 * gmax)
+
+
+def scanner_geometry(npix: int, n_views: int, n_bins: int, angle_rule: int = 1) -> ScanGeometry:
+    """The paper's simulated fan-beam scanner (Table scanner): 360 degree
+    circular scan, source 75 cm from the isocentre (source-to-detector 150 cm),
+    30 degree fan, views at the quarter-shifted angles of Eq. (angulos).  The
+    image is the square inscribed in the fan's field of view (radius
+    75 sin 15 deg = 19.4 cm), so a 512 x 512 image has 0.536 mm pixels; lengths
+    are in pixel units.  The paper's own scan is scanner_geometry(512, 260,
+    1025): 266,500 rays x 262,144 pixels."""
+    r_src_cm, half_fan = 75.0, math.radians(15.0)
+    side_cm = 2.0 * r_src_cm * math.sin(half_fan) / math.sqrt(2.0)
+    pixel_cm = side_cm / npix
+    return ScanGeometry(FAN, npix, npix, 1.0, n_views, n_bins, 0.0, 2.0 * math.pi,
+                        r_src_cm / pixel_cm, 2.0 * half_fan, angle_rule)
 
 
 # The five workloads (sizes, seeds, noise) the tests and the benchmark use.

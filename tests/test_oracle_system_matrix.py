@@ -132,3 +132,45 @@ def test_config_geometries_have_no_empty_columns():
         A = O.system_matrix(O.Geometry(*g.as_tuple()))
         assert (A.sum(axis=0) > 0).all()
         assert A.min() >= 0.0
+
+
+ANGLES = os.path.join(os.path.dirname(__file__), "golden", "view_angles_eq_angulos.json")
+
+
+def test_view_angles_follow_the_quarter_shifts_of_eq_angulos():
+    """The oracle's angle rule 1 against hand-worked angles of Eq. (angulos)
+    (tests/golden/view_angles_eq_angulos.json states the reading)."""
+    spec = json.load(open(ANGLES))
+    for case in spec["cases"]:
+        g = I.scanner_geometry(16, case["views"], 21)
+        G = O.Geometry(*g.as_tuple())
+        got = [math.degrees(O.view_angle(G, i - 1)) for i in case["i"]]
+        assert np.allclose(got, case["degrees"], rtol=0, atol=1e-9), (case["views"], got)
+        # angle rule 0 is the uniform spacing
+        G0 = O.Geometry(*I.scanner_geometry(16, case["views"], 21, angle_rule=0).as_tuple())
+        assert np.allclose([math.degrees(O.view_angle(G0, i - 1)) for i in case["i"]],
+                           [360.0 * (i - 1) / case["views"] for i in case["i"]], atol=1e-9)
+
+
+def test_scanner_geometry_has_the_papers_scan_dimensions():
+    """Table scanner: 1025 detectors x 260 projections, 512 x 512 pixels, i.e.
+    a 266,500 x 262,144 system (Sec. III); the fan of 30 degrees from 75 cm
+    just covers the image's circumscribed circle."""
+    g = I.scanner_geometry(512, 260, 1025)
+    assert (g.m, g.n) == (266500, 262144)
+    assert math.isclose(math.degrees(g.det_span), 30.0)
+    half_diag = g.nx * g.pixel * math.sqrt(2.0) / 2.0
+    assert math.isclose(g.src_iso * math.sin(g.det_span / 2.0), half_diag, rel_tol=1e-12)
+
+
+def test_row_sums_are_chords_with_shifted_views():
+    """With the angle shifts every row sum is still the chord of its ray
+    through the whole image square."""
+    geom = I.scanner_geometry(12, 20, 17)
+    G = O.Geometry(*geom.as_tuple())
+    A = O.system_matrix(G)
+    R = _rays(G)
+    side = geom.nx * geom.pixel
+    chord = _chord_through_square(R[:, 0] * R[:, 3] - R[:, 1] * R[:, 2], R[:, 2], R[:, 3], side)
+    ok = np.minimum(np.abs(R[:, 2]), np.abs(R[:, 3])) > 1e-6
+    assert np.abs(A.sum(axis=1) - chord)[ok].max() <= 1e-10
