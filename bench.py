@@ -179,7 +179,7 @@ class OracleSampler:
         g = cfg["geom"]
         self.views = max(1, min(g.n_views, int(g.n_views * min(1.0, 2048.0 / max(g.m, 1)))))
         self.gs = O.Geometry(g.beam, g.nx, g.ny, g.pixel, self.views, g.n_bins, g.angle0,
-                             g.angle_span * self.views / g.n_views, g.src_iso, g.det_span)
+                             g.angle_span * self.views / g.n_views, g.src_iso, g.det_span, g.angle_rule)
         self.cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         self.rng = np.random.default_rng(0)
         # calibrate ns: grow until one QR + solve sample takes ~target_s / 2

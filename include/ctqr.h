@@ -88,6 +88,12 @@ typedef struct {
   double angle_span; /* views are spread over [angle0, angle0 + angle_span)     */
   double src_iso;    /* fan: source-to-isocentre distance                       */
   double det_span;   /* parallel: detector width; fan: total fan angle (rad)    */
+  int angle_rule;    /* 0: a_v as above; 1: a_v shifted per quarter of the      */
+                     /* views as Eq. (angulos) reads: by 0, +0.5, -0.25, -0.5   */
+                     /* degrees for views i = v + 1 with q n_views/4 < i <=     */
+                     /* (q+1) n_views/4, q = 0..3 (the printed equation is      */
+                     /* garbled; its +0.5, -0.75, -0.25 taken relative to the  */
+                     /* previous quarter)                                       */
 } ct_geometry;
 
 /* Options of ct_qr_factor.  NULL selects the defaults. */

@@ -25,6 +25,7 @@ bool geometry_ok(const ct_geometry* g) {
   if (!(g->pixel > 0.0) || !isfinite(g->pixel)) return false;
   if (!isfinite(g->angle0) || !isfinite(g->angle_span) || !isfinite(g->det_span)) return false;
   if (g->beam == 1 && !(g->src_iso > 0.0 && isfinite(g->src_iso))) return false;
+  if (g->angle_rule != 0 && g->angle_rule != 1) return false;
   const double half = 0.5 * sqrt((double)g->nx * g->nx + (double)g->ny * g->ny) * g->pixel;
   if (g->beam == 1 && g->src_iso <= half) return false;  // source inside the image
   return true;

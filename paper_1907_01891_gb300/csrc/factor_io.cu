@@ -167,6 +167,7 @@ uint64_t ct_geometry_hash(const ct_geometry* g, double lambda) {
   mix_d(g->angle_span);
   mix_d(g->src_iso);
   mix_d(g->det_span);
+  mix_i(g->angle_rule);
   mix_d(lambda);
   return h == 0 ? 1 : h;
 }

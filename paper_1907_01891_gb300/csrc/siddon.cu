@@ -16,14 +16,27 @@ namespace ctqr {
 namespace {
 
 struct Geo {
-  int beam, nx, ny, n_views, n_bins;
+  int beam, nx, ny, n_views, n_bins, angle_rule;
   double pixel, angle0, angle_span, src_iso, det_span, x0, y0;
 };
+
+// Angle of view v; angle_rule 1 adds the per-quarter shifts of Eq. (angulos)
+// (0, +0.5, -0.25, -0.5 degrees; view i = v + 1 is in quarter q when
+// q * n_views / 4 < i <= (q + 1) * n_views / 4).
+__device__ __forceinline__ double view_angle(const Geo& g, int v) {
+  double ang = g.angle0 + (double)v * g.angle_span / (double)g.n_views;
+  if (g.angle_rule == 1) {
+    const double i = (double)(v + 1), q4 = (double)g.n_views / 4.0;
+    const double shift = i <= q4 ? 0.0 : (i <= 2.0 * q4 ? 0.5 : (i <= 3.0 * q4 ? -0.25 : -0.5));
+    ang += shift * 3.14159265358979323846 / 180.0;
+  }
+  return ang;
+}
 
 __device__ __forceinline__ void ray_of(const Geo& g, int64_t ray, double& px, double& py,
                                        double& dx, double& dy) {
   const int v = (int)(ray / g.n_bins), b = (int)(ray % g.n_bins);
-  const double ang = g.angle0 + (double)v * g.angle_span / (double)g.n_views;
+  const double ang = view_angle(g, v);
   const double c = (double)b - 0.5 * (double)(g.n_bins - 1);
   if (g.beam == 0) {
     const double s = c * (g.det_span / (double)g.n_bins);
@@ -156,7 +169,7 @@ Geo make_geo(const ct_geometry* gg) {
   Geo g;
   g.beam = gg->beam; g.nx = gg->nx; g.ny = gg->ny; g.n_views = gg->n_views; g.n_bins = gg->n_bins;
   g.pixel = gg->pixel; g.angle0 = gg->angle0; g.angle_span = gg->angle_span;
-  g.src_iso = gg->src_iso; g.det_span = gg->det_span;
+  g.src_iso = gg->src_iso; g.det_span = gg->det_span; g.angle_rule = gg->angle_rule;
   g.x0 = -0.5 * (double)g.nx * g.pixel;
   g.y0 = -0.5 * (double)g.ny * g.pixel;
   return g;

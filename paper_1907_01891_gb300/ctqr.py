@@ -39,7 +39,7 @@ class Geometry(ctypes.Structure):
         ("beam", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("pixel", ctypes.c_double), ("n_views", ctypes.c_int), ("n_bins", ctypes.c_int),
         ("angle0", ctypes.c_double), ("angle_span", ctypes.c_double),
-        ("src_iso", ctypes.c_double), ("det_span", ctypes.c_double),
+        ("src_iso", ctypes.c_double), ("det_span", ctypes.c_double), ("angle_rule", ctypes.c_int),
     ]
 
 
@@ -231,7 +231,7 @@ def to_colmajor(x, dtype=None, device="cuda") -> torch.Tensor:
 def geometry(g) -> Geometry:
     """Geometry from an ``inputs.ScanGeometry`` (or anything with the fields)."""
     return Geometry(g.beam, g.nx, g.ny, g.pixel, g.n_views, g.n_bins, g.angle0, g.angle_span,
-                    g.src_iso, g.det_span)
+                    g.src_iso, g.det_span, getattr(g, "angle_rule", 0))
 
 
 def version() -> str:

@@ -32,8 +32,9 @@ def _og(g):
 # ---------------------------------------------------------------- system matrix
 @pytest.mark.parametrize("geom", [I.CONFIG1["geom"], I.fan_geometry(24, 30, 37),
                                   I.parallel_geometry(20, 13, 29, pixel=0.37),
-                                  I.ScanGeometry(0, 8, 8, 1.0, 2, 9, 0.0, np.pi, 0.0, 8.1)],
-                         ids=["config1", "fan24", "par20_pix037", "axis_aligned"])
+                                  I.ScanGeometry(0, 8, 8, 1.0, 2, 9, 0.0, np.pi, 0.0, 8.1),
+                                  I.scanner_geometry(20, 36, 31)],
+                         ids=["config1", "fan24", "par20_pix037", "axis_aligned", "scanner20_eq_angulos"])
 def test_system_matrix_matches_oracle(geom):
     A = ctqr.build_system(geom, torch.float64)
     ref = O.system_matrix(_og(geom))
