@@ -125,6 +125,122 @@ void oracle_system_matrix(const og_geometry* g, double* A, int64_t lda) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Joseph's projector (the paper simulates its sinograms with it, Sec. III;  */
+/* Joseph, "An improved algorithm for reprojecting rays through pixel        */
+/* images", 1982).  For a ray with unit direction (dx, dy): when             */
+/* |dy| >= |dx| it crosses every pixel row; at row iy's centre line          */
+/* y_c = y0 + (iy + 1/2) p it is at x(y_c), which lies between the centres    */
+/* of columns i0 and i0 + 1 with u = (x - x0)/p - 1/2, i0 = floor(u),         */
+/* f = u - i0; the row contributes p/|dy| * ((1 - f) X[iy, i0] + f X[iy, i0+1]), */
+/* a pixel outside the image counting as zero.  Otherwise the same with the  */
+/* roles of rows and columns exchanged (step p/|dx|).                        */
+/* B[i, c] = sum over rows (or columns) for image c.                         */
+/* ------------------------------------------------------------------------ */
+void oracle_joseph(const og_geometry* g, const double* X, int64_t ldx, int64_t k, double* B, int64_t ldb) {
+  int64_t m = (int64_t)g->n_views * g->n_bins;
+  double p = g->pixel;
+  double x0 = -0.5 * (double)g->nx * p;
+  double y0 = -0.5 * (double)g->ny * p;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < m; i++) {
+    double px, py, dx, dy;
+    oracle_ray(g, i, &px, &py, &dx, &dy);
+    int by_rows = fabs(dy) >= fabs(dx);
+    int lines = by_rows ? g->ny : g->nx;
+    int cells = by_rows ? g->nx : g->ny;
+    double step = by_rows ? p / fabs(dy) : p / fabs(dx);
+    for (int64_t c = 0; c < k; c++) {
+      double acc = 0.0;
+      for (int q = 0; q < lines; q++) {
+        double u;
+        if (by_rows) {
+          double yc = y0 + ((double)q + 0.5) * p;
+          double t = (yc - py) / dy;
+          double x = px + t * dx;
+          u = (x - x0) / p - 0.5;
+        } else {
+          double xc = x0 + ((double)q + 0.5) * p;
+          double t = (xc - px) / dx;
+          double y = py + t * dy;
+          u = (y - y0) / p - 0.5;
+        }
+        double fl = floor(u);
+        double f = u - fl;
+        int64_t i0 = (int64_t)fl;
+        double v = 0.0;
+        if (i0 >= 0 && i0 < cells) {
+          int64_t j = by_rows ? (int64_t)q * g->nx + i0 : i0 * g->nx + q;
+          v += (1.0 - f) * X[IDX(j, c, ldx)];
+        }
+        if (i0 + 1 >= 0 && i0 + 1 < cells) {
+          int64_t j = by_rows ? (int64_t)q * g->nx + (i0 + 1) : (i0 + 1) * g->nx + q;
+          v += f * X[IDX(j, c, ldx)];
+        }
+        acc += v;
+      }
+      B[IDX(i, c, ldb)] = step * acc;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Image quality of Sec. II-D: MSE (Eq. MSE), PSNR with the reference's       */
+/* maximum (Eq. psnr) and SSIM (Eq. ssim).  The paper leaves SSIM's window   */
+/* and constants open; the reading (Wang et al. 2004): an 11 x 11 Gaussian   */
+/* window of sigma 1.5 (weights normalised to sum 1), c1 = (0.01 L)^2,       */
+/* c2 = (0.03 L)^2 with L = max - min of the reference, SSIM evaluated at    */
+/* every pixel whose whole window lies in the image and averaged.            */
+/* x, ref: one image each (pixel iy*nx + ix).  out[0] = MSE, out[1] = PSNR   */
+/* (dB), out[2] = SSIM.                                                      */
+/* ------------------------------------------------------------------------ */
+void oracle_quality(const double* x, const double* ref, int nx, int ny, double* out) {
+  int64_t n = (int64_t)nx * ny;
+  double mse = 0.0, mx = -INFINITY, mn = INFINITY;
+  for (int64_t j = 0; j < n; j++) {
+    double d = x[j] - ref[j];
+    mse += d * d;
+    if (ref[j] > mx) mx = ref[j];
+    if (ref[j] < mn) mn = ref[j];
+  }
+  mse /= (double)n;
+  out[0] = mse;
+  out[1] = 10.0 * log10(mx * mx / mse);
+  const int R = 5;
+  double w[11 * 11], ws = 0.0;
+  for (int a = -R; a <= R; a++)
+    for (int b = -R; b <= R; b++) {
+      double e = exp(-(double)(a * a + b * b) / (2.0 * 1.5 * 1.5));
+      w[(a + R) * 11 + (b + R)] = e;
+      ws += e;
+    }
+  for (int q = 0; q < 121; q++) w[q] /= ws;
+  double L = mx - mn;
+  double c1 = (0.01 * L) * (0.01 * L), c2 = (0.03 * L) * (0.03 * L);
+  double total = 0.0;
+  int64_t count = 0;
+  for (int iy = R; iy < ny - R; iy++) {
+    for (int ix = R; ix < nx - R; ix++) {
+      double mux = 0.0, muy = 0.0, sxx = 0.0, syy = 0.0, sxy = 0.0;
+      for (int a = -R; a <= R; a++)
+        for (int b = -R; b <= R; b++) {
+          double wt = w[(a + R) * 11 + (b + R)];
+          int64_t j = (int64_t)(iy + a) * nx + (ix + b);
+          mux += wt * x[j];
+          muy += wt * ref[j];
+          sxx += wt * x[j] * x[j];
+          syy += wt * ref[j] * ref[j];
+          sxy += wt * x[j] * ref[j];
+        }
+      double vx = sxx - mux * mux, vy = syy - muy * muy, cxy = sxy - mux * muy;
+      total += ((2.0 * mux * muy + c1) * (2.0 * cxy + c2)) /
+               ((mux * mux + muy * muy + c1) * (vx + vy + c2));
+      count++;
+    }
+  }
+  out[2] = count > 0 ? total / (double)count : NAN;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Householder QR, unblocked (column by column).  For column j:              */
 /*   alpha = A[j,j], sigma = sum_{i>j} A[i,j]^2.                             */
 /*   sigma == 0: tau_j = 0, nothing changes (H_j = I).                       */

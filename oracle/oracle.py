@@ -79,6 +79,8 @@ def _load():
         I64 = ctypes.c_int64
         lib.oracle_ray.argtypes = [ctypes.POINTER(Geometry), I64, D, D, D, D]
         lib.oracle_view_angle.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int]
+        lib.oracle_joseph.argtypes = [ctypes.POINTER(Geometry), D, I64, I64, D, I64]
+        lib.oracle_quality.argtypes = [D, D, ctypes.c_int, ctypes.c_int, D]
         lib.oracle_view_angle.restype = ctypes.c_double
         lib.oracle_system_matrix.argtypes = [ctypes.POINTER(Geometry), D, I64]
         lib.oracle_qr.argtypes = [D, I64, I64, I64, D]
@@ -164,6 +166,25 @@ def backsolve(F, Y) -> np.ndarray:
         raise np.linalg.LinAlgError("R is numerically rank deficient")
     X = Yo[:n]
     return X if np.ndim(Y) == 2 else X[:, 0]
+
+
+def joseph_project(g: Geometry, X) -> np.ndarray:
+    """Sinograms of the images X (n x k, or a length-n vector) by Joseph's
+    projector: B (m x k)."""
+    Xo = _f64f(X if np.ndim(X) == 2 else np.reshape(X, (-1, 1)))
+    k = Xo.shape[1]
+    B = np.zeros((g.m, k), dtype=np.float64, order="F")
+    _load().oracle_joseph(ctypes.byref(g), _p(Xo), Xo.shape[0], k, _p(B), g.m)
+    return B if np.ndim(X) == 2 else B[:, 0]
+
+
+def quality(x, ref, nx: int, ny: int) -> tuple[float, float, float]:
+    """(MSE, PSNR in dB, SSIM) of image x against the reference image."""
+    xo = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    ro = np.ascontiguousarray(ref, dtype=np.float64).reshape(-1)
+    out = np.zeros(3)
+    _load().oracle_quality(_p(xo), _p(ro), nx, ny, _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def lstsq(A, B) -> np.ndarray:
