@@ -173,13 +173,21 @@ typedef struct {
 typedef struct {
   int tile;       /* tile size 32 or 64; 0 = measured choice per size class,   */
                   /* cached in $CTQR_TUNE_CACHE (else ~/.cache/ctqr_tune.json) */
+  int prec;       /* CT_PREC_F64 (0, default): the persistent tile-task launch */
+                  /* below; CT_PREC_TF32: each system factored by the tensor-  */
+                  /* core path of ct_qr_factor (widths tuned per size class)   */
+                  /* and refined to the FP64 least-squares solution by         */
+                  /* ct_reconstruct_batch against its FP64 A, which is then    */
+                  /* left unchanged                                            */
 } ct_batch_opts;
 
 /* Optional report of ct_qr_solve_batched. */
 typedef struct {
-  int tile;       /* tile size used                                              */
-  double ms;      /* device time of the persistent launch                        */
-  int tasks;      /* tile tasks executed                                         */
+  int tile;       /* tile size used (0 for CT_PREC_TF32)                         */
+  double ms;      /* device time of the persistent launch (CT_PREC_TF32: wall    */
+                  /* time of all factorizations and refinements)                 */
+  int tasks;      /* tile tasks executed (CT_PREC_TF32: 0)                       */
+  int iterations; /* CT_PREC_TF32: most refinement steps any system took         */
 } ct_batch_report;
 
 /* Where the caller's B and X live for ct_reconstruct_scan. */
@@ -205,6 +213,31 @@ ct_status ct_system_size(const ct_geometry* geom, double lambda, int64_t* m,
  * Lengths are computed in FP64; CT_F32 stores them rounded. */
 ct_status ct_build_system(const ct_geometry* geom, ct_dtype dtype, double lambda,
                           void* A, int64_t lda, void* stream);
+
+/* Sinograms of k images by Joseph's projector, the paper's sinogram
+ * simulator (Sec. III; Joseph 1982), for data that do not come from the
+ * system matrix itself (reconstructing them with the Siddon A of
+ * ct_build_system carries the model mismatch of a real scan).  For the ray of
+ * unit direction (dx, dy) with |dy| >= |dx| (else the same with rows and
+ * columns exchanged): at every pixel row's centre line the ray lies between
+ * two pixel centres of that row; the row adds p/|dy| times their linear
+ * interpolation (a pixel outside the image counts as zero).  X: n x k device
+ * FP64 images (pixel iy*nx + ix, ldx >= n); B: m x k device FP64 (ldb >= m,
+ * rays only: no lambda rows).  Asynchronous on `stream`. */
+ct_status ct_project_joseph(const ct_geometry* geom, const double* X, int64_t ldx, int64_t k, double* B,
+                            int64_t ldb, void* stream);
+
+/* Image quality of k reconstructed slices X against reference slices R
+ * (Sec. II-D), both n x k device FP64 (n = nx*ny, pixel iy*nx + ix):
+ * out[3c] = MSE (Eq. MSE), out[3c+1] = PSNR in dB with the reference slice's
+ * maximum as peak (Eq. psnr), out[3c+2] = SSIM (Eq. ssim), out a device array
+ * of 3k doubles.  SSIM's window and constants are not given in the paper:
+ * 11 x 11 Gaussian window of sigma 1.5 normalised to 1, c1 = (0.01 L)^2,
+ * c2 = (0.03 L)^2, L = the reference slice's max - min, averaged over the
+ * pixels whose window lies inside the image (NaN when none does).
+ * Asynchronous on `stream`. */
+ct_status ct_image_quality(const double* X, int64_t ldx, const double* R, int64_t ldr, int nx, int ny, int64_t k,
+                           double* out, void* stream);
 
 /* Householder QR A = QR (Eq. (QR)) of the m x n (m >= n) matrix A, blocked in
  * panels of nb columns: per panel a panel factorization (reflector generation,
@@ -304,7 +337,9 @@ ct_status ct_apply_qt_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k,
  * it calls no allocation routine.  Limit: k <= 64 right-hand sides per call;
  * a larger k returns CT_ERR_INVALID (split B into column blocks).  The first
  * call on each device looks up the array's device address and caches it;
- * make that first call before any stream capture.  All calls share the one
+ * make that first call before any stream capture.  The cached address
+ * belongs to the device's primary context: after cudaDeviceReset it is stale,
+ * so do not use this entry point on a device that was reset.  All calls share the one
  * array and it keeps the last call's contents (nothing in it needs clearing:
  * each call writes what it reads), so calls that overlap on the GPU -- on
  * different streams, threads or factors -- race and corrupt each other's

@@ -636,9 +636,14 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   const bool tc = prec == CT_PREC_TF32;
   const int passes = opts && opts->tf32_passes ? opts->tf32_passes : 3;
   if (tc && passes != 1 && passes != 3) { delete f; return CT_ERR_INVALID; }
-  const int outer = opts && opts->outer_nb ? opts->outer_nb : 256;
+  int outer = opts && opts->outer_nb ? opts->outer_nb : 256;
   if (outer != 128 && outer != 256) { delete f; return CT_ERR_INVALID; }
+  if (prec == CT_PREC_F64 && outer == 256 && opts && opts->outer_nb) { delete f; return CT_ERR_INVALID; }
   int want = (opts && opts->nb) ? opts->nb : (prec == CT_PREC_F64 ? 64 : 32);
+  // TF32 factors whose widths the caller leaves open take the tuned pair
+  if (tc && !(opts && opts->nb) && !(opts && opts->outer_nb)) {
+    if ((st = tuned_factor_widths(m, n, passes, s, &want, &outer)) != CT_OK) { delete f; return st; }
+  }
   if (tc && (want > 32 || (want & (want - 1)))) { delete f; return CT_ERR_INVALID; }
   f->nb = panel_width_that_fits(m, want, di, store == CT_F64 ? 8 : 4, tc);
   const size_t es = elem_size(store);
@@ -691,7 +696,25 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
     }
     return apply_block_reflector(a, (double*)work.p, work_elems, di.sms, s);
   };
-  if (!tc) {
+  // FP64 factors whose panels had to be narrowed for a tall matrix (or on
+  // request, outer_nb = 128) update the trailing matrix once per outer block
+  // of 128 // nb panels instead of once per panel
+  const int outer_req = opts ? opts->outer_nb : 0;
+  const bool two_level64 = store == CT_F64 && n > 128 && (outer_req == 128 || (outer_req == 0 && f->nb < 64));
+  if (!tc && two_level64) {
+    const int ow = (128 / f->nb) * f->nb;
+    const size_t w64 = fp64_outer_work_elems(di.sms, n);
+    Scratch ow64;
+    if ((st = ow64.alloc(w64 * sizeof(double), s)) != CT_OK) { free_factor(f); return st; }
+    for (int64_t J = 0; J < n; J += ow) {
+      const int nbo = (int)(n - J < ow ? n - J : ow);
+      for (int64_t j0 = J; j0 < J + nbo; j0 += f->nb) {
+        const int nbp = (int)(J + nbo - j0 < f->nb ? J + nbo - j0 : f->nb);
+        if ((st = panel_step(j0, nbp, J + nbo)) != CT_OK) { free_factor(f); return st; }
+      }
+      if ((st = fp64_outer_update(f, J, nbo, (double*)ow64.p, w64, di.sms, s)) != CT_OK) { free_factor(f); return st; }
+    }
+  } else if (!tc) {
     for (int64_t j0 = 0; j0 < n; j0 += f->nb) {
       const int nbp = (int)(n - j0 < f->nb ? n - j0 : f->nb);
       if ((st = panel_step(j0, nbp, n)) != CT_OK) { free_factor(f); return st; }
@@ -1085,6 +1108,46 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
   DeviceInfo di;
   ct_status st = device_info(&di);
   if (st != CT_OK) return st;
+  const int bprec = opts ? opts->prec : CT_PREC_F64;
+  if (bprec != CT_PREC_F64 && bprec != CT_PREC_TF32) return CT_ERR_INVALID;
+  if (bprec == CT_PREC_TF32) {
+    // one system after another through the tensor-core factorization and
+    // the FP64 refinement against its own (unchanged) FP64 A
+    const auto t0 = std::chrono::steady_clock::now();
+    int worst_it = 0;
+    ct_status agg = CT_OK;
+    for (int i = 0; i < count; ++i) {
+      const ct_batch_system& q = systems[i];
+      ct_factor* f = nullptr;
+      if ((st = ct_qr_factor(q.A, CT_F64, q.m, q.n, q.lda, CT_PREC_TF32, nullptr, &f, stream)) != CT_OK) return st;
+      if (q.k > 0) {
+        Scratch xs;
+        if ((st = xs.alloc((size_t)q.n * q.k * sizeof(double), s)) != CT_OK) {
+          ct_factor_destroy(f);
+          return st;
+        }
+        ct_report rep;
+        ct_status rs = ct_reconstruct_batch(f, q.A, CT_F64, q.lda, q.B, q.ldb, (double*)xs.p, q.n, q.k, nullptr,
+                                            &rep, stream);
+        if (rep.iterations > worst_it) worst_it = rep.iterations;
+        if (rs == CT_OK)
+          rs = launch_copy_matrix(xs.p, CT_F64, q.n, q.B, CT_F64, q.ldb, q.n, q.k, s);
+        if (rs != CT_OK && agg == CT_OK) agg = rs;
+      } else {
+        const ct_status fs = ct_factor_status(f, stream);
+        if (fs != CT_OK && agg == CT_OK) agg = fs;
+      }
+      ct_factor_destroy(f);
+    }
+    CT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (report) {
+      report->tile = 0;
+      report->tasks = 0;
+      report->iterations = worst_it;
+      report->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return agg;
+  }
   int tile = opts ? opts->tile : 0;
   if (tile != 0 && tile != 32 && tile != 64) return CT_ERR_INVALID;
   // Large batches take the larger tile without measuring: the task list of

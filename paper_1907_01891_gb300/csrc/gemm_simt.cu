@@ -36,7 +36,7 @@ __device__ __forceinline__ Acc v_at(const TV* V, int64_t ldv, int64_t r, int a, 
 // P_s = V^T C over the row chunk of split s (blockIdx.y): BM rows of V^T
 // (reflectors, padded) x BN columns of C per CTA, RM = BM / 16 rows and
 // TN = BN / 16 columns per thread.
-template <typename TV, typename TC, typename Acc, int BN, int BM = kBM>
+template <typename TV, typename TC, typename Acc, int BN, int BM = kBM, bool CMASK = false>
 __global__ void __launch_bounds__(kGT) k_vtc(const TV* __restrict__ V, int64_t ldv, int nbp,
                                               const TC* __restrict__ C, int64_t ldc, int64_t mr,
                                               int64_t nc, int64_t chunk, double* __restrict__ part) {
@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(kGT) k_vtc(const TV* __restrict__ V, int64_t l
       if (e < BN * kBK) {
         const int c = e / kBK, rr = e % kBK;
         const int64_t r = r0 + rr, cg = c0 + c;
-        Cs[rr][c] = (r < rend && cg < nc) ? (Acc)C[r + cg * ldc] : (Acc)0;
+        if (CMASK) Cs[rr][c] = r < rend ? v_at<Acc>(C, ldc, r, (int)cg, mr, (int)nc, true) : (Acc)0;
+        else Cs[rr][c] = (r < rend && cg < nc) ? (Acc)C[r + cg * ldc] : (Acc)0;
       }
     }
     __syncthreads();
@@ -167,18 +168,19 @@ __global__ void __launch_bounds__(kGT) k_tw(const double* __restrict__ part, int
 // r > i; tau_i = 0 gives w'_i = 0).  One CTA per column c: the eight warps
 // sum the splits (fixed order), warp 0 substitutes (lane l: rows l + 32 q).
 constexpr int kOB = 128;
-template <typename Acc>
+template <typename Acc, typename TG = float>
 __global__ void __launch_bounds__(kGT) k_solve_blk(const double* __restrict__ part, int splits, int64_t nc,
-                                                   const float* __restrict__ G, const double* __restrict__ tau,
+                                                   const TG* __restrict__ G, const double* __restrict__ tau,
                                                    int nbo, double* __restrict__ W) {
   constexpr int NW = kGT / 32;
-  extern __shared__ float gs[];  // G(i, r) at gs[i * (kOB + 1) + r]
+  extern __shared__ __align__(16) unsigned char gs_raw[];
+  TG* gs = (TG*)gs_raw;  // G(i, r) at gs[i * (kOB + 1) + r]
   __shared__ double red[NW][kOB];
   __shared__ Acc ts[kOB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c = blockIdx.x;
   for (int e0 = tid; e0 < kOB * kOB; e0 += kGT * 8) {  // eight loads in flight per thread
-    float v[8];
+    TG v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = __ldcg(G + e0 + kGT * u);  // kOB * kOB is a multiple of 8 * kGT
 #pragma unroll
@@ -625,6 +627,99 @@ ct_status run_outer(const ct_factor* f, int64_t J, TC* C, int64_t ldc, int64_t k
 }
 
 }  // namespace
+
+namespace {
+// G(i, r) = sum_z P_z(i, r) for i, r < nbo (zero elsewhere), 128 x 128 FP64;
+// partial z at P + z * 128 * nbo, entry (i, r) at i + r * 128.
+__global__ void k_reduce_g64(const double* __restrict__ P, int splits, int nbo, double* __restrict__ G) {
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e >= kOB * kOB) return;
+  const int i = e % kOB, r = e / kOB;
+  double acc = 0.0;
+  if (i < nbo && r < nbo)
+    for (int z = 0; z < splits; ++z) acc += __ldcg(P + (size_t)z * kOB * nbo + i + (size_t)r * kOB);
+  G[e] = acc;
+}
+}  // namespace
+
+size_t fp64_outer_work_elems(int sms, int64_t n) {
+  return (size_t)2 * sms * kOB * kOB + (size_t)kOB * kOB + (size_t)kOB * (2 * sms * 64 + 64 + 2 * n);
+}
+
+// FP64 two-level factorization: the trailing matrix C = F[J:m, J+nbo:n]
+// updated once with the block reflector of the nbo (<= 128) reflectors of
+// F[J:m, J:J+nbo], through S = diag(1/tau) + striu(V^T V):
+//   G = V^T V (split over rows, reduced), W = V^T C (split-K), W' = S^{-T} W
+//   (forward substitution per column), C -= V W'.
+// Used when tall panels must be narrow (the panel kernel keeps its rows in
+// shared memory), so that the trailing update still contracts over 128.
+ct_status fp64_outer_update(ct_factor* f, int64_t J, int nbo, double* work, size_t work_elems, int sms,
+                            cudaStream_t s) {
+  const int64_t m = f->m, n = f->n, ld = f->ld, mr = m - J, nc = n - J - nbo;
+  if (nc <= 0) return CT_OK;
+  if (nbo < 1 || nbo > kOB || f->store != CT_F64) return CT_ERR_INVALID;
+  if (fp64_outer_work_elems(sms, n) > work_elems) return CT_ERR_INVALID;
+  double* V = (double*)f->F + J + J * ld;
+  double* C = V + (size_t)nbo * ld;
+  double* Gp = work;
+  double* G = Gp + (size_t)2 * sms * kOB * kOB;
+  double* Wp = G + (size_t)kOB * kOB;
+  // 1. G = V^T V
+  int64_t gs = (mr + 2047) / 2048;
+  if (gs > 2 * sms) gs = 2 * sms;
+  if (gs < 1) gs = 1;
+  int64_t gchunk = (mr + gs - 1) / gs;
+  gchunk = (gchunk + kBK - 1) / kBK * kBK;
+  gs = (mr + gchunk - 1) / gchunk;
+  {
+    LaunchScope ls(K_VTC, s, (double)mr * nbo * nbo, 16.0 * mr * nbo);
+    k_vtc<double, double, double, 64, kOB, true><<<dim3((unsigned)((nbo + 63) / 64), (unsigned)gs), kGT, 0, s>>>(
+        V, ld, nbo, V, ld, mr, nbo, gchunk, Gp);
+    CT_LAUNCH_CHECK();
+    k_reduce_g64<<<kOB * kOB / 256, 256, 0, s>>>(Gp, (int)gs, nbo, G);
+    CT_LAUNCH_CHECK();
+  }
+  // 2. W = V^T C, split over rows for about two waves of CTAs
+  const int64_t tiles_n = (nc + 63) / 64;
+  int64_t splits = (2 * sms + tiles_n - 1) / tiles_n;
+  const int64_t max_rows = (mr + 255) / 256;
+  if (splits > max_rows) splits = max_rows;
+  const int64_t cap = (int64_t)((work_elems - (size_t)(Wp - work)) / ((size_t)kOB * nc)) - 1;
+  if (splits > cap) splits = cap;
+  if (splits < 1) return CT_ERR_INVALID;
+  int64_t chunk = (mr + splits - 1) / splits;
+  chunk = (chunk + kBK - 1) / kBK * kBK;
+  splits = (mr + chunk - 1) / chunk;
+  double* W = Wp + (size_t)splits * kOB * nc;
+  const double mnk = (double)mr * nbo * nc;
+  {
+    LaunchScope ls(K_VTC, s, 2.0 * mnk, 8.0 * ((double)mr * nc + (double)mr * nbo));
+    k_vtc<double, double, double, 64, kOB><<<dim3((unsigned)tiles_n, (unsigned)splits), kGT, 0, s>>>(
+        V, ld, nbo, C, ld, mr, nc, chunk, Wp);
+    CT_LAUNCH_CHECK();
+  }
+  // 3. W' = S^{-T} W
+  {
+    const size_t smem = (size_t)kOB * (kOB + 1) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_solve_blk<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+      attr = true;
+    }
+    LaunchScope ls(K_TW, s, (double)kOB * kOB * nc, (double)(splits + 1) * kOB * nc * 8 + smem);
+    k_solve_blk<double, double><<<(unsigned)nc, kGT, smem, s>>>(Wp, (int)splits, nc, G, f->tau + J, nbo, W);
+    CT_LAUNCH_CHECK();
+  }
+  // 4. C -= V W'
+  {
+    LaunchScope ls(K_UPDATE, s, 2.0 * mnk, 16.0 * mr * nc + 8.0 * mr * nbo);
+    k_update<double, double, double, double, 64><<<dim3((unsigned)((mr + kBM - 1) / kBM), (unsigned)tiles_n), kGT, 0,
+                                                   s>>>(V, ld, nbo, true, W, kOB, C, ld, mr, nc);
+    CT_LAUNCH_CHECK();
+  }
+  return CT_OK;
+}
 
 ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f64, int64_t ldc, int64_t k,
                                 bool fp32_math, double* work, size_t work_elems, int sms, cudaStream_t s) {

@@ -221,6 +221,13 @@ ct_status apply_qt_outer_persist(const ct_factor* f, float* C, int64_t ldc, int6
 ct_status apply_outer_reflector(const ct_factor* f, int64_t J, void* C, bool c_f64, int64_t ldc, int64_t k,
                                 bool fp32_math, double* work, size_t work_elems, int sms, cudaStream_t s);
 
+// FP64 two-level factorization (gemm_simt.cu): the trailing update of the
+// columns right of the nbo (<= 128) reflectors at column J, with a contraction
+// over all nbo of them; work holds fp64_outer_work_elems(...) doubles.
+size_t fp64_outer_work_elems(int sms, int64_t n);
+ct_status fp64_outer_update(ct_factor* f, int64_t J, int nbo, double* work, size_t work_elems, int sms,
+                            cudaStream_t s);
+
 // Q^T C for all panels of the factor, in factorization order (api.cu).
 ct_status apply_qt_all(const ct_factor* f, void* C, bool c_f64, int64_t ldc, int64_t k, bool fp32_math,
                        double* work, size_t work_elems, int sms, cudaStream_t s, int max_splits = 0);
@@ -328,6 +335,10 @@ ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int
 // Tile tasks the batch would hold with tile size b (each task is ~100 bytes
 // of host and device memory).
 int64_t batch_task_count(int count, const ct_batch_system* in, int b);
+// Panel width and outer-block width of a CT_PREC_TF32 factorization of an
+// m x n matrix with `passes` TF32 passes: cached choice, or measured now on a
+// synthetic matrix (CTQR_NO_TUNE=1: the defaults 32 and 256).
+ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, cudaStream_t s, int* nb, int* outer);
 // Tile size for systems of this shape: cached choice, or measured now.
 ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* tile);
 

@@ -25,14 +25,20 @@ constexpr size_t kScratchElems = (size_t)(kMaxSplits + 1) * 64 * kMaxK + 64;
 static __device__ __align__(256) double g_apply_scratch[kScratchElems];
 
 std::mutex g_mu;
-double* g_scratch_addr[64] = {};  // device address of the array, per device
+// Device address of the array, per device (as many devices as device_info
+// serves).  The address belongs to the device's primary context: after
+// cudaDeviceReset the module is loaded again and this cached address is
+// stale, so a process that resets a device must not call this entry point
+// on it afterwards.
+constexpr int kMaxDevices = 16;
+double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the array on the current device, looked up once per
 // device (the host-side symbol is only a stand-in for it).
 ct_status scratch_address(double** out) {
   int dev = 0;
   CT_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return CT_ERR_UNSUPPORTED;
+  if (dev < 0 || dev >= kMaxDevices) return CT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;

@@ -165,6 +165,47 @@ __global__ void k_lambda_rows(S* __restrict__ A, int64_t lda, int64_t row0, int6
   if (j < n) A[row0 + j + j * lda] = (S)lambda;
 }
 
+// Joseph's projector (the paper simulates its sinograms with it, Sec. III):
+// one thread per (ray, image).  A ray with |dy| >= |dx| is sampled at every
+// pixel row's centre line, where it falls between two pixel centres of that
+// row; their values are interpolated linearly (a pixel outside the image
+// counts as zero) and weighted by the step p / |dy|; otherwise the same with
+// columns.  B[ray + c ldb] = the ray's sum for image c.
+__global__ void __launch_bounds__(128) k_joseph(Geo g, const double* __restrict__ X, int64_t ldx, int64_t k,
+                                                double* __restrict__ B, int64_t ldb) {
+  const int64_t ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  if (ray >= rays) return;
+  double px, py, dx, dy;
+  ray_of(g, ray, px, py, dx, dy);
+  const bool by_rows = fabs(dy) >= fabs(dx);
+  const int lines = by_rows ? g.ny : g.nx, cells = by_rows ? g.nx : g.ny;
+  const double step = by_rows ? g.pixel / fabs(dy) : g.pixel / fabs(dx);
+  for (int64_t c = blockIdx.y; c < k; c += gridDim.y) {
+    const double* x = X + c * ldx;
+    double acc = 0.0;
+    for (int q = 0; q < lines; ++q) {
+      double u;
+      if (by_rows) {
+        const double yc = g.y0 + ((double)q + 0.5) * g.pixel;
+        const double t = (yc - py) / dy;
+        u = (px + t * dx - g.x0) / g.pixel - 0.5;
+      } else {
+        const double xc = g.x0 + ((double)q + 0.5) * g.pixel;
+        const double t = (xc - px) / dx;
+        u = (py + t * dy - g.y0) / g.pixel - 0.5;
+      }
+      const double fl = floor(u), f = u - fl;
+      const int64_t i0 = (int64_t)fl;
+      double v = 0.0;
+      if (i0 >= 0 && i0 < cells) v += (1.0 - f) * x[by_rows ? (int64_t)q * g.nx + i0 : i0 * g.nx + q];
+      if (i0 + 1 >= 0 && i0 + 1 < cells) v += f * x[by_rows ? (int64_t)q * g.nx + i0 + 1 : (i0 + 1) * g.nx + q];
+      acc += v;
+    }
+    B[ray + c * ldb] = step * acc;
+  }
+}
+
 Geo make_geo(const ct_geometry* gg) {
   Geo g;
   g.beam = gg->beam; g.nx = gg->nx; g.ny = gg->ny; g.n_views = gg->n_views; g.n_bins = gg->n_bins;
@@ -197,6 +238,17 @@ ct_status launch_ray_fill(const ct_geometry* gg, const int64_t* row_ptr, int* co
 
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
                              cudaStream_t s);
+
+ct_status launch_joseph(const ct_geometry* gg, const double* X, int64_t ldx, int64_t k, double* B, int64_t ldb,
+                        cudaStream_t s) {
+  const Geo g = make_geo(gg);
+  const int64_t rays = (int64_t)g.n_views * g.n_bins;
+  const unsigned gy = (unsigned)(k < 256 ? k : 256);
+  LaunchScope ls(K_SIDDON, s, 3.0 * rays * (g.nx > g.ny ? g.nx : g.ny) * k, 16.0 * rays * (g.nx + g.ny) * k);
+  k_joseph<<<dim3((unsigned)((rays + 127) / 128), gy), 128, 0, s>>>(g, X, ldx, k, B, ldb);
+  CT_LAUNCH_CHECK();
+  return CT_OK;
+}
 
 ct_status launch_build_system(const ct_geometry* gg, ct_dtype dtype, double lambda, void* A,
                               int64_t lda, int64_t m, int64_t n, cudaStream_t s) {

@@ -81,11 +81,12 @@ class BatchSystem(ctypes.Structure):
 
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int)]
+    _fields_ = [("tile", ctypes.c_int), ("prec", ctypes.c_int)]
 
 
 class BatchReport(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("ms", ctypes.c_double), ("tasks", ctypes.c_int)]
+    _fields_ = [("tile", ctypes.c_int), ("ms", ctypes.c_double), ("tasks", ctypes.c_int),
+                ("iterations", ctypes.c_int)]
 
 
 class SurrogateOpts(ctypes.Structure):
@@ -111,6 +112,8 @@ SIGNATURES = {
     "ct_qr_factor": ([_VP, _I, _I64, _I64, _I64, _I, ctypes.POINTER(QrOpts),
                       ctypes.POINTER(_VP), _VP], _I),
     "ct_qr_factor_host": ([_VP, _I64, _I64, _I64, ctypes.POINTER(OocOpts), ctypes.POINTER(_VP), _VP], _I),
+    "ct_project_joseph": ([ctypes.POINTER(Geometry), _VP, _I64, _I64, _VP, _I64, _VP], _I),
+    "ct_image_quality": ([_VP, _I64, _VP, _I64, _I, _I, _I64, _VP, _VP], _I),
     "ct_factor_info": ([_VP, _P64, _P64, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "ct_factor_data": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I), _P64, ctypes.POINTER(_VP)], _I),
     "ct_factor_status": ([_VP, _VP], _I),
@@ -252,6 +255,26 @@ def build_system(geom, dtype=torch.float64, lam: float = 0.0, out: torch.Tensor 
     _check(load().ct_build_system(ctypes.byref(geometry(geom)), _dt(A), lam, A.data_ptr(), _ld(A),
                                   _stream()), "ct_build_system")
     return A
+
+
+def project_joseph(geom, X: torch.Tensor, B: torch.Tensor | None = None) -> torch.Tensor:
+    """Sinograms (m x k) of the images X (n x k, FP64 CUDA) by Joseph's projector."""
+    m, n = system_size(geom)
+    k = X.shape[1]
+    if B is None:
+        B = colmajor(m, k)
+    _check(load().ct_project_joseph(ctypes.byref(geometry(geom)), X.data_ptr(), _ld(X), k, B.data_ptr(), _ld(B),
+                                    _stream()), "ct_project_joseph")
+    return B
+
+
+def image_quality(X: torch.Tensor, R: torch.Tensor, nx: int, ny: int) -> torch.Tensor:
+    """k x 3 tensor of (MSE, PSNR dB, SSIM) per slice of X against R."""
+    k = X.shape[1]
+    out = torch.empty(3 * max(k, 1), dtype=torch.float64, device=X.device)
+    _check(load().ct_image_quality(X.data_ptr(), _ld(X), R.data_ptr(), _ld(R), nx, ny, k, out.data_ptr(),
+                                   _stream()), "ct_image_quality")
+    return out[:3 * k].view(k, 3)
 
 
 class Factor:
@@ -475,7 +498,7 @@ def gemm_status() -> int:
     return load().ct_gemm_status(_stream())
 
 
-def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True):
+def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True, prec: Prec = Prec.F64):
     """Factor and solve a batch of systems in place (lists of column-major
     FP64 CUDA tensors; Bs entries may be None).  Rows [0, n) of every B hold X
     afterwards.  Returns (status, BatchReport)."""
@@ -485,7 +508,8 @@ def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True):
         arr[q] = BatchSystem(m, n, A.data_ptr(), _ld(A), B.data_ptr() if B is not None else None,
                              _ld(B) if B is not None else m, B.shape[1] if B is not None else 0)
     rep = BatchReport()
-    st = load().ct_qr_solve_batched(len(As), arr, ctypes.byref(BatchOpts(tile)), ctypes.byref(rep), _stream())
+    st = load().ct_qr_solve_batched(len(As), arr, ctypes.byref(BatchOpts(tile, int(prec))), ctypes.byref(rep),
+                                    _stream())
     if check:
         _check(st, "ct_qr_solve_batched")
     return st, rep

@@ -124,3 +124,37 @@ def test_batched_stalled_task_times_out_and_context_survives(monkeypatch):
     X = Bt.cpu().numpy()[:120]
     Xo = O.lstsq(A, B)
     assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10
+
+
+def test_mixed_precision_batch_matches_oracle_and_keeps_A():
+    """ct_qr_solve_batched with CT_PREC_TF32: every system through the
+    tensor-core factorization and FP64 refinement against its own FP64 A
+    (left unchanged): the four smallest systems of the uneven 64-system batch
+    and two random ones, against the oracle's least-squares solutions."""
+    cfg = I.CONFIG4B
+    geoms = I.uneven_systems(cfg["count"], cfg["seed"])
+    idx = sorted(range(len(geoms)), key=lambda q: geoms[q].m * geoms[q].n)[:4]
+    lam = cfg["lam"]
+    As, Bs, ref = [], [], []
+    for q in idx:
+        g = geoms[q]
+        Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+        b = np.vstack([Ao @ I.phantoms(g, [cfg["seed0"] + q]), np.zeros((g.n, 1))])
+        As.append(ctqr.build_system(g, torch.float64, lam=lam))
+        Bs.append(ctqr.to_colmajor(b))
+        ref.append((np.vstack([Ao, lam * np.eye(g.n)]), b, g.n))
+    for q, (m, n, k) in enumerate([(700, 300, 3), (1300, 650, 2)]):
+        A = I.random_matrix(m, n, seed=600 + q)
+        B = I.random_matrix(m, k, seed=610 + q)
+        As.append(ctqr.to_colmajor(A))
+        Bs.append(ctqr.to_colmajor(B))
+        ref.append((A, B, n))
+    before = [A.clone() for A in As]
+    st, rep = ctqr.qr_solve_batched(As, Bs, prec=ctqr.Prec.TF32)
+    assert st == ctqr.CT_OK and rep.tasks == 0 and rep.iterations >= 1
+    torch.cuda.synchronize()
+    for (Asys, b, n), Bt, A0, A1 in zip(ref, Bs, before, As):
+        assert torch.equal(A0, A1)
+        X = Bt.cpu().numpy()[:n]
+        Xo = O.lstsq(Asys, b)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10, n

@@ -297,7 +297,7 @@ def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape):
     torch.cuda.synchronize()
     ctqr.profile_reset()
     ctqr.profile_enable(True)
-    f = ctqr.qr_factor(Af, prec=ctqr.Prec.TF32)
+    f = ctqr.qr_factor(Af, prec=ctqr.Prec.TF32, nb=32)  # explicit width: no tuning runs inside
     torch.cuda.synchronize()
     ctqr.profile_enable(False)
     launches = {p_["name"]: p_["launches"] for p_ in ctqr.profile_kernels()}
@@ -524,3 +524,81 @@ def test_qr_options_reject_bad_outer_width():
     with pytest.raises(ctqr.CtError) as e:
         ctqr.qr_factor(A, prec=ctqr.Prec.TF32, outer_nb=192)
     assert e.value.status == ctqr.CT_ERR_INVALID
+
+
+@pytest.mark.parametrize("cond,bound", [(1e3, 2e-6), (1e6, 2e-5)])
+def test_fp32_panel_gram_is_better_than_fp32(cond, bound):
+    """One 32-column panel of an FP32-stored factor with condition number
+    1e3: the Cholesky-QR panel forms its Gram matrix as compensated FP32
+    products (about twice FP32's precision); in plain FP32 the Gram's error,
+    amplified by kappa^2 = 1e6, would put R off by ~1e-1 relative.  R must
+    match the oracle's R (of the same FP32-exact data) to FP32 storage level.
+    With condition 1e6 the panel's kappa_1(R1) exceeds the Cholesky-QR limit
+    and it falls back to per-column Householder, again to FP32 level."""
+    rng = np.random.default_rng(int(cond))
+    m, n = 5000, 32
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    Vt, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (U * np.logspace(0, -np.log10(cond), n)) @ Vt.T
+    A = A.astype(np.float32).astype(np.float64)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A, dtype=torch.float32), prec=ctqr.Prec.F32, nb=32)
+    F, _ = ctqr.factor_matrix(f)
+    R = np.triu(_np(F).astype(np.float64)[:n])
+    Fo, _ = O.qr(A)
+    Ro = np.triu(Fo[:n])
+    sgn = np.sign(np.diag(R)) * np.sign(np.diag(Ro))  # rows fixed up to sign
+    err = np.abs(R - sgn[:, None] * Ro).max() / np.abs(Ro).max()
+    assert err <= bound, err
+
+
+def test_tf32_factor_widths_are_tuned_and_cached(tmp_path, monkeypatch):
+    """With the widths left open, a TF32 factorization takes the panel and
+    outer-block widths the tuner measured for its size class (16 or 32; 128
+    or 256) and caches them in the JSON file; the second factorization of the
+    same class reuses the cached pair (no measurement: no extra launches)."""
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("CTQR_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("CTQR_NO_TUNE", raising=False)
+    A = I.random_matrix(3000, 700, seed=61)
+    Af = ctqr.to_colmajor(A, dtype=torch.float32)
+    f1 = ctqr.qr_factor(Af, prec=ctqr.Prec.TF32)
+    assert f1.info()["nb"] in (16, 32)
+    import json
+    text = json.loads(cache.read_text())
+    keys = [k for k in text if k.startswith("factor_tf32/")]
+    assert len(keys) == 1 and text[keys[0]] // 1000 == f1.info()["nb"] and text[keys[0]] % 1000 in (128, 256)
+    torch.cuda.synchronize()
+    ctqr.profile_reset()
+    ctqr.profile_enable(True)
+    f2 = ctqr.qr_factor(Af, prec=ctqr.Prec.TF32)
+    torch.cuda.synchronize()
+    ctqr.profile_enable(False)
+    panels = {p_["name"]: p_["launches"] for p_ in ctqr.profile_kernels()}["panel_qr"]
+    assert panels == -(-700 // f2.info()["nb"])  # one factorization's panels, no tuning runs
+    b = A @ I.random_matrix(700, 1, seed=62)
+    X, rep = ctqr.reconstruct(f2, ctqr.to_colmajor(b), A=ctqr.to_colmajor(A))
+    Xo = O.lstsq(A, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
+
+
+@pytest.mark.parametrize("shape,nb", [((1000, 513), 64), ((2700, 1024), 24), ((700, 300), 40)])
+def test_fp64_two_level_factor_matches_oracle(shape, nb):
+    """FP64 factorization with the trailing matrix updated once per outer
+    block of (128 // nb) * nb columns (the form tall FP64 matrices take when
+    their panels must be narrow): R, V and tau against the oracle (1e-11), the
+    solution to 1e-10, and Q^T through the panel T blocks unchanged."""
+    m, n = shape
+    A = I.random_matrix(m, n, seed=800 + n)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A), nb=nb, outer_nb=128)
+    assert f.status() == ctqr.CT_OK and f.info()["nb"] == nb
+    F, tau = ctqr.factor_matrix(f)
+    Fo, tauo = O.qr(A)
+    F, tau = _np(F), _np(tau)
+    scale = np.abs(Fo).max()
+    assert np.abs(np.triu(F[:n]) - np.triu(Fo[:n])).max() <= 1e-11 * scale
+    assert np.abs(np.tril(F, -1) - np.tril(Fo, -1)).max() <= 1e-11 * max(1.0, np.abs(np.tril(Fo, -1)).max())
+    assert np.abs(tau - tauo).max() <= 1e-11
+    b = I.random_matrix(m, 3, seed=801)
+    X, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b))
+    Xo = O.lstsq(A, b)
+    assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10

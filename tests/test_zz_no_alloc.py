@@ -2,7 +2,11 @@
 C ABI, against the allocating ct_apply_qt on the same factor and inputs, two
 calls in a row (the second call reuses the static workspace the first one
 left behind).  Tolerance: the same 1e-11 relative bound as the Q^T parity tests
-(both paths do identical arithmetic up to the row splitting of V^T B)."""
+(both paths do identical arithmetic up to the row splitting of V^T B).
+Callers that cannot allocate are modelled with the library's allocation-
+failure injection: with it on, the allocating entry point fails and this one
+still works.  A tall case (9000 rows, k = 64) fills the static workspace: 64
+row splits of V^T B."""
 import numpy as np
 import pytest
 import torch
@@ -13,18 +17,26 @@ from paper_1907_01891_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.F32])
-def test_noalloc_apply_qt_matches_allocating_entry_point_twice(prec):
+@pytest.mark.parametrize("prec,m,n,ks", [(ctqr.Prec.F64, 1500, 330, (37, 64)), (ctqr.Prec.F32, 1500, 330, (37, 64)),
+                                         (ctqr.Prec.F64, 9000, 330, (64, 64))])
+def test_noalloc_apply_qt_matches_allocating_entry_point_twice(prec, m, n, ks, monkeypatch):
     lib = ctqr.load()
-    m, n = 1500, 330
     A = ctqr.to_colmajor(I.random_matrix(m, n, seed=101))
     f = ctqr.qr_factor(A if prec == ctqr.Prec.F64 else A.to(torch.float32), prec=prec)
-    for call, k in enumerate((37, 64)):
+    refs = []
+    for call, k in enumerate(ks):
         B = I.random_matrix(m, k, seed=200 + call)
         ref = ctqr.to_colmajor(B)
         ctqr.apply_qt(f, ref)
+        refs.append((B, ref))
+    torch.cuda.synchronize()
+    monkeypatch.setenv("CTQR_FAULT_NOMEM", "1")  # every library allocation now fails
+    s = torch.cuda.current_stream().cuda_stream
+    for B, ref in refs:
+        k = B.shape[1]
         got = ctqr.to_colmajor(B)
-        st = lib.ct_apply_qt_noalloc(f.handle, got.data_ptr(), m, k, torch.cuda.current_stream().cuda_stream)
+        assert lib.ct_apply_qt(f.handle, ctqr.to_colmajor(B).data_ptr(), m, k, s) == ctqr.CT_ERR_NOMEM
+        st = lib.ct_apply_qt_noalloc(f.handle, got.data_ptr(), m, k, s)
         assert st == ctqr.CT_OK
         torch.cuda.synchronize()
         r, g = ref.cpu().numpy(), got.cpu().numpy()
