@@ -342,6 +342,14 @@ ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, cudaStream_t s, 
 // Tile size for systems of this shape: cached choice, or measured now.
 ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* tile);
 
+// ---- surrogate convolutions on the tensor cores (conv_tc.cu) -------------
+}  // namespace ctqr
+#include <cuda_bf16.h>
+namespace ctqr {
+ct_status launch_conv_tc(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, int H, int W, int64_t B,
+                         const __nv_bfloat16* res, __nv_bfloat16* r_out, __nv_bfloat16* a_out, int* status,
+                         cudaStream_t s);
+
 // ---- solve through a factor (api.cu) ---------------------------------------
 // X = solution of the system f factors for the right-hand sides B (f->m rows):
 // the plain FP64 apply + back-solve when sp is NULL, else FP64-residual

@@ -424,6 +424,16 @@ struct Surrogate {
 
 namespace {
 
+// The residual layers' forward convolutions run on the tensor cores unless
+// CTQR_CONV_SIMT=1 selects the CUDA-core kernel (for comparison).
+bool conv_tc_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("CTQR_CONV_SIMT");
+    return !(e && *e == '1');
+  }();
+  return on;
+}
+
 dim3 conv_grid(const Surrogate& s, int64_t B) {
   return dim3((unsigned)((s.nx + kTile - 1) / kTile), (unsigned)((s.ny + kTile - 1) / kTile), (unsigned)B);
 }
@@ -440,6 +450,13 @@ ct_status forward(Surrogate& s, int64_t B, bool train, cudaStream_t st) {
                                            train ? s.r[1] : nullptr, s.a[1], nullptr);
   }
   for (int l = 1; l < L - 1; ++l) {
+    if (conv_tc_enabled()) {
+      // the 32 -> 32 residual layers on the tensor cores (conv_tc.cu)
+      const ct_status r = launch_conv_tc(s.a[l], s.pb + s.w_off[l], s.p + s.b_off[l], s.ny, s.nx, B, s.a[l],
+                                         train ? s.r[l + 1] : nullptr, s.a[l + 1], s.status, st);
+      if (r != CT_OK) return r;
+      continue;
+    }
     LaunchScope ls(K_CONV, st, 18.0 * px * C * C, px * C * (train ? 8.0 : 6.0));
     k_conv_fwd<C, C><<<grid, 256, 0, st>>>(s.a[l], s.pb + s.w_off[l], s.p + s.b_off[l], s.ny, s.nx, 2, s.a[l],
                                            train ? s.r[l + 1] : nullptr, s.a[l + 1], nullptr);

@@ -38,9 +38,12 @@
 #include <cuda.h>
 
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace ctqr {
 namespace {
+
+using namespace tc;
 
 constexpr int kBM = 128;
 constexpr int kBK = 32;  // floats per K slice = one 128-byte swizzle row
@@ -48,7 +51,6 @@ constexpr int kThreads = 192;
 // K slices (of kBK rows) per TMEM accumulation chunk: 256 rows, about 96
 // truncating accumulations of 3xTF32 MMAs per chunk.
 constexpr int kAccChunkSlices = 8;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 struct TcArgs {
   int64_t M, N, K;
@@ -60,108 +62,6 @@ struct TcArgs {
   int mode;
   int* status;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase of `bar` with the given parity.  With
-// bail = true it also gives up as soon as another thread recorded an error.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, bool bail = true) {
-  uint64_t t0 = 0;
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u) {
-      const uint64_t now = globaltimer_ns();
-      if (t0 == 0) t0 = now;
-      if (bail && ld_volatile_i32(status) != 0) return false;
-      if (now - t0 > kWaitLimitNs) {
-        set_status(status, CT_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO), fixed field 0b001 at bit 46.
-__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
-  const uint64_t a = smem_u32(p);
-  uint64_t d = (a >> 4) & 0x3FFFull;
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-      "%13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 __device__ __forceinline__ float tf32_trunc(float x) {
   return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
@@ -365,11 +265,28 @@ constexpr size_t kUpdCbufBytes = (size_t)256 * 64 * sizeof(float);  // 64 column
 
 struct UpdArgs {
   int64_t M, N, K;
+  // tile t -> (row tile, column tile) (see update_tile)
   float* C;
   int64_t ldc;
   int64_t mtiles, ntiles;
   int* status;
 };
+
+// Output tile t of the persistent update -> its first row m0 and column n0.
+// Row tiles are taken in bands of G = gridDim.x: inside a band, tile
+// t = band_start + c + i*G goes to row (c + i*G) % R and column
+// (c + i*G) / R, R the band's rows.  With full bands every CTA keeps one row
+// tile (its slice of V) and walks the columns in step with the others, so
+// each V tile is read from DRAM once per band and each W' tile once per
+// band, both while they are hot in L2; a row-major walk instead re-reads all
+// of V (up to 0.28 GB) for every column tile.
+__device__ __forceinline__ void update_tile(int64_t t, int64_t mtiles, int64_t ntiles, int64_t G, int64_t& m0,
+                                            int64_t& n0) {
+  const int64_t band = t / (G * ntiles), local = t - band * G * ntiles;
+  const int64_t rows = mtiles - band * G < G ? mtiles - band * G : G;
+  m0 = (band * G + local % rows) * kBM;
+  n0 = (local / rows) * kBM;
+}
 
 template <bool SPLIT3, int STAGES>
 __global__ void __launch_bounds__(kUpdThreads, 1)
@@ -417,7 +334,9 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
       int64_t g = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
-        const int m0 = (int)((t % args.mtiles) * kBM), n0 = (int)((t / args.mtiles) * kBM);
+        int64_t m0l, n0l;
+        update_tile(t, args.mtiles, args.ntiles, gridDim.x, m0l, n0l);
+        const int m0 = (int)m0l, n0 = (int)n0l;
         for (int ks = 0; ks < nk; ++ks, ++g) {
           const int s = (int)(g % STAGES);
           const int64_t u = g / STAGES;
@@ -481,7 +400,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     const int et = threadIdx.x - 128;
     float* cbuf = (float*)(smem + STAGES * STAGE_BYTES + 256);
     auto prefetch = [&](int64_t t) {
-      const int64_t m0 = (t % args.mtiles) * kBM, n0 = (t / args.mtiles) * kBM;
+      int64_t m0, n0;
+      update_tile(t, args.mtiles, args.ntiles, gridDim.x, m0, n0);
       const int64_t row = m0 + lg * 32 + lane, c0 = n0 + half * 64;
       const bool rok = row < args.M;
 #pragma unroll 16
@@ -495,7 +415,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
       const int acc = it & 1, ua = it >> 1;
-      const int64_t m0 = (t % args.mtiles) * kBM, n0 = (t / args.mtiles) * kBM;
+      int64_t m0, n0;
+      update_tile(t, args.mtiles, args.ntiles, gridDim.x, m0, n0);
       const int64_t row = m0 + lg * 32 + lane;
       const int64_t c0 = n0 + half * 64;
       const bool rok = row < args.M;
