@@ -11,9 +11,11 @@ HBM.  value = slices reconstructed per second (whole job, all ranks).
   python bench.py --probe M N [--rhs K]  # per-kernel launch list of one factorization
 
 The default workload is the 256 x 256 fan-beam system stacked over 1e-3 I
-(135232 x 65536, 64 slices) with the 3xTF32 tensor-core factor and FP64
-refinement; after the timed steps the plain FP64 QR path reconstructs the same
-scan once, for the relative error and the FP64 path's slices/s.
+(135232 x 65536, 64 slices) with the tensor-core factor whose products split
+every FP32 operand into two FP16 parts (--prec f16x3; --prec tf32 selects the
+three-pass TF32 split) and FP64 refinement; after the timed steps the plain
+FP64 QR path reconstructs the same scan once, for the relative error and the
+FP64 path's slices/s.
 
 Multi-GPU (torchrun): every rank reconstructs its own scan (independent
 replicas, weak scaling); there is no data-path collective.
@@ -38,8 +40,8 @@ from paper_1907_01891_gb300 import inputs as I  # noqa: E402
 
 METRIC = "slices/s & QR TFLOP/s: mixed-prec+refine vs FP64 QR, 1 GB300, rel err ≤1e-10"
 WORKLOADS = {"fan128": I.CONFIG2, "fan256": I.CONFIG3, "parallel32": I.CONFIG1, "batch64": I.CONFIG4B}
-PREC = {"f64": 0, "f32": 1, "tf32": 2}
-DTYPE_NAME = {"f64": "f64", "f32": "f32+f64", "tf32": "tf32+f64"}
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "f16x3": 3}
+DTYPE_NAME = {"f64": "f64", "f32": "f32+f64", "tf32": "tf32+f64", "f16x3": "f16x3+f64"}
 
 
 def parse():
@@ -49,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="fan256")
-    p.add_argument("--prec", choices=sorted(PREC), default="tf32")
+    p.add_argument("--prec", choices=sorted(PREC), default="f16x3")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -487,22 +489,29 @@ def roofline(dom, prec, ms_step, peaks):
     hbm = peaks.get("hbm_gbs")
     hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800 GB/s"
     hbm = hbm or 6800.0
-    # TF32 tensor peak: cuBLAS TF32 8192^3 measured on this machine's GB300 (1040
-    # TFLOP/s), above the BF16-derived figure (sustained BF16 x 1.1/2.25)
-    tf32_peak = TF32_MEASURED_TFLOPS
+    # Tensor peak of the products' input type.  TF32: cuBLAS TF32 8192^3
+    # measured on this machine's GB300 (1040 TFLOP/s), above the BF16-derived
+    # figure (sustained BF16 x 1.1/2.25).  FP16 (the FP16-split factor): the
+    # measured sustained BF16 rate (FP16 and BF16 MMAs run at the same rate;
+    # the factorization is a seconds-long step).
+    if prec == "f16x3":
+        t_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        t_src = ("measured sustained cuBLAS BF16 (MEASURED_PEAKS.json bf16_tflops_sustained; FP16 runs at "
+                 "the BF16 rate)" if peaks.get("bf16_tflops_sustained") else "fallback 1.7 PFLOP/s sustained")
+        t_note = "algorithmic flops 2MNK; the FP16 split issues three FP16 MMAs per product"
+    else:
+        t_peak, t_src = TF32_MEASURED_TFLOPS, "measured cuBLAS TF32 (8192^3) on a GB300 of this pool"
+        t_note = "algorithmic flops 2MNK; 3xTF32 issues three MMAs per product"
     name = dom["name"]
     if name in ("zero_fill", "copy", "system_matrix", "tc_update", "tc_fused"):
         roof = {"bound": "hbm", "achieved": dom["bytes"] / (dom["ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": hbm_src}
         if name in ("tc_update", "tc_fused"):
-            roof["tensor_rate"] = {"achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": tf32_peak,
-                                   "unit": "TFLOP/s", "issued_x": 3,
-                                   "peak_source": "measured cuBLAS TF32 (8192^3) on a GB300 of this pool",
-                                   "note": "algorithmic flops 2MNK; 3xTF32 issues three MMAs per product"}
+            roof["tensor_rate"] = {"achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": t_peak,
+                                   "unit": "TFLOP/s", "issued_x": 3, "peak_source": t_src, "note": t_note}
     elif name == "tc_gemm":
-        roof = {"bound": "tensor", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": tf32_peak,
-                "unit": "TFLOP/s", "peak_source": "measured cuBLAS TF32 (8192^3) on a GB300 of this pool",
-                "note": "achieved counts algorithmic flops 2MNK; 3xTF32 issues 3 MMAs per product"}
+        roof = {"bound": "tensor", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": t_peak,
+                "unit": "TFLOP/s", "peak_source": t_src, "note": t_note}
     else:
         alu = fp64_peak if prec == "f64" or name == "panel_qr" else fp32_peak
         roof = {"bound": "alu", "achieved": dom["flops"] / (dom["ms"] / 1e3) / 1e12, "peak": alu,
@@ -691,6 +700,12 @@ def main():
             "panel_arithmetic": ("FP32-stored factors: Cholesky-QR panels whose Gram matrix and row solves are "
                                  "compensated FP32 (Dot2) products, the 32x32 algebra, tau and T in FP64"
                                  if args.prec != "f64" else "FP64 per-column Householder panels"),
+            "update_arithmetic": {
+                "f16x3": "tcgen05 kind::f16: each FP32 operand split into two FP16 parts (per-column power-of-two "
+                         "scales), three FP16 products with FP32 accumulation, TMEM chunks summed every 256 rows",
+                "tf32": "tcgen05 kind::tf32: each FP32 operand split into TF32 high and low parts, three products "
+                        "with FP32 accumulation, TMEM chunks summed every 256 rows",
+                "f32": "FP32 on the CUDA cores", "f64": "FP64 on the CUDA cores"}[args.prec],
             "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "kernels": {s_["name"]: {"launches": s_["launches"], "ms": round(s_["ms"], 3)}
                         for s_ in kstats if s_["launches"]}}
@@ -769,7 +784,7 @@ def main_batch(args, world, rank, local, cfg):
     ctqr.load()
     # FP64: the persistent tile-task launch; tf32: per-system tensor-core
     # factor + FP64 refinement
-    bprec = ctqr.Prec.F64 if args.prec == "f64" else ctqr.Prec.TF32
+    bprec = ctqr.Prec(PREC[args.prec]) if args.prec in ("tf32", "f16x3") else ctqr.Prec.F64
     A0, B0, As, Bs = [], [], [], []
     for g, x in zip(geoms, Xtrue):
         A = ctqr.build_system(g, torch.float64, lam=lam)

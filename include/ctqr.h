@@ -60,8 +60,15 @@ typedef enum { CT_F64 = 0, CT_F32 = 1 } ct_dtype;
  * CT_PREC_F32: factor stored in FP32, updates in FP32 (CUDA cores).
  * CT_PREC_TF32: factor stored in FP32; 128-column outer blocks of 32-column
  * panels, the outer trailing updates on the tensor cores (tcgen05) in TF32 with
- * FP32 accumulation (error-compensated by default, see ct_qr_opts). */
-typedef enum { CT_PREC_F64 = 0, CT_PREC_F32 = 1, CT_PREC_TF32 = 2 } ct_prec;
+ * FP32 accumulation (error-compensated by default, see ct_qr_opts).
+ * CT_PREC_F16X3: as CT_PREC_TF32, but each FP32 operand of the outer updates'
+ * two tensor-core products is split into two FP16 parts h + l (22 significant
+ * bits; the reflectors scaled by 2^8, the trailing matrix and T^T V^T C by a
+ * power of two per column) and three FP16 products h h + l h + h l are
+ * accumulated in FP32: about the accuracy of the three-pass TF32 split at
+ * half its tensor time and operand bytes.  A reflector entry of magnitude
+ * >= 192 is reported as CT_ERR_NONFINITE.  tf32_passes must be 0. */
+typedef enum { CT_PREC_F64 = 0, CT_PREC_F32 = 1, CT_PREC_TF32 = 2, CT_PREC_F16X3 = 3 } ct_prec;
 
 /* Scanner geometry (Sec. II-A and Table (scanner) describe the paper's fan-beam
  * scanner; this struct parameterises parallel and fan beams).
@@ -174,8 +181,9 @@ typedef struct {
   int tile;       /* tile size 32 or 64; 0 = measured choice per size class,   */
                   /* cached in $CTQR_TUNE_CACHE (else ~/.cache/ctqr_tune.json) */
   int prec;       /* CT_PREC_F64 (0, default): the persistent tile-task launch */
-                  /* below; CT_PREC_TF32: each system factored by the tensor-  */
-                  /* core path of ct_qr_factor (widths tuned per size class)   */
+                  /* below; CT_PREC_TF32 or CT_PREC_F16X3: each system        */
+                  /* factored by the tensor-core path of ct_qr_factor in that  */
+                  /* precision (TF32 widths tuned per size class)              */
                   /* and refined to the FP64 least-squares solution by         */
                   /* ct_reconstruct_batch against its FP64 A, which is then    */
                   /* left unchanged                                            */
@@ -407,8 +415,20 @@ ct_status ct_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64
                           const float* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
                           int split3, void* stream);
 
+/* The same contraction with each FP32 operand split into two FP16 parts (the
+ * products of CT_PREC_F16X3 factors): A scaled by 2^8 (|A| < 128 required),
+ * B per column by a power of two from its largest magnitude; C = A^T B
+ * (accumulate == 0: the split-K product kernel, B split on chip) or C -= A^T B
+ * (accumulate == 1: the persistent update kernel, both operands split first;
+ * K <= 256).  M, N <= 65535; lda, ldb multiples of 4, A and B 16-byte
+ * aligned.  Allocates its split operands on `stream`.  Errors as
+ * ct_gemm_tf32_tn (CT_ERR_NONFINITE is not checked here). */
+ct_status ct_gemm_f16x3_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                           const float* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
+                           void* stream);
+
 /* Synchronise `stream` and return (and clear) the device status recorded by
- * ct_gemm_tf32_tn calls. */
+ * ct_gemm_tf32_tn and ct_gemm_f16x3_tn calls. */
 ct_status ct_gemm_status(void* stream);
 
 /* Whole method for one scan: build A from `geom` on the device (Eq.

@@ -499,7 +499,7 @@ void free_factor(ct_factor* f) {
 }
 
 ct_status alloc_factor_aux(ct_factor* f, const DeviceInfo& di) {
-  const bool tc = f->prec == CT_PREC_TF32;
+  const bool tc = tc_prec(f->prec);
   const int64_t n = f->n, np = npanels(f);
   f->partials_elems = panel_partials_elems(di.sms, f->nb);
   ct_status st;
@@ -617,7 +617,7 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   *out = nullptr;
   if (!A || !aligned16(A) || n < 1 || m < n || lda < m) return CT_ERR_INVALID;
   if (dtype != CT_F64 && dtype != CT_F32) return CT_ERR_INVALID;
-  if (prec != CT_PREC_F64 && prec != CT_PREC_F32 && prec != CT_PREC_TF32) return CT_ERR_INVALID;
+  if (prec != CT_PREC_F64 && prec != CT_PREC_F32 && !tc_prec(prec)) return CT_ERR_INVALID;
   const ct_dtype store = prec == CT_PREC_F64 ? CT_F64 : CT_F32;
   const bool in_place = opts && opts->in_place;
   if (in_place && dtype != store) return CT_ERR_INVALID;
@@ -633,16 +633,18 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
   f->prec = prec;
   f->store = store;
   f->device = di.device;
-  const bool tc = prec == CT_PREC_TF32;
+  const bool tc = tc_prec(prec);
+  const bool f16 = prec == CT_PREC_F16X3;
   const int passes = opts && opts->tf32_passes ? opts->tf32_passes : 3;
   if (tc && passes != 1 && passes != 3) { delete f; return CT_ERR_INVALID; }
+  if (f16 && opts && opts->tf32_passes) { delete f; return CT_ERR_INVALID; }
   int outer = opts && opts->outer_nb ? opts->outer_nb : 256;
   if (outer != 128 && outer != 256) { delete f; return CT_ERR_INVALID; }
   if (prec == CT_PREC_F64 && outer == 256 && opts && opts->outer_nb) { delete f; return CT_ERR_INVALID; }
   int want = (opts && opts->nb) ? opts->nb : (prec == CT_PREC_F64 ? 64 : 32);
   // TF32 factors whose widths the caller leaves open take the tuned pair
   if (tc && !(opts && opts->nb) && !(opts && opts->outer_nb)) {
-    if ((st = tuned_factor_widths(m, n, passes, s, &want, &outer)) != CT_OK) { delete f; return st; }
+    if ((st = tuned_factor_widths(m, n, passes, prec, s, &want, &outer)) != CT_OK) { delete f; return st; }
   }
   if (tc && (want > 32 || (want & (want - 1)))) { delete f; return CT_ERR_INVALID; }
   f->nb = panel_width_that_fits(m, want, di, store == CT_F64 ? 8 : 4, tc);
@@ -724,9 +726,24 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
     // own 128-column half, the first half's block reflector updates the
     // second half, and the rest of the matrix gets one tensor-core update
     // per outer block.
-    const size_t owf = outer_work_floats(di.sms, m, n, outer);
-    Scratch owork;
+    const size_t owf = f16 ? outer_work_floats16(di.sms, m, n, outer) : outer_work_floats(di.sms, m, n, outer);
+    Scratch owork, cwork;
     if ((st = owork.alloc(owf * sizeof(float), s)) != CT_OK) { free_factor(f); return st; }
+    // FP16-split updates: bounds on the trailing columns' magnitudes (the
+    // first block's from one pass over the matrix)
+    F16Cols cols;
+    if (f16) {
+      if ((st = cwork.alloc((size_t)n * (sizeof(double) + sizeof(unsigned)), s)) != CT_OK) {
+        free_factor(f);
+        return st;
+      }
+      cols.acc = (double*)cwork.p;
+      cols.bound = (unsigned*)(cols.acc + n);
+      if ((st = f16_bounds(f, &cols, s)) != CT_OK) {
+        free_factor(f);
+        return st;
+      }
+    }
     // Look-ahead (opt-in, CTQR_LOOKAHEAD=1): while the columns beyond the
     // next outer block are updated on a second stream (on all but kReserve
     // SMs), the next block's panels and inner updates run on the reserved
@@ -761,7 +778,7 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       return CT_ERR_CUDA;
     }
     const char* la_env = getenv("CTQR_LOOKAHEAD");
-    const bool la_on = outer == 128 && la_env && *la_env == '1' && di.sms > 2 * kReserve;
+    const bool la_on = !f16 && outer == 128 && la_env && *la_env == '1' && di.sms > 2 * kReserve;
     if (la_on) {
       if (cudaStreamCreateWithFlags(&la.s2, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&la.ev_w, cudaEventDisableTiming) != cudaSuccess ||
@@ -784,10 +801,13 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       const int nbo_b = (int)(n - J - 128 <= 0 ? 0 : (n - J - 128 < 128 ? n - J - 128 : 128));
       if ((st = half_panels(J, nbo_a)) != CT_OK) { free_factor(f); return st; }
       if (nbo_b == 0) break;
-      if ((st = outer_block_update(f, J, nbo_a, (float*)owork.p, owf, di.sms, passes == 3, s, &la,
-                                   J + 128 + nbo_b)) != CT_OK ||
+      if ((st = f16 ? outer_update16(f, J, nbo_a, (float*)owork.p, owf, di.sms, s, &la, J + 128 + nbo_b, &cols)
+                    : outer_block_update(f, J, nbo_a, (float*)owork.p, owf, di.sms, passes == 3, s, &la,
+                                         J + 128 + nbo_b)) != CT_OK ||
           (st = half_panels(J + 128, nbo_b)) != CT_OK ||
-          (st = outer_block_update256(f, J, nbo_b, (float*)owork.p, owf, di.sms, passes == 3, s, &la)) != CT_OK) {
+          (st = f16 ? outer_update256_16(f, J, nbo_b, (float*)owork.p, owf, di.sms, s, &la, &cols)
+                    : outer_block_update256(f, J, nbo_b, (float*)owork.p, owf, di.sms, passes == 3, s, &la)) !=
+              CT_OK) {
         free_factor(f);
         return st;
       }
@@ -802,7 +822,8 @@ ct_status ct_qr_factor(const void* A, ct_dtype dtype, int64_t m, int64_t n, int6
       }
       f->panel_cap = 0;
       la.defer = la_on && J + 256 < n && panel_fits_ctas(m - (J + 128), f->nb, kReserve, di);
-      if ((st = outer_block_update(f, J, nbo, (float*)owork.p, owf, di.sms, passes == 3, s, &la)) != CT_OK) {
+      if ((st = f16 ? outer_update16(f, J, nbo, (float*)owork.p, owf, di.sms, s, &la, 0, &cols)
+                    : outer_block_update(f, J, nbo, (float*)owork.p, owf, di.sms, passes == 3, s, &la)) != CT_OK) {
         free_factor(f);
         return st;
       }
@@ -980,7 +1001,7 @@ ct_status ct_reconstruct_scan(const ct_geometry* geom, double lambda, ct_prec pr
   if (st != CT_OK) return st;
   if (k < 0 || (k > 0 && (!B || !X || ldb < m || ldx < n))) return CT_ERR_INVALID;
   if (where != CT_DEVICE_BUFFERS && where != CT_HOST_BUFFERS) return CT_ERR_INVALID;
-  if (prec != CT_PREC_F64 && prec != CT_PREC_F32 && prec != CT_PREC_TF32) return CT_ERR_INVALID;
+  if (prec != CT_PREC_F64 && prec != CT_PREC_F32 && !tc_prec(prec)) return CT_ERR_INVALID;
   if (m < n) return CT_ERR_INVALID;
   if (k == 0) return CT_OK;
   cudaStream_t s = as_stream(stream);
@@ -1076,6 +1097,45 @@ ct_status ct_gemm_tf32_tn(int64_t M, int64_t N, int64_t K, const float* A, int64
                     as_stream(stream));
 }
 
+ct_status ct_gemm_f16x3_tn(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                           int64_t ldb, float* C, int64_t ldc, int accumulate, void* stream) {
+  if (M < 0 || N < 0 || K < 0) return CT_ERR_INVALID;
+  if (M == 0 || N == 0) return CT_OK;
+  if (!A || !B || !C || !aligned16(A) || !aligned16(B) || lda < K || ldb < K || ldc < M || (lda & 3) || (ldb & 3))
+    return CT_ERR_INVALID;
+  if (M > 65535 || N > 65535 || (accumulate && K > 256)) return CT_ERR_INVALID;
+  ct_status err = CT_OK;
+  int* status = gemm_status_word(&err);
+  if (!status) return err;
+  DeviceInfo di;
+  ct_status st = device_info(&di);
+  if (st != CT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  if (K == 0) {
+    if (accumulate) return CT_OK;
+    return launch_zero_matrix(C, sizeof(float), ldc, M, N, s);
+  }
+  const int64_t ldk = (K + 7) / 8 * 8;
+  const size_t ha = (size_t)ldk * M, hb = (size_t)ldk * N;
+  Scratch work;
+  if ((st = work.alloc((2 * ha + 2 * hb) * sizeof(__half) + (size_t)N * 16 + 1024, s)) != CT_OK) return st;
+  __half* Ah = (__half*)work.p;
+  __half* Al = Ah + ha;
+  __half* Bh = Al + ha;
+  __half* Bl = Bh + hb;
+  unsigned* bmax = (unsigned*)(((uintptr_t)(Bl + hb) + 15) & ~(uintptr_t)15);
+  // colinv: 16-byte aligned, readable up to N rounded up to 128 entries
+  float* colinv = (float*)(((uintptr_t)(bmax + N) + 15) & ~(uintptr_t)15);
+  double* nacc = (double*)(((uintptr_t)(colinv + N + 128) + 15) & ~(uintptr_t)15);
+  if ((st = launch_split16(A, lda, K, M, nullptr, 8, 0, Ah, Al, ldk, nullptr, s)) != CT_OK) return st;
+  if ((st = launch_colnorm_bound(B, ldb, K, N, nacc, bmax, s)) != CT_OK) return st;
+  if (!accumulate)
+    return tc_gemm16(Ah, Al, ldk, B, nullptr, ldb, bmax, nullptr, M, N, K, 1.f / 256.f, C, ldc, 0, 1, status, s,
+                     nullptr);
+  if ((st = launch_split16(B, ldb, K, N, bmax, 0, 8, Bh, Bl, ldk, colinv, s)) != CT_OK) return st;
+  return tc_update16(Ah, Al, ldk, Bh, Bl, ldk, colinv, M, N, K, C, ldc, di.sms, status, s);
+}
+
 ct_status ct_gemm_status(void* stream) {
   ct_status err = CT_OK;
   int* status = gemm_status_word(&err);
@@ -1109,8 +1169,8 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
   ct_status st = device_info(&di);
   if (st != CT_OK) return st;
   const int bprec = opts ? opts->prec : CT_PREC_F64;
-  if (bprec != CT_PREC_F64 && bprec != CT_PREC_TF32) return CT_ERR_INVALID;
-  if (bprec == CT_PREC_TF32) {
+  if (bprec != CT_PREC_F64 && !tc_prec((ct_prec)bprec)) return CT_ERR_INVALID;
+  if (tc_prec((ct_prec)bprec)) {
     // one system after another through the tensor-core factorization and
     // the FP64 refinement against its own (unchanged) FP64 A
     const auto t0 = std::chrono::steady_clock::now();
@@ -1119,7 +1179,7 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
     for (int i = 0; i < count; ++i) {
       const ct_batch_system& q = systems[i];
       ct_factor* f = nullptr;
-      if ((st = ct_qr_factor(q.A, CT_F64, q.m, q.n, q.lda, CT_PREC_TF32, nullptr, &f, stream)) != CT_OK) return st;
+      if ((st = ct_qr_factor(q.A, CT_F64, q.m, q.n, q.lda, (ct_prec)bprec, nullptr, &f, stream)) != CT_OK) return st;
       if (q.k > 0) {
         Scratch xs;
         if ((st = xs.alloc((size_t)q.n * q.k * sizeof(double), s)) != CT_OK) {

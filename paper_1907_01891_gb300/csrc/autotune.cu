@@ -3,10 +3,11 @@
 // Batched tile QR: for a size class (GPU name, log2 of n, rows-per-column
 // ratio in quarters) the tuner factors one synthetic system of that size with
 // each candidate tile (32 and 64) and keeps the faster.
-// Tensor-core factorization (CT_PREC_TF32): for a size class (GPU name, log2
-// of m and n, 3xTF32 or plain TF32) it factors a synthetic m x min(n, 2048)
-// FP32 matrix with each panel width (16, 32) and outer-block width (128,
-// 256) and keeps the fastest pair.
+// Tensor-core factorization: for a size class (GPU name, log2 of m and n,
+// and the product arithmetic: 3xTF32, plain TF32 or the FP16 split) it
+// factors a synthetic m x min(n, 2048) FP32 matrix with each panel width
+// (16, 32) and, for TF32, each outer-block width (128, 256) and keeps the
+// fastest; FP16-split factors keep 256-column outer blocks.
 // Choices are cached in a small JSON file ($CTQR_TUNE_CACHE, else
 // $HOME/.cache/ctqr_tune.json) so later runs skip the measurement.
 #include <math.h>
@@ -95,9 +96,10 @@ __global__ void k_fill_synthetic_f32(float* A, int64_t lda, int64_t m, int64_t n
 
 }  // namespace
 
-ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, cudaStream_t s, int* nb, int* outer) {
+ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, ct_prec prec, cudaStream_t s, int* nb, int* outer) {
   *nb = 32;
   *outer = 256;
+  const bool f16 = prec == CT_PREC_F16X3;
   const char* off = getenv("CTQR_NO_TUNE");
   if ((off && *off == '1') || n <= 128) return CT_OK;
   cudaDeviceProp prop;
@@ -106,7 +108,10 @@ ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, cudaStream_t s, 
   CT_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
   char key[256];
   const int lm = (int)floor(log2((double)m) + 0.5), ln = (int)floor(log2((double)n) + 0.5);
-  snprintf(key, sizeof(key), "factor_tf32/%s/passes=%d/log2m=%d/log2n=%d", prop.name, passes, lm, ln);
+  if (f16)
+    snprintf(key, sizeof(key), "factor_f16x3/%s/log2m=%d/log2n=%d", prop.name, lm, ln);
+  else
+    snprintf(key, sizeof(key), "factor_tf32/%s/passes=%d/log2m=%d/log2n=%d", prop.name, passes, lm, ln);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     load_cache();
@@ -148,10 +153,14 @@ ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, cudaStream_t s, 
     for (int cand_nb : {16, 32}) {
       for (int cand_outer : {128, 256}) {
         if (round == 0 && !(cand_nb == 32 && cand_outer == 256)) continue;
-        ct_qr_opts o = {cand_nb, 0, passes, cand_outer};
+        // FP16-split factors keep 256-column outer blocks: on the proxy's
+        // 2048 columns 128 can look as fast, but on a wide matrix 256 halves
+        // the passes over the trailing matrix, which bound these updates
+        if (f16 && cand_outer != 256) continue;
+        ct_qr_opts o = {cand_nb, 0, f16 ? 0 : passes, cand_outer};
         ct_factor* f = nullptr;
         CT_CUDA_TRY(cudaEventRecord(e0, s));
-        ct_status st = ct_qr_factor(A, CT_F32, m, nt, lda, CT_PREC_TF32, &o, &f, s);
+        ct_status st = ct_qr_factor(A, CT_F32, m, nt, lda, f16 ? CT_PREC_F16X3 : CT_PREC_TF32, &o, &f, s);
         if (st != CT_OK) return st;
         CT_CUDA_TRY(cudaEventRecord(e1, s));
         CT_CUDA_TRY(cudaEventSynchronize(e1));

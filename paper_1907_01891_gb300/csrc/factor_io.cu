@@ -136,9 +136,9 @@ ct_status read_header(FILE* fp, FileHeader* hd) {
   if (memcmp(hd->magic, kMagic, 8) != 0 || hd->version != kVersion || hd->header_bytes != sizeof(*hd))
     return CT_ERR_INVALID;
   if (hd->n < 1 || hd->m < hd->n || hd->nb < 1 || hd->nb > 64) return CT_ERR_INVALID;
-  if (hd->prec != CT_PREC_F64 && hd->prec != CT_PREC_F32 && hd->prec != CT_PREC_TF32) return CT_ERR_INVALID;
+  if (hd->prec != CT_PREC_F64 && hd->prec != CT_PREC_F32 && !tc_prec((ct_prec)hd->prec)) return CT_ERR_INVALID;
   if (hd->store != (hd->prec == CT_PREC_F64 ? CT_F64 : CT_F32)) return CT_ERR_INVALID;
-  if (hd->has_blocks != (hd->prec == CT_PREC_TF32 ? 1 : 0)) return CT_ERR_INVALID;
+  if (hd->has_blocks != (tc_prec((ct_prec)hd->prec) ? 1 : 0)) return CT_ERR_INVALID;
   return CT_OK;
 }
 

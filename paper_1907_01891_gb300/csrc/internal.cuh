@@ -165,6 +165,10 @@ struct ct_factor {
 
 namespace ctqr {
 
+// Factors whose outer trailing updates run on the tensor cores (two-level
+// factors with per-128-column V^T V and T blocks).
+inline bool tc_prec(ct_prec p) { return p == CT_PREC_TF32 || p == CT_PREC_F16X3; }
+
 int64_t npanels(const ct_factor* f);
 // Release a factor and every buffer it owns (no synchronisation).
 void free_factor(ct_factor* f);
@@ -269,6 +273,26 @@ ct_status outer_block_update(ct_factor* f, int64_t J, int nbo, float* work, size
 // 256) floats.
 ct_status outer_block_update256(ct_factor* f, int64_t J, int nbo_b, float* work, size_t work_floats, int sms,
                                 bool split3, cudaStream_t s, Lookahead* la);
+// ---- FP16-split outer updates (outer_update.cu, tc_f16.cu) ----------------
+// Per-column bounds (float bits) on the trailing matrix's magnitudes: each
+// column's 2-norm over the rows from the current outer block's first row
+// down, which the orthogonal updates preserve, so it bounds every entry below
+// any later block's first row.  The first block's come from one pass over the
+// matrix; each later block's from the sums of squares that the previous
+// block's V^T C product forms while it splits the trailing matrix (acc).
+// bound and acc hold n entries each.
+struct F16Cols {
+  unsigned* bound = nullptr;
+  double* acc = nullptr;
+};
+size_t outer_work_floats16(int sms, int64_t m, int64_t n, int width);
+// cs->bound = the column norms of the FP32 factored matrix (the first block's).
+ct_status f16_bounds(ct_factor* f, F16Cols* cs, cudaStream_t s);
+// As outer_block_update / outer_block_update256 with the FP16-split products.
+ct_status outer_update16(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
+                         cudaStream_t s, Lookahead* la, int64_t cend, const F16Cols* cs);
+ct_status outer_update256_16(ct_factor* f, int64_t J, int nbo_b, float* work, size_t work_floats, int sms,
+                             cudaStream_t s, Lookahead* la, const F16Cols* cs);
 // Whether a panel of mr rows and nbp columns fits on `ctas` CTAs (qr_panel.cu).
 bool panel_fits_ctas(int64_t mr, int nbp, int ctas, const DeviceInfo& di);
 ct_status launch_zero_matrix(void* A, size_t elem, int64_t lda, int64_t rows, int64_t cols,
@@ -335,17 +359,44 @@ ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int
 // Tile tasks the batch would hold with tile size b (each task is ~100 bytes
 // of host and device memory).
 int64_t batch_task_count(int count, const ct_batch_system* in, int b);
-// Panel width and outer-block width of a CT_PREC_TF32 factorization of an
-// m x n matrix with `passes` TF32 passes: cached choice, or measured now on a
-// synthetic matrix (CTQR_NO_TUNE=1: the defaults 32 and 256).
-ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, cudaStream_t s, int* nb, int* outer);
+// Panel width and outer-block width of a tensor-core factorization of an
+// m x n matrix (CT_PREC_TF32 with `passes` TF32 passes, or CT_PREC_F16X3,
+// whose outer width stays 256): cached choice, or measured now on a synthetic
+// matrix (CTQR_NO_TUNE=1: the defaults 32 and 256).
+ct_status tuned_factor_widths(int64_t m, int64_t n, int passes, ct_prec prec, cudaStream_t s, int* nb, int* outer);
 // Tile size for systems of this shape: cached choice, or measured now.
 ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* tile);
 
 // ---- surrogate convolutions on the tensor cores (conv_tc.cu) -------------
 }  // namespace ctqr
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 namespace ctqr {
+// ---- FP16-split tensor-core products (tc_f16.cu) ---------------------------
+// W (M x N) = A^T B with A (K x M) given as FP16 parts Ah + Al (ld lda, a
+// multiple of 8) and B either FP32 (Bl == NULL; ldb a multiple of 4; split
+// on chip with per-column scales from bmax, bounds on its columns'
+// magnitudes as float bits) or FP16 parts (Bh, Bl; ldb a multiple of 8); every output
+// multiplied by out_scale (and by the inverse column scale for FP32 B).
+// Split z of `splits` over K writes C + z * split_stride; *made = splits made.
+ct_status tc_gemm16(const __half* Ah, const __half* Al, int64_t lda, const void* Bh, const __half* Bl, int64_t ldb,
+                    const unsigned* bmax, double* nrm2, int64_t M, int64_t N, int64_t K, float out_scale, float* C,
+                    int64_t ldc, int64_t split_stride, int splits, int* status, cudaStream_t s, int* made);
+// C (M x N) -= colinv[c] * (A^T B)[:, c] on FP16 parts (ld multiples of 8,
+// K <= 256; colinv 16-byte aligned and readable up to N rounded up to 128).
+ct_status tc_update16(const __half* Ah, const __half* Al, int64_t lda, const __half* Bh, const __half* Bl, int64_t ldb,
+                      const float* colinv, int64_t M, int64_t N, int64_t K, float* C, int64_t ldc, int sms, int* status,
+                      cudaStream_t s);
+// bound[c] = bits of a float above sqrt(nrm2[c]).
+ct_status launch_norm_bound(const double* nrm2, int64_t cols, unsigned* bound, cudaStream_t s);
+// bound[c] = bits of a float above ||X[0:rows, c]||_2 (acc: cols doubles of scratch).
+ct_status launch_colnorm_bound(const float* X, int64_t ldx, int64_t rows, int64_t cols, double* acc, unsigned* bound,
+                               cudaStream_t s);
+// FP16 parts H + L = s X (K x cols, ld ldo) with s = 2^exp_fixed, or per column
+// from cmax (a bound on its magnitudes, below 2^14 after scaling);
+// colinv[c] = 1 / (s_c 2^extra_exp).
+ct_status launch_split16(const float* X, int64_t ldx, int64_t K, int64_t cols, const unsigned* cmax, int exp_fixed,
+                         int extra_exp, __half* H, __half* L, int64_t ldo, float* colinv, cudaStream_t s);
 ct_status launch_conv_tc(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, int H, int W, int64_t B,
                          const __nv_bfloat16* res, __nv_bfloat16* r_out, __nv_bfloat16* a_out, int* status,
                          cudaStream_t s);

@@ -16,6 +16,10 @@
 // This is the paper's Apply_left_Qt_of_dense_QR with its "S factor"
 // (Sec. II-C-3) applied to a 128-column block at once, so C is read and
 // written once per 128 columns instead of once per 32.
+#include <cuda_fp16.h>
+
+#include <utility>
+
 #include "internal.cuh"
 
 namespace ctqr {
@@ -795,6 +799,443 @@ ct_status apply_qt_outer_persist(const ct_factor* f, float* C, int64_t ldc, int6
                  2.0 * (double)nblk * kNB * (double)f->m * 4.0);
   CT_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
   return CT_OK;
+}
+
+}  // namespace ctqr
+
+namespace ctqr {
+
+// ---------------------------------------------------------------------------
+// The same outer-block updates with the operands of the two tensor-core
+// products split into two FP16 parts (tc_f16.cu): V scaled by 2^kVExp16, W'
+// and the trailing matrix per column.  The trailing matrix's per-column
+// scales come from bounds on its columns' magnitudes (F16Cols: column
+// 2-norms, which the orthogonal updates keep; the V^T C product of each
+// block sums the squares it splits, giving the next block's bounds).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kVExp16 = 8;
+
+// Vc16 (column-major, ld ldv) and Vr16 (row-major, row stride W) get the FP16
+// parts of the explicit reflectors scaled by 2^kVExp16 (see k_extract_v);
+// |v| >= 192 (which would leave FP16's range) is recorded as non-finite.
+template <int W>
+__global__ void __launch_bounds__(256) k_extract_v16(const float* __restrict__ F, int64_t ld, int64_t mr, int nbo,
+                                                     __half* __restrict__ Vch, __half* __restrict__ Vcl, int64_t ldv,
+                                                     __half* __restrict__ Vrh, __half* __restrict__ Vrl, int* status) {
+  __shared__ float tile[32][W + 1];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const float s = (float)(1 << kVExp16);
+  bool bad = false;
+  for (int e = threadIdx.x; e < 32 * W; e += 256) {
+    const int rr = e % 32, a = e / 32;
+    const int64_t r = r0 + rr;
+    float v = 0.f;
+    if (r < mr && a < nbo) v = r > a ? F[r + (int64_t)a * ld] : (r == a ? 1.f : 0.f);
+    bad |= !(fabsf(v) < 192.f);
+    tile[rr][a] = v;
+    if (r < mr) {
+      const float xs = v * s;
+      const __half h = __float2half_rn(xs);
+      Vch[r + (int64_t)a * ldv] = h;
+      Vcl[r + (int64_t)a * ldv] = __float2half_rn(xs - __half2float(h));
+    }
+  }
+  if (bad) set_status(status, CT_ERR_NONFINITE);
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * W; e += 256) {
+    const int a = e % W, rr = e / W;
+    const int64_t r = r0 + rr;
+    if (r < mr) {
+      const float xs = tile[rr][a] * s;
+      const __half h = __float2half_rn(xs);
+      Vrh[r * W + a] = h;
+      Vrl[r * W + a] = __float2half_rn(xs - __half2float(h));
+    }
+  }
+}
+
+// T (128 x 128, T(k, r) at k + r * kNB) into Ts[k * kNB + r].
+__device__ __forceinline__ void load_t128(const float* __restrict__ T, float* Ts) {
+  for (int e0 = threadIdx.x; e0 < kNB * kNB; e0 += 256 * 16) {
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = __ldcg(T + e0 + 256 * u);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = e0 + 256 * u, k = e % kNB, r = e / kNB;
+      Ts[k * kNB + r] = v[u];
+    }
+  }
+}
+
+// Ws[k * kTC + c] = sum_z Wp[z * wstride + k + (c0 + c) * ldw] (k < 128, c < 64,
+// the splits added in order; zero beyond nc).
+__device__ __forceinline__ void load_w128(const float* __restrict__ Wp, int wsplits, int64_t wstride, int64_t ldw,
+                                          int64_t c0, int64_t nc, float* Ws) {
+#pragma unroll 1
+  for (int hv = 0; hv < 2; ++hv) {
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = 0.f;
+    for (int z = 0; z < wsplits; ++z) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = threadIdx.x + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
+        v[u] += c0 + c < nc ? __ldcg(Wp + z * wstride + k + (c0 + c) * ldw) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = threadIdx.x + 256 * (16 * hv + u), k = e % kNB, c = e / kNB;
+      Ws[k * kTC + c] = v[u];
+    }
+  }
+}
+
+// acc[i][j] += sum_k Ts[k][ty + 16 i] Ws[k][tx * 4 + j]
+__device__ __forceinline__ void tt_product(const float* Ts, const float* Ws, int ty, int tx, float (&acc)[8][4]) {
+#pragma unroll 4
+  for (int k = 0; k < kNB; ++k) {
+    float a[8], b[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = Ts[k * kNB + ty + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Ws[k * kTC + tx * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+}
+
+// W' = T^T W for 64 columns per CTA and all ROWS rows at once -- ROWS = 128:
+// T_A^T W; ROWS = 256: [T_A^T W_A; T_AB^T W_A + T_B^T W_B] -- W summed over
+// its split partials.  Each column c is scaled by 2^e_c (its largest |W'|
+// below 2^14) and written as FP16 parts Wh + Wl (K x N, column stride ldo);
+// winv[c] = 2^-(e_c + kVExp16), the factor the update's epilogue applies.
+template <int ROWS>
+__global__ void __launch_bounds__(256) k_apply_tt16(const float* __restrict__ Wp, int wsplits, int64_t wstride,
+                                                    int64_t ldw, const float* __restrict__ Ta,
+                                                    const float* __restrict__ Tab, const float* __restrict__ Tb,
+                                                    int64_t nc, __half* __restrict__ Wh, __half* __restrict__ Wl,
+                                                    int64_t ldo, float* __restrict__ winv) {
+  extern __shared__ float sm[];
+  float* Ts = sm;               // Ts[k * kNB + r] = T(k, r)
+  float* Ws = Ts + kNB * kNB;   // Ws[k * kTC + c] = W(k, c0 + c)
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * kTC;
+  const int ty = tid % 16, tx = tid / 16;
+  float top[8][4], bot[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) top[i][j] = bot[i][j] = 0.f;
+  load_t128(Ta, Ts);
+  load_w128(Wp, wsplits, wstride, ldw, c0, nc, Ws);
+  __syncthreads();
+  tt_product(Ts, Ws, ty, tx, top);
+  if (ROWS == 256) {
+    __syncthreads();
+    load_t128(Tab, Ts);
+    __syncthreads();
+    tt_product(Ts, Ws, ty, tx, bot);
+    __syncthreads();
+    load_t128(Tb, Ts);
+    load_w128(Wp + kNB, wsplits, wstride, ldw, c0, nc, Ws);
+    __syncthreads();
+    tt_product(Ts, Ws, ty, tx, bot);
+  }
+  // per-column largest |W'| over the ROWS rows: this thread's rows, then the
+  // 16 threads (ty) of the column in this half-warp
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fmaxf(fabsf(top[i][j]), ROWS == 256 ? fabsf(bot[i][j]) : 0.f));
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f && isfinite(mx)) {
+      int ex;
+      frexpf(mx, &ex);
+      e = 14 - ex;
+      e = e < -126 ? -126 : (e > 126 ? 126 : e);
+    }
+    const int64_t c = c0 + tx * 4 + j;
+    if (c >= nc) continue;
+    const float s = ldexpf(1.f, e);
+    if (ty == 0) winv[c] = ldexpf(1.f, -(e + kVExp16));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t o = ty + 16 * i + c * ldo;
+      float xs = top[i][j] * s;
+      __half h = __float2half_rn(xs);
+      Wh[o] = h;
+      Wl[o] = __float2half_rn(xs - __half2float(h));
+      if (ROWS == 256) {
+        xs = bot[i][j] * s;
+        h = __float2half_rn(xs);
+        Wh[o + kNB] = h;
+        Wl[o + kNB] = __float2half_rn(xs - __half2float(h));
+      }
+    }
+  }
+}
+
+int64_t up64(int64_t x) { return (x + 63) / 64 * 64; }
+
+// Sub-buffers of the FP16-split update's workspace (offsets in floats, each a
+// multiple of 64 floats = 256 bytes).
+struct Work16 {
+  __half *vch, *vcl, *vrh, *vrl, *wh, *wl;
+  float *wp, *winv, *gp, *gab, *tab, *ysc;
+  int64_t ldv, wcols;
+  size_t total;
+};
+
+Work16 carve16(float* base, int sms, int64_t m, int64_t n, int width) {
+  Work16 w;
+  const int64_t W = width;
+  w.ldv = (m + 7) / 8 * 8;
+  w.wcols = 8 * n > (int64_t)4 * sms * 128 ? 8 * n : (int64_t)4 * sms * 128;
+  int64_t o = 0;
+  auto take = [&](int64_t floats) {
+    float* p = base ? base + o : nullptr;
+    o += up64(floats);
+    return p;
+  };
+  w.vch = (__half*)take(w.ldv * W / 2);
+  w.vcl = (__half*)take(w.ldv * W / 2);
+  w.vrh = (__half*)take((m * W + 1) / 2);
+  w.vrl = (__half*)take((m * W + 1) / 2);
+  w.wp = take(W * w.wcols);
+  w.wh = (__half*)take((W * n + 1) / 2);
+  w.wl = (__half*)take((W * n + 1) / 2);
+  w.winv = take(n + 128);  // read by whole 128-column tiles
+  w.gp = take((int64_t)(2 * sms + 2) * W * W);
+  w.gab = take((int64_t)kNB * kNB);
+  w.tab = take((int64_t)kNB * kNB);
+  w.ysc = take((int64_t)kNB * kNB);
+  w.total = (size_t)o;
+  return w;
+}
+
+// Split count of W = V^T C over rows: full waves of CTAs, at most wcols / nc
+// partial blocks and 1024 rows per split at least (as outer_block_update).
+int64_t vtc_splits(int64_t mr, int64_t nc, int64_t wcols, int sms) {
+  const int64_t tiles = (nc + 127) / 128;
+  int64_t wsmax = (mr + 1023) / 1024;
+  if (wsmax * nc > wcols) wsmax = wcols / nc;
+  if (wsmax < 1) wsmax = 1;
+  int64_t ws0 = (2 * sms + tiles - 1) / tiles;
+  if (ws0 > wsmax) ws0 = wsmax;
+  if (ws0 < 1) ws0 = 1;
+  int64_t ws = ws0;
+  double best = -1.0;
+  for (int64_t w = ws0; w <= 3 * ws0 && w <= wsmax; ++w) {
+    int64_t chunk = (mr + w - 1) / w;
+    chunk = (chunk + 31) / 32 * 32;
+    const int64_t made = (mr + chunk - 1) / chunk;
+    const int64_t ctas = made * tiles;
+    const double eff = (double)ctas / (double)(sms * ((ctas + sms - 1) / sms));
+    if (eff > best + 0.02) {
+      best = eff;
+      ws = w;
+    }
+  }
+  return ws;
+}
+
+constexpr size_t kApplyTt16Smem = (size_t)(kNB * kNB + kNB * kTC) * sizeof(float);
+
+}  // namespace
+
+size_t outer_work_floats16(int sms, int64_t m, int64_t n, int width) {
+  return carve16(nullptr, sms, m, n, width).total;
+}
+
+ct_status f16_bounds(ct_factor* f, F16Cols* cs, cudaStream_t s) {
+  return launch_colnorm_bound((const float*)f->F, f->ld, f->m, f->n, cs->acc, cs->bound, s);
+}
+
+// 128-column outer block [J, J + nbo) applied to C = F[J:m, J+nbo:cend] with
+// the FP16-split products (cend <= 0: to the last column); cs->bound holds
+// bounds on C's column magnitudes.
+ct_status outer_update16(ct_factor* f, int64_t J, int nbo, float* work, size_t work_floats, int sms,
+                         cudaStream_t s, Lookahead* la, int64_t cend, const F16Cols* cs) {
+  const int64_t m = f->m, n = f->n, mr = m - J, nc = (cend > 0 ? cend : n) - J - nbo;
+  if (nc <= 0) return CT_OK;
+  if (!f->Gblk || !f->Tblk || !cs) return CT_ERR_INVALID;
+  const Work16 w = carve16(work, sms, m, n, kNB);
+  if (w.total > work_floats) return CT_ERR_INVALID;
+  float* F = (float*)f->F;
+  const int64_t ld = f->ld;
+  {
+    LaunchScope ls(K_COPY, s, 0.0, (double)mr * kNB * 12);
+    k_extract_v16<kNB><<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, w.vch, w.vcl, w.ldv,
+                                                                   w.vrh, w.vrl, f->status);
+    CT_LAUNCH_CHECK();
+  }
+  ct_status st;
+  // G = V^T V (128 x 128), split over rows
+  int gs = (int)((mr + 2047) / 2048);
+  if (gs > 2 * sms) gs = 2 * sms;
+  if (gs < 1) gs = 1;
+  const float vinv2 = 1.f / (float)(1 << (2 * kVExp16));
+  if ((st = tc_gemm16(w.vch, w.vcl, w.ldv, w.vch, w.vcl, w.ldv, nullptr, nullptr, kNB, kNB, mr, vinv2, w.gp, kNB,
+                      (int64_t)kNB * kNB, gs, f->status, s, &gs)) != CT_OK)
+    return st;
+  float* Gred = f->Gblk + (size_t)(J / kNB) * kNB * kNB;
+  {
+    LaunchScope ls(K_TW, s, (double)kNB * kNB * gs, 4.0 * kNB * kNB * (gs + 1));
+    k_reduce_gram<<<kNB * kNB / 256, 256, 0, s>>>(w.gp, gs, (int64_t)kNB * kNB, nbo, Gred);
+    CT_LAUNCH_CHECK();
+  }
+  float* Tb = f->Tblk + (size_t)(J / kNB) * kNB * kNB;
+  const bool side = la && la->s3;
+  {
+    static bool attr = false;
+    if (!attr) {
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt16<kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kApplyTt16Smem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt16<2 * kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kApplyTt16Smem));
+      attr = true;
+    }
+    cudaStream_t st_t = s;
+    if (side) {
+      CT_CUDA_TRY(cudaEventRecord(la->ev_g, s));
+      CT_CUDA_TRY(cudaStreamWaitEvent(la->s3, la->ev_g, 0));
+      st_t = la->s3;
+    }
+    LaunchScope ls(K_TINV, st_t, (double)kNB * kNB * kNB / 3.0, 8.0 * kNB * kNB);
+    k_tinv<<<1, kTinvThreads, kTinvSmem, st_t>>>(Gred, f->tau + J, nbo, Tb);
+    CT_LAUNCH_CHECK();
+    if (side) CT_CUDA_TRY(cudaEventRecord(la->ev_t, la->s3));
+  }
+  // W = V^T C (128 x nc), C split in shared memory with its column scales;
+  // for a whole trailing matrix (cend <= 0) the split also sums each
+  // column's squares, the next block's bounds
+  float* C = F + J + (J + nbo) * ld;
+  const bool last = cend <= 0;
+  if (last) CT_CUDA_TRY(cudaMemsetAsync(cs->acc + J + nbo, 0, (size_t)nc * sizeof(double), s));
+  int ws = (int)vtc_splits(mr, nc, w.wcols, sms);
+  if ((st = tc_gemm16(w.vch, w.vcl, w.ldv, C, nullptr, ld, cs->bound + J + nbo, last ? cs->acc + J + nbo : nullptr,
+                      kNB, nc, mr, 1.f / (float)(1 << kVExp16), w.wp, kNB, (int64_t)kNB * nc, ws, f->status, s,
+                      &ws)) != CT_OK) {
+    if (side) cudaStreamWaitEvent(s, la->ev_t, 0);
+    return st;
+  }
+  if (last && (st = launch_norm_bound(cs->acc + J + nbo, nc, cs->bound + J + nbo, s)) != CT_OK) {
+    if (side) cudaStreamWaitEvent(s, la->ev_t, 0);
+    return st;
+  }
+  if (side) CT_CUDA_TRY(cudaStreamWaitEvent(s, la->ev_t, 0));
+  {
+    LaunchScope ls(K_TW, s, 2.0 * kNB * kNB * nc, 4.0 * kNB * nc * (ws + 1));
+    k_apply_tt16<kNB><<<(unsigned)((nc + kTC - 1) / kTC), 256, kApplyTt16Smem, s>>>(
+        w.wp, ws, (int64_t)kNB * nc, kNB, Tb, nullptr, nullptr, nc, w.wh, w.wl, kNB, w.winv);
+    CT_LAUNCH_CHECK();
+  }
+  return tc_update16(w.vrh, w.vrl, kNB, w.wh, w.wl, kNB, w.winv, mr, nc, kNB, C, ld, sms, f->status, s);
+}
+
+// The 256-column update (see outer_block_update256) with the FP16-split
+// products; cs->bound holds bounds on the trailing columns' magnitudes.
+ct_status outer_update256_16(ct_factor* f, int64_t J, int nbo_b, float* work, size_t work_floats, int sms,
+                             cudaStream_t s, Lookahead* la, const F16Cols* cs) {
+  constexpr int kW = 2 * kNB;
+  const int nbo = kNB + nbo_b;
+  const int64_t m = f->m, n = f->n, mr = m - J, nc = n - J - nbo;
+  if (nbo_b < 1 || nbo_b > kNB) return CT_ERR_INVALID;
+  if (nc <= 0) return CT_OK;
+  if (!f->Gblk || !f->Tblk || !cs) return CT_ERR_INVALID;
+  const Work16 w = carve16(work, sms, m, n, kW);
+  if (w.total > work_floats) return CT_ERR_INVALID;
+  float* F = (float*)f->F;
+  const int64_t ld = f->ld;
+  {
+    LaunchScope ls(K_COPY, s, 0.0, (double)mr * kW * 12);
+    k_extract_v16<kW><<<(unsigned)((mr + 31) / 32), 256, 0, s>>>(F + J + J * ld, ld, mr, nbo, w.vch, w.vcl, w.ldv,
+                                                                  w.vrh, w.vrl, f->status);
+    CT_LAUNCH_CHECK();
+  }
+  ct_status st;
+  // [V_A^T V_B; V_B^T V_B] (256 x 128), split over rows
+  int gs = (int)((mr + 2047) / 2048);
+  if (gs > 2 * sms) gs = 2 * sms;
+  if (gs < 1) gs = 1;
+  const float vinv2 = 1.f / (float)(1 << (2 * kVExp16));
+  if ((st = tc_gemm16(w.vch, w.vcl, w.ldv, w.vch + (size_t)kNB * w.ldv, w.vcl + (size_t)kNB * w.ldv, w.ldv, nullptr,
+                      nullptr, kW, kNB, mr, vinv2, w.gp, kW, (int64_t)kW * kNB, gs, f->status, s, &gs)) != CT_OK)
+    return st;
+  const int64_t hb = J / kNB + 1;
+  float* Gb = f->Gblk + (size_t)hb * kNB * kNB;
+  float* Tb = f->Tblk + (size_t)hb * kNB * kNB;
+  const float* Ta = f->Tblk + (size_t)(hb - 1) * kNB * kNB;
+  {
+    LaunchScope ls(K_TW, s, 2.0 * kNB * kNB * gs, 8.0 * kNB * kNB * (gs + 1));
+    k_reduce_block<<<kNB * kNB / 256, 256, 0, s>>>(w.gp, gs, (int64_t)kW * kNB, kW, kNB, kNB, kNB, nbo_b, nbo_b, 1,
+                                                   Gb, kNB);
+    CT_LAUNCH_CHECK();
+    k_reduce_block<<<kNB * kNB / 256, 256, 0, s>>>(w.gp, gs, (int64_t)kW * kNB, kW, 0, kNB, kNB, kNB, nbo_b, 0,
+                                                   w.gab, kNB);
+    CT_LAUNCH_CHECK();
+  }
+  const bool side = la && la->s3;
+  {
+    static bool attr = false;
+    if (!attr) {
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt16<kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kApplyTt16Smem));
+      CT_CUDA_TRY(cudaFuncSetAttribute(k_apply_tt16<kW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kApplyTt16Smem));
+      attr = true;
+    }
+    cudaStream_t st_t = s;
+    if (side) {
+      CT_CUDA_TRY(cudaEventRecord(la->ev_g, s));
+      CT_CUDA_TRY(cudaStreamWaitEvent(la->s3, la->ev_g, 0));
+      st_t = la->s3;
+    }
+    LaunchScope ls(K_TINV, st_t, (double)kNB * kNB * kNB / 3.0 + 4.0 * kNB * kNB * kNB, 8.0 * kNB * kNB * 4);
+    k_tinv<<<1, kTinvThreads, kTinvSmem, st_t>>>(Gb, f->tau + J + kNB, nbo_b, Tb);
+    CT_LAUNCH_CHECK();
+    k_small_gemm128<<<dim3(kNB / 16, kNB / 16), 256, 0, st_t>>>(w.gab, Tb, 1.f, w.ysc);
+    CT_LAUNCH_CHECK();
+    k_small_gemm128<<<dim3(kNB / 16, kNB / 16), 256, 0, st_t>>>(Ta, w.ysc, -1.f, w.tab);
+    CT_LAUNCH_CHECK();
+    if (side) CT_CUDA_TRY(cudaEventRecord(la->ev_t, la->s3));
+  }
+  // W = V^T C (256 x nc): each CTA covers both halves' reflectors, so C is
+  // read and split once per slice
+  float* C = F + J + (J + nbo) * ld;
+  CT_CUDA_TRY(cudaMemsetAsync(cs->acc + J + nbo, 0, (size_t)nc * sizeof(double), s));
+  int ws = (int)vtc_splits(mr, nc, w.wcols, sms);
+  if ((st = tc_gemm16(w.vch, w.vcl, w.ldv, C, nullptr, ld, cs->bound + J + nbo, cs->acc + J + nbo, kW, nc, mr,
+                      1.f / (float)(1 << kVExp16), w.wp, kW, (int64_t)kW * nc, ws, f->status, s, &ws)) != CT_OK) {
+    if (side) cudaStreamWaitEvent(s, la->ev_t, 0);
+    return st;
+  }
+  // the next block's bounds: these columns' norms over rows J.. (kept by
+  // the update below, which is orthogonal on those rows)
+  if ((st = launch_norm_bound(cs->acc + J + nbo, nc, cs->bound + J + nbo, s)) != CT_OK) {
+    if (side) cudaStreamWaitEvent(s, la->ev_t, 0);
+    return st;
+  }
+  if (side) CT_CUDA_TRY(cudaStreamWaitEvent(s, la->ev_t, 0));
+  {
+    LaunchScope ls(K_TW, s, 2.0 * kW * kNB * nc * 1.5, 4.0 * kW * nc * (ws + 1));
+    k_apply_tt16<kW><<<(unsigned)((nc + kTC - 1) / kTC), 256, kApplyTt16Smem, s>>>(
+        w.wp, ws, (int64_t)kW * nc, kW, Ta, w.tab, Tb, nc, w.wh, w.wl, kW, w.winv);
+    CT_LAUNCH_CHECK();
+  }
+  // C -= V W'  (K = 256)
+  return tc_update16(w.vrh, w.vrl, kW, w.wh, w.wl, kW, w.winv, mr, nc, kW, C, ld, sms, f->status, s);
 }
 
 }  // namespace ctqr

@@ -26,6 +26,7 @@ class Prec(enum.IntEnum):
     F64 = 0
     F32 = 1
     TF32 = 2
+    F16X3 = 3
 
 
 class CtError(RuntimeError):
@@ -134,6 +135,7 @@ SIGNATURES = {
     "ct_reconstruct_scan": ([ctypes.POINTER(Geometry), _D, _I, _VP, _I64, _VP, _I64, _I64, _I,
                              ctypes.POINTER(RefineOpts), ctypes.POINTER(Report), _VP], _I),
     "ct_gemm_tf32_tn": ([_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _I, _I, _VP], _I),
+    "ct_gemm_f16x3_tn": ([_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _I, _VP], _I),
     "ct_gemm_status": ([_VP], _I),
     "ct_qr_solve_batched": ([_I, ctypes.POINTER(BatchSystem), ctypes.POINTER(BatchOpts),
                              ctypes.POINTER(BatchReport), _VP], _I),
@@ -491,6 +493,19 @@ def gemm_tf32_tn(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None
         C = colmajor(M, N, dtype=torch.float32)
     _check(load().ct_gemm_tf32_tn(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
                                   1 if accumulate else 0, 1 if split3 else 0, _stream()), "ct_gemm_tf32_tn")
+    return C
+
+
+def gemm_f16x3_tn(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None,
+                  accumulate: bool = False) -> torch.Tensor:
+    """C = A^T B (or C -= A^T B) on the tensor cores with the operands split
+    into two FP16 parts each; A is K x M, B is K x N, FP32 column-major."""
+    K, M = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = colmajor(M, N, dtype=torch.float32)
+    _check(load().ct_gemm_f16x3_tn(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                                   1 if accumulate else 0, _stream()), "ct_gemm_f16x3_tn")
     return C
 
 

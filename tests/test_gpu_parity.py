@@ -281,9 +281,10 @@ def test_reconstruct_scan_host_and_device_buffers_agree():
 
 
 # ---------------------------------------------------------------- tensor-core factor
+@pytest.mark.parametrize("prec", [ctqr.Prec.TF32, ctqr.Prec.F16X3], ids=["tf32x3", "f16x3"])
 @pytest.mark.parametrize("shape", [(300, 200), (700, 300), (1000, 513), (49000, 150), (90000, 150)])
-def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape):
-    """3xTF32 outer updates give an FP32-quality factor (R within ~1e-4 of the
+def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape, prec):
+    """3xTF32 (or FP16-split) outer updates give an FP32-quality factor (R within ~1e-4 of the
     oracle's, relative to max |R|); refinement then reaches the 1e-10 target.
     The inner panels' updates run as one cooperative launch each while every
     SM's share of the rows fits 320 (the 49000- and 90000-row cases take the
@@ -297,7 +298,7 @@ def test_tf32_factor_is_close_to_oracle_and_refines_to_fp64(shape):
     torch.cuda.synchronize()
     ctqr.profile_reset()
     ctqr.profile_enable(True)
-    f = ctqr.qr_factor(Af, prec=ctqr.Prec.TF32, nb=32)  # explicit width: no tuning runs inside
+    f = ctqr.qr_factor(Af, prec=prec, nb=32)  # explicit width: no tuning runs inside
     torch.cuda.synchronize()
     ctqr.profile_enable(False)
     launches = {p_["name"]: p_["launches"] for p_ in ctqr.profile_kernels()}
@@ -333,19 +334,20 @@ def test_tf32_single_pass_option_is_less_accurate_but_refines():
     assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
 
 
-def test_tf32_ct_reconstruction_config1_and_noisy_subset():
+@pytest.mark.parametrize("prec", [ctqr.Prec.TF32, ctqr.Prec.F16X3], ids=["tf32x3", "f16x3"])
+def test_tf32_ct_reconstruction_config1_and_noisy_subset(prec):
     g = I.CONFIG1["geom"]
     A = ctqr.build_system(g, torch.float64)
     Anp = _np(A)
     b = np.hstack([Anp @ I.phantoms(g, [1]),
                    I.poisson_noise(Anp @ I.phantoms(g, [1001, 1002]), g.fov, 1e4, seed=9)])
-    f = ctqr.qr_factor(A.to(torch.float32), prec=ctqr.Prec.TF32)
+    f = ctqr.qr_factor(A.to(torch.float32), prec=prec)
     X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A)
     Xo = O.lstsq(Anp, b)
     assert np.linalg.norm(_np(X) - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
 
 
-@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.F32, ctqr.Prec.TF32])
+@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.F32, ctqr.Prec.TF32, ctqr.Prec.F16X3])
 def test_lambda_stacked_scan_matches_oracle(prec):
     """[A; lambda I] x = [b; 0] with a rank-deficient A (fan beam with 1.06
     rays per pixel): the stacked system is full rank and every precision path
@@ -389,8 +391,9 @@ def test_fp32_triangular_solve_matches_oracle(n, k, transpose):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("prec", [ctqr.Prec.TF32, ctqr.Prec.F16X3], ids=["tf32x3", "f16x3"])
 @pytest.mark.parametrize("shape,k", [((700, 300), 3), ((1200, 520), 17)])
-def test_tf32_factor_qt_by_outer_blocks(shape, k):
+def test_tf32_factor_qt_by_outer_blocks(shape, k, prec):
     """Q^T of a two-level TF32 factor is applied by 128-column outer blocks
     (the block reflector through S = diag(1/tau) + striu(V^T V)); it matches
     the oracle's Q^T to the factor's FP32-level accuracy, and the per-panel
@@ -398,7 +401,7 @@ def test_tf32_factor_qt_by_outer_blocks(shape, k):
     m, n = shape
     A = I.random_matrix(m, n, seed=90 + n)
     B = I.random_matrix(m, k, seed=91 + n)
-    f = ctqr.qr_factor(ctqr.to_colmajor(A, dtype=torch.float32), prec=ctqr.Prec.TF32)
+    f = ctqr.qr_factor(ctqr.to_colmajor(A, dtype=torch.float32), prec=prec)
     Y = _np(ctqr.apply_qt(f, ctqr.to_colmajor(B)))
     Yp = _np(ctqr.apply_qt_noalloc(f, ctqr.to_colmajor(B)))
     Fo, tau = O.qr(A)
@@ -415,7 +418,8 @@ def test_tf32_factor_qt_by_outer_blocks(shape, k):
 
 @pytest.mark.parametrize("prec,shape,k", [(ctqr.Prec.TF32, (1200, 520), 17), (ctqr.Prec.TF32, (700, 300), 3),
                                           (ctqr.Prec.TF32, (700, 300), 40), (ctqr.Prec.TF32, (24500, 260), 5),
-                                          (ctqr.Prec.F32, (500, 200), 4)])
+                                          (ctqr.Prec.F32, (500, 200), 4), (ctqr.Prec.F16X3, (1200, 520), 17),
+                                          (ctqr.Prec.F16X3, (24500, 260), 5)])
 def test_fp32_qt_matches_oracle_with_the_factors_reflectors(prec, shape, k):
     """ct_apply_qt_f32 (Q^T B in FP32, the refinement's first solve) against
     the oracle's reflector-by-reflector Q^T built from the factor's own V and
@@ -440,7 +444,7 @@ def test_fp32_qt_matches_oracle_with_the_factors_reflectors(prec, shape, k):
     Y = _np(Bg).astype(np.float64)
     assert np.linalg.norm(Y - Yo) <= 2e-5 * np.linalg.norm(B), np.linalg.norm(Y - Yo) / np.linalg.norm(B)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    one_launch = prec == ctqr.Prec.TF32 and k <= 32 and -(-m // sms) <= 160 and n > 128
+    one_launch = prec in (ctqr.Prec.TF32, ctqr.Prec.F16X3) and k <= 32 and -(-m // sms) <= 160 and n > 128
     assert launches.get("qt_outer", 0) == (1 if one_launch else 0), launches
 
 
@@ -490,8 +494,9 @@ def test_refinement_cap_reports_noconverge():
     assert np.all(np.isfinite(_np(X)))
 
 
+@pytest.mark.parametrize("prec", [ctqr.Prec.TF32, ctqr.Prec.F16X3], ids=["tf32x3", "f16x3"])
 @pytest.mark.parametrize("shape", [(400, 200), (900, 300), (1500, 700), (3000, 1100)])
-def test_tf32_outer_blocks_of_256_and_128_agree_and_refine(shape):
+def test_tf32_outer_blocks_of_256_and_128_agree_and_refine(shape, prec):
     """The trailing update with 256-column outer blocks (two 128-column
     halves merged into one compact-WY reflector, T = [[T_A, T_AB], [0, T_B]])
     against 128-column blocks: both R factors are FP32-quality copies of the
@@ -506,7 +511,7 @@ def test_tf32_outer_blocks_of_256_and_128_agree_and_refine(shape):
     b = A @ I.random_matrix(n, 2, seed=401)
     Xo = O.lstsq(A, b)
     for outer in (128, 256):
-        f = ctqr.qr_factor(At.to(torch.float32), prec=ctqr.Prec.TF32, outer_nb=outer)
+        f = ctqr.qr_factor(At.to(torch.float32), prec=prec, outer_nb=outer)
         assert f.status() == ctqr.CT_OK
         F, _ = ctqr.factor_matrix(f)
         R = np.triu(_np(F).astype(np.float64)[:n])

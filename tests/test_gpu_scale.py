@@ -56,7 +56,8 @@ def test_fan72_fp64_path_matches_oracle(fan72):
     assert ok, e
 
 
-def test_fan72_tf32_path_crosses_every_threshold_and_matches_oracle(fan72):
+@pytest.mark.parametrize("prec", [ctqr.Prec.TF32, ctqr.Prec.F16X3], ids=["tf32x3", "f16x3"])
+def test_fan72_tf32_path_crosses_every_threshold_and_matches_oracle(fan72, prec):
     g, Ao, b, Xo = fan72
     m, n = g.m, g.n
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -67,7 +68,7 @@ def test_fan72_tf32_path_crosses_every_threshold_and_matches_oracle(fan72):
     torch.cuda.synchronize()
     ctqr.profile_reset()
     ctqr.profile_enable(True)
-    f = ctqr.qr_factor(A32, ctqr.Prec.TF32)
+    f = ctqr.qr_factor(A32, prec)
     X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=A64)
     torch.cuda.synchronize()
     ctqr.profile_enable(False)
@@ -94,7 +95,7 @@ def tall():
     return A, np.asfortranarray(b), Xo
 
 
-@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.TF32])
+@pytest.mark.parametrize("prec", [ctqr.Prec.F64, ctqr.Prec.TF32, ctqr.Prec.F16X3])
 def test_tall_135232_rows_matches_oracle(tall, prec):
     A, b, Xo = tall
     At = ctqr.to_colmajor(A)
@@ -102,7 +103,7 @@ def test_tall_135232_rows_matches_oracle(tall, prec):
         f = ctqr.qr_factor(At)
         X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b))
     else:
-        f = ctqr.qr_factor(At.to(torch.float32), ctqr.Prec.TF32)
+        f = ctqr.qr_factor(At.to(torch.float32), prec)
         X, rep = ctqr.reconstruct(f, ctqr.to_colmajor(b), A=At)
     assert f.status() == ctqr.CT_OK
     ok, e = _close(_np(X), Xo)
@@ -126,7 +127,8 @@ def test_config4a_512_right_hand_sides_in_one_call():
     assert ok, e
     x1, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b[:, 311:312]))
     assert np.abs(_np(x1)[:, 0] - _np(X)[:, 311]).max() <= 1e-13 * np.abs(_np(X)[:, 311]).max()
-    ft = ctqr.qr_factor(A.to(torch.float32), ctqr.Prec.TF32)
-    Xt, rep = ctqr.reconstruct(ft, ctqr.to_colmajor(b), A=A)
-    ok, e = _close(_np(Xt), Xo)
-    assert ok, (e, rep)
+    for prec in (ctqr.Prec.TF32, ctqr.Prec.F16X3):
+        ft = ctqr.qr_factor(A.to(torch.float32), prec)
+        Xt, rep = ctqr.reconstruct(ft, ctqr.to_colmajor(b), A=A)
+        ok, e = _close(_np(Xt), Xo)
+        assert ok, (prec, e, rep)
