@@ -382,6 +382,8 @@ namespace ctqr {
 ct_status tc_gemm16(const __half* Ah, const __half* Al, int64_t lda, const void* Bh, const __half* Bl, int64_t ldb,
                     const unsigned* bmax, double* nrm2, int64_t M, int64_t N, int64_t K, float out_scale, float* C,
                     int64_t ldc, int64_t split_stride, int splits, int* status, cudaStream_t s, int* made);
+// CTAs tc_gemm16 puts on the M rows of one column tile for FP32 B.
+int tc_gemm16_m_ctas(int64_t M);
 // C (M x N) -= colinv[c] * (A^T B)[:, c] on FP16 parts (ld multiples of 8,
 // K <= 256; colinv 16-byte aligned and readable up to N rounded up to 128).
 ct_status tc_update16(const __half* Ah, const __half* Al, int64_t lda, const __half* Bh, const __half* Bl, int64_t ldb,

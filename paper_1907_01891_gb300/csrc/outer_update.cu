@@ -1024,8 +1024,8 @@ Work16 carve16(float* base, int sms, int64_t m, int64_t n, int width) {
 
 // Split count of W = V^T C over rows: full waves of CTAs, at most wcols / nc
 // partial blocks and 1024 rows per split at least (as outer_block_update).
-int64_t vtc_splits(int64_t mr, int64_t nc, int64_t wcols, int sms) {
-  const int64_t tiles = (nc + 127) / 128;
+int64_t vtc_splits(int64_t mr, int64_t nc, int64_t wcols, int sms, int m_ctas) {
+  const int64_t tiles = m_ctas * ((nc + 127) / 128);
   int64_t wsmax = (mr + 1023) / 1024;
   if (wsmax * nc > wcols) wsmax = wcols / nc;
   if (wsmax < 1) wsmax = 1;
@@ -1122,7 +1122,7 @@ ct_status outer_update16(ct_factor* f, int64_t J, int nbo, float* work, size_t w
   float* C = F + J + (J + nbo) * ld;
   const bool last = cend <= 0;
   if (last) CT_CUDA_TRY(cudaMemsetAsync(cs->acc + J + nbo, 0, (size_t)nc * sizeof(double), s));
-  int ws = (int)vtc_splits(mr, nc, w.wcols, sms);
+  int ws = (int)vtc_splits(mr, nc, w.wcols, sms, 1);
   if ((st = tc_gemm16(w.vch, w.vcl, w.ldv, C, nullptr, ld, cs->bound + J + nbo, last ? cs->acc + J + nbo : nullptr,
                       kNB, nc, mr, 1.f / (float)(1 << kVExp16), w.wp, kNB, (int64_t)kNB * nc, ws, f->status, s,
                       &ws)) != CT_OK) {
@@ -1215,7 +1215,7 @@ ct_status outer_update256_16(ct_factor* f, int64_t J, int nbo_b, float* work, si
   // read and split once per slice
   float* C = F + J + (J + nbo) * ld;
   CT_CUDA_TRY(cudaMemsetAsync(cs->acc + J + nbo, 0, (size_t)nc * sizeof(double), s));
-  int ws = (int)vtc_splits(mr, nc, w.wcols, sms);
+  int ws = (int)vtc_splits(mr, nc, w.wcols, sms, tc_gemm16_m_ctas(kW));
   if ((st = tc_gemm16(w.vch, w.vcl, w.ldv, C, nullptr, ld, cs->bound + J + nbo, cs->acc + J + nbo, kW, nc, mr,
                       1.f / (float)(1 << kVExp16), w.wp, kW, (int64_t)kW * nc, ws, f->status, s, &ws)) != CT_OK) {
     if (side) cudaStreamWaitEvent(s, la->ev_t, 0);

@@ -24,8 +24,9 @@
 //                  (two TMEM accumulators sharing each B slice, so B is read
 //                  once for up to 256 reflectors).  B (K x N) is either
 //                  pre-split or FP32, split in shared memory by four converter
-//                  warps with its per-column scale.  K slices of 32 elements
-//                  (64-byte rows, 64-byte swizzle), TMEM accumulation
+//                  warps with its per-column scale into a two-slot ring beside
+//                  the TMA ring.  K slices of 32 elements (64-byte rows,
+//                  64-byte swizzle), TMEM accumulation
 //                  restarted every 256 rows and the chunks summed on the CUDA
 //                  cores (the tensor cores' FP32 sums truncate).
 //   k_tc_update16  C (M x N) -= A^T B with both operands pre-split, K <= 256:
@@ -109,23 +110,30 @@ struct G16Args {
 // MMA issuer, 2 .. 2 + 4 MT - 1 drain the accumulators (warps 2-5 also split
 // raw B slices).
 template <int MT, bool BRAW, int STAGES>
-__global__ void __launch_bounds__(64 + 128 * MT, 1)
+__global__ void __launch_bounds__(64 + 128 * MT, 1) __maxnreg__(MT == 2 ? 200 : 255)
     k_tc_gemm16(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, G16Args args) {
-  constexpr uint32_t A_OFF = 0;                        // [mt][h, l] tiles
-  constexpr uint32_t B_OFF = MT * 2 * kT16;            // B h, B l
-  constexpr uint32_t R_OFF = B_OFF + 2 * kT16;         // raw B (BRAW)
-  constexpr uint32_t STAGE_BYTES = R_OFF + (BRAW ? kTRaw : 0);
-  constexpr uint32_t TX_BYTES = MT * 2 * kT16 + (BRAW ? kTRaw : 2 * kT16);
+  // Operand ring (STAGES deep): A's [mt][h, l] tiles, then B's FP16 h, l
+  // tiles, or for raw B its FP32 slice.  Raw B is split into a separate
+  // two-slot ring of FP16 h, l tiles, so the deep ring holds only what TMA
+  // loads (more slices in flight for the same shared memory).
+  constexpr uint32_t A_OFF = 0;
+  constexpr uint32_t B_OFF = MT * 2 * kT16;            // B h, B l (pre-split B)
+  constexpr uint32_t R_OFF = MT * 2 * kT16;            // raw B (BRAW)
+  constexpr uint32_t STAGE_BYTES = MT * 2 * kT16 + (BRAW ? kTRaw : 2 * kT16);
+  constexpr uint32_t TX_BYTES = STAGE_BYTES;
+  constexpr uint32_t HL_BYTES = BRAW ? 2 * (2 * kT16) : 0;
   constexpr uint32_t TMEM_COLS = 2 * MT * kBN;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  unsigned char* hl = smem + STAGES * STAGE_BYTES;     // [2][h, l] split raw B slices
+  uint64_t* full = (uint64_t*)(hl + HL_BYTES);
   uint64_t* conv = full + STAGES;
   uint64_t* empty = conv + STAGES;
   uint64_t* tfull = empty + STAGES;  // [2] a chunk's MMAs are done in TMEM buffer b
   uint64_t* tempty = tfull + 2;      // [2] every drain warp has read buffer b
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* hlempty = tempty + 2;    // [2] the MMAs have read split slot h
+  uint32_t* tmem_slot = (uint32_t*)(hlempty + 2);
   float* colinv = (float*)(tmem_slot + 4);  // [kBN] 1 / (per-column scale of raw B)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -163,6 +171,7 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 4 * MT);
+      mbar_init(&hlempty[b], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -219,7 +228,8 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1)
         if (!mbar_wait(BRAW ? &conv[s] : &full[s], (uint32_t)(u & 1), args.status)) break;
         tc_fence_after();
         unsigned char* st = smem + s * STAGE_BYTES;
-        const uint64_t dbh = sdesc_sw64(st + B_OFF), dbl = sdesc_sw64(st + B_OFF + kT16);
+        unsigned char* bt = BRAW ? hl + (kt & 1) * (2 * kT16) : st + B_OFF;
+        const uint64_t dbh = sdesc_sw64(bt), dbl = sdesc_sw64(bt + kT16);
 #pragma unroll
         for (int kk = 0; kk < kBK / 16; ++kk) {
           const uint64_t adv = (uint64_t)(kk * 2);  // 16 FP16 = 32 bytes = 2 x 16 B
@@ -234,6 +244,7 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1)
           }
         }
         mma_commit(&empty[s]);
+        if (BRAW) mma_commit(&hlempty[kt & 1]);
         if (kt % CH == CH - 1 || kt == nk - 1) mma_commit(&tfull[b]);
       }
     }
@@ -270,11 +281,19 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1)
       for (int kt = 0; kt < nk && ok; ++kt) {
         const int s = kt % STAGES, u = kt / STAGES;
         if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)(u & 1), args.status))) { ok = false; break; }
+        // split slot kt & 1 must have been read by slice kt - 2's MMAs
+        if (kt >= 2 &&
+            !__all_sync(0xffffffffu, mbar_wait(&hlempty[kt & 1], (uint32_t)(((kt >> 1) - 1) & 1), args.status))) {
+          ok = false;
+          break;
+        }
         unsigned char* st = smem + s * STAGE_BYTES;
         const unsigned char* raw = st + R_OFF + t * 128;
-        unsigned char* bh = st + B_OFF + t * 64;
-        unsigned char* bl = st + B_OFF + kT16 + t * 64;
-#pragma unroll
+        unsigned char* bh = hl + (kt & 1) * (2 * kT16) + t * 64;
+        unsigned char* bl = bh + kT16;
+        // one 16-byte output chunk at a time: few live registers beside the
+        // 128 accumulators these threads also hold
+#pragma unroll 1
         for (int q = 0; q < 4; ++q) {
           const float4 x0 = *(const float4*)(raw + (((2 * q) ^ sw_in) << 4));
           const float4 x1 = *(const float4*)(raw + (((2 * q + 1) ^ sw_in) << 4));
@@ -309,12 +328,13 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1)
     while (next < nch && ok) ok = drain(next++);
     if (ok) {
       const int64_t row = m0 + mt * kBM + lg * 32 + lane;
-      float* C = args.C + (int64_t)blockIdx.z * args.split_stride;
       if (row < args.M) {
+        const int nv = (int)(args.N - n0 < kBN ? args.N - n0 : kBN);
+        float* p = args.C + (int64_t)blockIdx.z * args.split_stride + row + n0 * args.ldc;
 #pragma unroll
         for (int j = 0; j < kBN; ++j) {
-          const int64_t col = n0 + j;
-          if (col < args.N) C[row + col * args.ldc] = acc[j] * args.out_scale * colinv[j];
+          if (j < nv) *p = acc[j] * args.out_scale * colinv[j];
+          p += args.ldc;
         }
       }
     }
@@ -620,8 +640,9 @@ bool make_map16(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int es
 
 template <int MT, bool BRAW, int STAGES>
 ct_status launch_g16(const CUtensorMap* maps, const G16Args& a, int splits, cudaStream_t s) {
-  constexpr size_t STAGE_BYTES = (size_t)MT * 2 * kT16 + 2 * kT16 + (BRAW ? kTRaw : 0);
-  const size_t smem = STAGES * STAGE_BYTES + 1024 + 256 + kBN * sizeof(float);
+  constexpr size_t STAGE_BYTES = (size_t)MT * 2 * kT16 + (BRAW ? kTRaw : 2 * kT16);
+  constexpr size_t HL_BYTES = BRAW ? 4 * kT16 : 0;
+  const size_t smem = STAGES * STAGE_BYTES + HL_BYTES + 1024 + 256 + kBN * sizeof(float);
   static bool attr_done = false;
   if (!attr_done) {
     CT_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm16<MT, BRAW, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -696,9 +717,18 @@ ct_status tc_gemm16(const __half* Ah, const __half* Al, int64_t lda, const void*
   a.status = status;
   if (made) *made = splits;
   LaunchScope ls(K_TC_GEMM, s, 2.0 * M * N * K, 4.0 * (double)K * (M + N) + 4.0 * M * N * splits);
+  // Two M tiles per CTA when M > 128: C is read and split once for all 256
+  // reflectors (one M tile per CTA was measured 1.6x slower on a 50,000 x
+  // 12,544 x 256 product, although the 10-warp CTA is capped at 168
+  // registers and spills a little in its split warps)
   const bool two = M > kBM;
-  if (braw) return two ? launch_g16<2, true, 3>(maps, a, splits, s) : launch_g16<1, true, 4>(maps, a, splits, s);
+  if (braw) return two ? launch_g16<2, true, 4>(maps, a, splits, s) : launch_g16<1, true, 6>(maps, a, splits, s);
   return two ? launch_g16<2, false, 4>(maps, a, splits, s) : launch_g16<1, false, 6>(maps, a, splits, s);
+}
+
+int tc_gemm16_m_ctas(int64_t M) {
+  const int per = M > kBM ? 2 * kBM : kBM;
+  return (int)((M + per - 1) / per);
 }
 
 // C (M x N) -= A^T B on pre-split operands (Ah/Al: K x M, Bh/Bl: K x N, FP16

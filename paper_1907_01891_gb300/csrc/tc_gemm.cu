@@ -282,10 +282,13 @@ struct UpdArgs {
 // of V (up to 0.28 GB) for every column tile.
 __device__ __forceinline__ void update_tile(int64_t t, int64_t mtiles, int64_t ntiles, int64_t G, int64_t& m0,
                                             int64_t& n0) {
-  const int64_t band = t / (G * ntiles), local = t - band * G * ntiles;
-  const int64_t rows = mtiles - band * G < G ? mtiles - band * G : G;
-  m0 = (band * G + local % rows) * kBM;
-  n0 = (local / rows) * kBM;
+  // 32-bit index arithmetic (the host keeps the tile count below 2^31):
+  // 64-bit divisions cost more than the rest of a tile's epilogue
+  const uint32_t tt = (uint32_t)t, g = (uint32_t)G, nt = (uint32_t)ntiles, mt = (uint32_t)mtiles;
+  const uint32_t band = tt / (g * nt), local = tt - band * g * nt;
+  const uint32_t rows = mt - band * g < g ? mt - band * g : g;
+  m0 = (int64_t)(band * g + local % rows) * kBM;
+  n0 = (int64_t)(local / rows) * kBM;
 }
 
 template <bool SPLIT3, int STAGES>
@@ -399,15 +402,17 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     // tile waits for its accumulator and is stored
     const int et = threadIdx.x - 128;
     float* cbuf = (float*)(smem + STAGES * STAGE_BYTES + 256);
+    const int64_t ldc = args.ldc;
     auto prefetch = [&](int64_t t) {
       int64_t m0, n0;
       update_tile(t, args.mtiles, args.ntiles, gridDim.x, m0, n0);
       const int64_t row = m0 + lg * 32 + lane, c0 = n0 + half * 64;
-      const bool rok = row < args.M;
+      const int nv = row < args.M ? (int)(args.N - c0 < 64 ? args.N - c0 : 64) : 0;
+      const float* p = args.C + row + c0 * ldc;
 #pragma unroll 16
       for (int j = 0; j < 64; ++j) {
-        const bool v = rok && c0 + j < args.N;
-        cp_async_f32(cbuf + j * 256 + et, v ? args.C + row + (c0 + j) * args.ldc : args.C, v);
+        cp_async_f32(cbuf + j * 256 + et, j < nv ? p : args.C, j < nv);
+        p += ldc;
       }
       cp_async_commit();
     };
@@ -441,9 +446,13 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
       if (rok) {
+        const int nv = (int)(args.N - c0 < 64 ? args.N - c0 : 64);
+        float* p = args.C + row + c0 * ldc;
 #pragma unroll
-        for (int j = 0; j < 64; ++j)
-          if (c0 + j < args.N) args.C[row + (c0 + j) * args.ldc] = c[j];
+        for (int j = 0; j < 64; ++j) {
+          if (j < nv) *p = c[j];
+          p += ldc;
+        }
       }
     }
   }
@@ -555,6 +564,7 @@ ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, cons
   a.ldc = ldc;
   a.mtiles = (M + kBM - 1) / kBM;
   a.ntiles = (N + kBM - 1) / kBM;
+  if (a.mtiles * a.ntiles + sms > INT32_MAX) return CT_ERR_INVALID;  // 32-bit tile indices
   a.status = status;
   LaunchScope ls(K_TC_UPDATE, s, 2.0 * M * N * K, 4.0 * ((double)K * (M + N) * (split3 ? 2 : 1) + 2.0 * M * N));
   if (split3) return launch_upd<true, 2>(maps, a, sms, s);

@@ -158,3 +158,88 @@ def test_mixed_precision_batch_matches_oracle_and_keeps_A():
         X = Bt.cpu().numpy()[:n]
         Xo = O.lstsq(Asys, b)
         assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10, n
+
+@pytest.mark.slow
+def test_largest_uneven_batch_system_solves_its_normal_equations():
+    """The largest system of the 64-system uneven batch (96^2 image, [A; 1e-3 I],
+    26752 x 9216) in one persistent launch beside the smallest.  Its oracle
+    solution takes minutes on the host cores, so it is held to a property
+    that holds at any size -- the FP64 normal equations of the oracle's own
+    system matrix, ||A^T (b - A x) - lam^2 x|| / (||A||_F^2 ||x||), at the
+    level of a backward-stable QR's backward error (20 sqrt(n) u = 2e-13 for
+    n = 9216; the tile runtime gives ~5e-14) -- and to the single-system FP64
+    path (whose
+    solutions match the oracle at smaller sizes); the smallest system is
+    compared with the oracle element by element."""
+    cfg = I.CONFIG4B
+    geoms = I.uneven_systems(cfg["count"], cfg["seed"])
+    order = sorted(range(len(geoms)), key=lambda q: geoms[q].m * geoms[q].n)
+    small, big = order[0], order[-1]
+    lam = cfg["lam"]
+    assert geoms[big].nx == 96
+    As, Bs, ref = [], [], []
+    for q in (small, big):
+        g = geoms[q]
+        Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+        b = np.vstack([Ao @ I.phantoms(g, [cfg["seed0"] + q]), np.zeros((g.n, 1))])
+        As.append(ctqr.build_system(g, torch.float64, lam=lam))
+        Bs.append(ctqr.to_colmajor(b))
+        ref.append((Ao, b, g))
+    st, rep = ctqr.qr_solve_batched(As, Bs, tile=0)
+    assert st == ctqr.CT_OK
+    torch.cuda.synchronize()
+    # smallest: the oracle's least-squares solution
+    Ao, b, g = ref[0]
+    Xs = Bs[0].cpu().numpy()[:g.n]
+    Xo = O.lstsq(np.vstack([Ao, lam * np.eye(g.n)]), b)
+    fro, elem = _rel_err(Xs, Xo)
+    assert fro <= 1e-10 and elem <= 1e-10, (fro, elem)
+    # largest: FP64 normal equations of the oracle's matrix
+    Ao, b, g = ref[1]
+    x = Bs[1].cpu().numpy()[:g.n]
+    r = b[:g.m] - Ao @ x
+    gres = Ao.T @ r - lam * lam * x
+    ne = np.linalg.norm(gres) / (np.linalg.norm(Ao) ** 2 * np.linalg.norm(x))
+    assert ne <= 2e-13, ne
+    # and the single-system FP64 path on the same system
+    Asys = ctqr.build_system(g, torch.float64, lam=lam)
+    f = ctqr.qr_factor(Asys)
+    X1, _ = ctqr.reconstruct(f, ctqr.to_colmajor(b))
+    torch.cuda.synchronize()
+    fro, elem = _rel_err(x, X1.cpu().numpy())
+    assert fro <= 1e-10 and elem <= 1e-10, (fro, elem)
+
+
+def _rel_err(X, Xo):
+    return (np.linalg.norm(X - Xo) / np.linalg.norm(Xo), np.abs(X - Xo).max() / np.abs(Xo).max())
+
+
+@pytest.mark.parametrize("pos", [4, 12])
+def test_tile32_factor_of_ct_systems_with_noise_level_columns_matches_oracle(pos):
+    """Two systems of the uneven batch (38^2 and 45^2 images, [A; 1e-3 I]) whose
+    32-wide tile factorization meets columns that are rounding remainders of
+    exact zeros, down to magnitudes where their sums of squares underflow:
+    R and the solution against the oracle (R up to row signs, relative to
+    max |R|, 1e-11; x 1e-10).  Built from such columns, the triangle-on-square
+    reflectors were not orthogonal and lost up to 2.6e-2 of R."""
+    cfg = I.CONFIG4B
+    geoms = I.uneven_systems(cfg["count"], cfg["seed"])
+    order = sorted(range(len(geoms)), key=lambda q: geoms[q].m * geoms[q].n)
+    q = order[pos]
+    g = geoms[q]
+    lam = cfg["lam"]
+    Ao = O.system_matrix(O.Geometry(*g.as_tuple()))
+    As = np.vstack([Ao, lam * np.eye(g.n)])
+    b = np.vstack([Ao @ I.phantoms(g, [cfg["seed0"] + q]), np.zeros((g.n, 1))])
+    Fo, _ = O.qr(As)
+    Ro = np.triu(Fo[:g.n])
+    Xo = O.lstsq(As, b)
+    At, Bt = ctqr.to_colmajor(As), ctqr.to_colmajor(b)
+    st, _ = ctqr.qr_solve_batched([At], [Bt], tile=32)
+    assert st == ctqr.CT_OK
+    torch.cuda.synchronize()
+    R = np.triu(At.cpu().numpy()[:g.n])
+    sg = np.sign(np.diag(R)) * np.sign(np.diag(Ro))
+    assert np.abs(R * sg[:, None] - Ro).max() <= 1e-11 * np.abs(Ro).max()
+    fro, elem = _rel_err(Bt.cpu().numpy()[:g.n], Xo)
+    assert fro <= 1e-10 and elem <= 1e-10, (fro, elem)
