@@ -187,6 +187,14 @@ typedef struct {
                   /* and refined to the FP64 least-squares solution by         */
                   /* ct_reconstruct_batch against its FP64 A, which is then    */
                   /* left unchanged                                            */
+  int no_cache;   /* CT_PREC_F64 only.  0 (default): the task list, the tile T  */
+                  /* blocks and the instantiated CUDA graph of this batch's     */
+                  /* sizes stay on the device after the call, and the next call */
+                  /* with the same sizes and leading dimensions (any pointers)  */
+                  /* only uploads the pointers and replays the graph; one shape */
+                  /* is kept per process, released by the next shape or by     */
+                  /* ct_qr_solve_batched_release.  1: everything is released    */
+                  /* before the call returns                                   */
 } ct_batch_opts;
 
 /* Optional report of ct_qr_solve_batched. */
@@ -368,9 +376,10 @@ ct_status ct_trsm_solve(const ct_factor* f, double* B, int64_t ldb, int64_t k,
  * CT_PREC_F32 / CT_PREC_TF32 factor; B is an FP32 device matrix, ldb >= n.
  * The paper's factor is FP64 and has no counterpart; the operation is the
  * back substitution of Sec. II-C-4 at lower precision.  For k <= 64 one
- * persistent launch per 32 columns walks the 128-row block rows in
- * dependency order, each block row finished by a product with its inverted
- * diagonal block; wider B uses recursive halving with one product per split.
+ * persistent launch walks the 128-row block rows in dependency order (each
+ * block of R read once for all k columns), each block row finished by a
+ * product with its inverted diagonal block; wider B uses recursive halving
+ * with one product per split.
  * CT_ERR_UNSUPPORTED for an FP64 factor. */
 ct_status ct_trsm_solve_f32(const ct_factor* f, float* B, int64_t ldb, int64_t k, int transpose,
                             void* stream);
@@ -465,13 +474,20 @@ uint64_t ct_kernel_launches(void);
  * tasks_qr_ab), then X_s = R_s^{-1}(Q_s^T B_s) by the solve tasks of Table
  * tasks_solve_ab (the two Apply tasks on B, Trsm_lunn, Gemm_nn_mo).  The tasks
  * of all systems share one device work queue consumed by one CTA per SM, with
- * per-tile version counters ordering them (bounded waits); the launch is
- * recorded and replayed as a CUDA graph.  FP64 throughout.  `systems` is a host
+ * per-tile version counters ordering them (bounded waits); the task list is
+ * built on the host and uploaded once per batch shape, and the upload of the
+ * systems' pointers, the counter resets and the launch form one CUDA graph,
+ * instantiated once per shape and replayed by later calls of that shape (see
+ * ct_batch_opts.no_cache).  FP64 throughout.  `systems` is a host
  * array; A_s and B_s are overwritten.  Synchronous: returns when done, with
  * CT_ERR_RANK / CT_ERR_NONFINITE / CT_ERR_TIMEOUT if any system hit one.
  * Stack lambda*I under a rank-deficient A with ct_build_system. */
 ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const ct_batch_opts* opts,
                               ct_batch_report* report, void* stream);
+/* Free the device memory (task list, tile T blocks, counters) and the CUDA
+ * graph that ct_qr_solve_batched keeps for the last batch shape; the next call
+ * plans again.  Safe to call at any time, also when nothing is kept. */
+void ct_qr_solve_batched_release(void);
 
 /* A factor kept beyond the process.  The paper computes the factorization
  * once and stores it so that every later batch of slices reuses it (Sec.

@@ -1221,7 +1221,8 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
   CT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
   double ms = 0.0;
   int ntasks = 0;
-  if ((st = run_batch(count, systems, tile, di.sms, status, s, &ms, &ntasks)) != CT_OK) return st;
+  if ((st = run_batch(count, systems, tile, di.sms, status, s, !(opts && opts->no_cache), &ms, &ntasks)) != CT_OK)
+    return st;
   // Rank test on every R (same threshold as ct_qr_factor).
   for (int i = 0; i < count; ++i) {
     ct_factor tmp;
@@ -1245,6 +1246,8 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
   }
   return (ct_status)h;
 }
+
+void ct_qr_solve_batched_release(void) { release_batch_cache(); }
 
 void ct_factor_destroy(ct_factor* f) {
   if (!f) return;

@@ -221,7 +221,7 @@ ct_status tuned_batch_tile(int64_t m, int64_t n, int sms, cudaStream_t s, int* t
     cudaMemsetAsync(status, 0, sizeof(int), s);
     ct_batch_system sys = {m, n, A, lda, nullptr, m, 0};
     double ms = 0.0;
-    st = run_batch(1, &sys, cand, sms, status, s, &ms);
+    st = run_batch(1, &sys, cand, sms, status, s, false, &ms);
     if (st != CT_OK) break;
     if (ms < best_ms) { best_ms = ms; best = cand; }
   }

@@ -353,9 +353,13 @@ ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, cons
 
 // ---- batched tile QR (tile_qr.cu) and its autotuner (autotune.cu) --------
 // Factor and solve `count` systems with the tile-task runtime, tile b = 32 or
-// 64; *ms_out receives the device time of the persistent launch.
+// 64; *ms_out receives the device time of the persistent launch.  keep: the
+// task list, T blocks and instantiated graph stay on the device for the next
+// call with the same sizes (one shape per process; release_batch_cache frees
+// it); otherwise everything is released before returning.
 ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int* status, cudaStream_t s,
-                    double* ms_out, int* tasks_out = nullptr);
+                    bool keep, double* ms_out, int* tasks_out = nullptr);
+void release_batch_cache();
 // Tile tasks the batch would hold with tile size b (each task is ~100 bytes
 // of host and device memory).
 int64_t batch_task_count(int count, const ct_batch_system* in, int b);

@@ -28,7 +28,8 @@
 //                  the TMA ring.  K slices of 32 elements (64-byte rows,
 //                  64-byte swizzle), TMEM accumulation
 //                  restarted every 256 rows and the chunks summed on the CUDA
-//                  cores (the tensor cores' FP32 sums truncate).
+//                  cores (the tensor cores' FP32 sums truncate) by drain
+//                  warps, two warpgroups per M tile when B is raw.
 //   k_tc_update16  C (M x N) -= A^T B with both operands pre-split, K <= 256:
 //                  persistent, warp-specialised, double-buffered TMEM, C
 //                  prefetched by the epilogue warps; per-column inverse
@@ -63,6 +64,17 @@ __device__ __forceinline__ float split16(float x, float s, __half& h, __half& l)
   h = __float2half_rn(xs);
   l = __float2half_rn(xs - __half2float(h));
   return xs;
+}
+
+// Eight consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
@@ -106,11 +118,18 @@ struct G16Args {
   int* status;
 };
 
+// Threads of k_tc_gemm16: DW = 1 drains each M tile's 128 columns with one
+// warpgroup (whose first four warps also split raw B); DW = 2 drains them with
+// two warpgroups of 64 columns each, beside four warps that only split.
+__host__ __device__ constexpr int g16_threads(int MT, int DW) { return DW == 1 ? 64 + 128 * MT : 192 + 128 * MT * DW; }
+
 // W = A^T B, see the file comment.  Warps: 0 TMA producer, 1 TMEM owner and
-// MMA issuer, 2 .. 2 + 4 MT - 1 drain the accumulators (warps 2-5 also split
-// raw B slices).
-template <int MT, bool BRAW, int STAGES>
-__global__ void __launch_bounds__(64 + 128 * MT, 1) __maxnreg__(MT == 2 ? 200 : 255)
+// MMA issuer; DW = 1: 2 .. 2 + 4 MT - 1 drain the accumulators (warps 2-5
+// also split raw B slices); DW = 2: 2-5 split raw B, 6 .. 6 + 8 MT - 1 drain
+// (64 accumulator columns each, so every thread fits in the smaller register
+// share of the larger CTA).
+template <int MT, bool BRAW, int STAGES, int DW>
+__global__ void __launch_bounds__(g16_threads(MT, DW), 1) __maxnreg__(DW == 2 ? 88 : (MT == 2 ? 200 : 255))
     k_tc_gemm16(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, G16Args args) {
   // Operand ring (STAGES deep): A's [mt][h, l] tiles, then B's FP16 h, l
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1) __maxnreg__(MT == 2 ? 200 : 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4 * MT);
+      mbar_init(&tempty[b], 4 * MT * DW);
       mbar_init(&hlempty[b], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -249,92 +268,113 @@ __global__ void __launch_bounds__(64 + 128 * MT, 1) __maxnreg__(MT == 2 ? 200 : 
       }
     }
   } else {
-    // warps 2 .. 2 + 4 MT - 1
-    const int mt = (warp - 2) >> 2;
-    const int lg = warp & 3;  // TMEM lanes 32 lg .. +31 = tile rows
-    float acc[kBN];
-#pragma unroll
-    for (int j = 0; j < kBN; ++j) acc[j] = 0.f;
-    int next = 0;  // next chunk to read out
-    bool ok = true;
-    auto drain = [&](int c) -> bool {
-      const int b = c & 1;
-      // warp-uniform decision: the TMEM loads below are .sync.aligned
-      if (!__all_sync(0xffffffffu, mbar_wait(&tfull[b], (uint32_t)((c >> 1) & 1), args.status))) return false;
-      tc_fence_after();
-#pragma unroll
-      for (int cc = 0; cc < kBN; cc += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)((b * MT + mt) * kBN + cc), v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[cc + j] += v[j];
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
-      return true;
-    };
-    if (BRAW && warp < 6) {
+    // DW = 1: warps 2 .. 2 + 4 MT - 1; DW = 2: converters 2-5, drains 6 ..
+    constexpr int D0 = DW == 1 ? 2 : 6;  // first drain warp
+    constexpr int NC = kBN / DW;         // accumulator columns per drain thread
+    // Split raw B slice kt into FP16 h, l parts (warps 2-5, thread t owns
+    // column n0 + t); false when a wait gave up.
+    auto convert = [&](int kt, float& ssq) -> bool {
       const int t = (warp - 2) * 32 + lane;
       const int sw_in = t & 7, sw_out = (t >> 1) & 3;
-      float ssq = 0.f;  // sum of the scaled column entries' squares (each below 2^28)
-      for (int kt = 0; kt < nk && ok; ++kt) {
-        const int s = kt % STAGES, u = kt / STAGES;
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)(u & 1), args.status))) { ok = false; break; }
-        // split slot kt & 1 must have been read by slice kt - 2's MMAs
-        if (kt >= 2 &&
-            !__all_sync(0xffffffffu, mbar_wait(&hlempty[kt & 1], (uint32_t)(((kt >> 1) - 1) & 1), args.status))) {
-          ok = false;
-          break;
-        }
-        unsigned char* st = smem + s * STAGE_BYTES;
-        const unsigned char* raw = st + R_OFF + t * 128;
-        unsigned char* bh = hl + (kt & 1) * (2 * kT16) + t * 64;
-        unsigned char* bl = bh + kT16;
-        // one 16-byte output chunk at a time: few live registers beside the
-        // 128 accumulators these threads also hold
+      const int s = kt % STAGES, u = kt / STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)(u & 1), args.status))) return false;
+      // split slot kt & 1 must have been read by slice kt - 2's MMAs
+      if (kt >= 2 &&
+          !__all_sync(0xffffffffu, mbar_wait(&hlempty[kt & 1], (uint32_t)(((kt >> 1) - 1) & 1), args.status)))
+        return false;
+      unsigned char* st = smem + s * STAGE_BYTES;
+      const unsigned char* raw = st + R_OFF + t * 128;
+      unsigned char* bh = hl + (kt & 1) * (2 * kT16) + t * 64;
+      unsigned char* bl = bh + kT16;
+      // one 16-byte output chunk at a time: few live registers beside the
+      // accumulators that DW = 1 converter threads also hold
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-          const float4 x0 = *(const float4*)(raw + (((2 * q) ^ sw_in) << 4));
-          const float4 x1 = *(const float4*)(raw + (((2 * q + 1) ^ sw_in) << 4));
-          __half h[8], l[8];
-          float xs[8];
-          xs[0] = split16(x0.x, bsc, h[0], l[0]);
-          xs[1] = split16(x0.y, bsc, h[1], l[1]);
-          xs[2] = split16(x0.z, bsc, h[2], l[2]);
-          xs[3] = split16(x0.w, bsc, h[3], l[3]);
-          xs[4] = split16(x1.x, bsc, h[4], l[4]);
-          xs[5] = split16(x1.y, bsc, h[5], l[5]);
-          xs[6] = split16(x1.z, bsc, h[6], l[6]);
-          xs[7] = split16(x1.w, bsc, h[7], l[7]);
-          if (args.nrm2) {
+      for (int q = 0; q < 4; ++q) {
+        const float4 x0 = *(const float4*)(raw + (((2 * q) ^ sw_in) << 4));
+        const float4 x1 = *(const float4*)(raw + (((2 * q + 1) ^ sw_in) << 4));
+        __half h[8], l[8];
+        float xs[8];
+        xs[0] = split16(x0.x, bsc, h[0], l[0]);
+        xs[1] = split16(x0.y, bsc, h[1], l[1]);
+        xs[2] = split16(x0.z, bsc, h[2], l[2]);
+        xs[3] = split16(x0.w, bsc, h[3], l[3]);
+        xs[4] = split16(x1.x, bsc, h[4], l[4]);
+        xs[5] = split16(x1.y, bsc, h[5], l[5]);
+        xs[6] = split16(x1.z, bsc, h[6], l[6]);
+        xs[7] = split16(x1.w, bsc, h[7], l[7]);
+        if (args.nrm2) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) ssq = fmaf(xs[u], xs[u], ssq);
-          }
-          const int o = (q ^ sw_out) << 4;
-          *(uint4*)(bh + o) = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-          *(uint4*)(bl + o) = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+          for (int v = 0; v < 8; ++v) ssq = fmaf(xs[v], xs[v], ssq);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&conv[s]);
-        // the chunk before the one this slice completes is long done
-        if (kt % CH == CH - 1)
-          while (next < kt / CH && ok) ok = drain(next++);
+        const int o = (q ^ sw_out) << 4;
+        *(uint4*)(bh + o) = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+        *(uint4*)(bl + o) = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
       }
-      if (args.nrm2 && ok && ssq > 0.f && n0 + t < args.N)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+      return true;
+    };
+    // the sum of squares of column n0 + t, back at its original scale
+    auto add_nrm2 = [&](float ssq) {
+      const int t = (warp - 2) * 32 + lane;
+      if (args.nrm2 && ssq > 0.f && n0 + t < args.N)
         atomicAdd(args.nrm2 + n0 + t, (double)ssq * (double)inv * (double)inv);
-    }
-    while (next < nch && ok) ok = drain(next++);
-    if (ok) {
-      const int64_t row = m0 + mt * kBM + lg * 32 + lane;
-      if (row < args.M) {
-        const int nv = (int)(args.N - n0 < kBN ? args.N - n0 : kBN);
-        float* p = args.C + (int64_t)blockIdx.z * args.split_stride + row + n0 * args.ldc;
+    };
+    if (DW == 2 && BRAW && warp < 6) {
+      float ssq = 0.f;
+      bool ok = true;
+      for (int kt = 0; kt < nk && ok; ++kt) ok = convert(kt, ssq);
+      if (ok) add_nrm2(ssq);
+    } else {
+      const int g = (warp - D0) >> 2;
+      const int mt = g / DW, c0 = (g % DW) * NC;
+      const int lg = warp & 3;  // TMEM lanes 32 lg .. +31 = tile rows
+      float acc[NC];
 #pragma unroll
-        for (int j = 0; j < kBN; ++j) {
-          if (j < nv) *p = acc[j] * args.out_scale * colinv[j];
-          p += args.ldc;
+      for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+      int next = 0;  // next chunk to read out
+      bool ok = true;
+      auto drain = [&](int c) -> bool {
+        const int b = c & 1;
+        // warp-uniform decision: the TMEM loads below are .sync.aligned
+        if (!__all_sync(0xffffffffu, mbar_wait(&tfull[b], (uint32_t)((c >> 1) & 1), args.status))) return false;
+        tc_fence_after();
+        constexpr int LW = DW == 1 ? 16 : 8;  // columns per TMEM load
+#pragma unroll
+        for (int cc = 0; cc < NC; cc += LW) {
+          float v[LW];
+          const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)((b * MT + mt) * kBN + c0 + cc);
+          if (LW == 16) tmem_ld16(ta, v); else tmem_ld8(ta, v);
+#pragma unroll
+          for (int j = 0; j < LW; ++j) acc[cc + j] += v[j];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+        return true;
+      };
+      if (DW == 1 && BRAW && warp < 6) {
+        float ssq = 0.f;
+        for (int kt = 0; kt < nk && ok; ++kt) {
+          ok = convert(kt, ssq);
+          // the chunk before the one this slice completes is long done
+          if (ok && kt % CH == CH - 1)
+            while (next < kt / CH && ok) ok = drain(next++);
+        }
+        if (ok) add_nrm2(ssq);
+      }
+      while (next < nch && ok) ok = drain(next++);
+      if (ok) {
+        const int64_t row = m0 + mt * kBM + lg * 32 + lane;
+        if (row < args.M) {
+          const int nv = (int)(args.N - n0 < kBN ? args.N - n0 : kBN) - c0;
+          float* p = args.C + (int64_t)blockIdx.z * args.split_stride + row + (n0 + c0) * args.ldc;
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            if (j < nv) *p = acc[j] * args.out_scale * colinv[c0 + j];
+            p += args.ldc;
+          }
         }
       }
     }
@@ -638,20 +678,20 @@ bool make_map16(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int es
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MT, bool BRAW, int STAGES>
+template <int MT, bool BRAW, int STAGES, int DW = 1>
 ct_status launch_g16(const CUtensorMap* maps, const G16Args& a, int splits, cudaStream_t s) {
   constexpr size_t STAGE_BYTES = (size_t)MT * 2 * kT16 + (BRAW ? kTRaw : 2 * kT16);
   constexpr size_t HL_BYTES = BRAW ? 4 * kT16 : 0;
   const size_t smem = STAGES * STAGE_BYTES + HL_BYTES + 1024 + 256 + kBN * sizeof(float);
   static bool attr_done = false;
   if (!attr_done) {
-    CT_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm16<MT, BRAW, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CT_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm16<MT, BRAW, STAGES, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     attr_done = true;
   }
   const dim3 grid((unsigned)((a.M + kBM * MT - 1) / (kBM * MT)), (unsigned)((a.N + kBN - 1) / kBN),
                   (unsigned)splits);
-  k_tc_gemm16<MT, BRAW, STAGES><<<grid, 64 + 128 * MT, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+  k_tc_gemm16<MT, BRAW, STAGES, DW><<<grid, g16_threads(MT, DW), smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
   CT_LAUNCH_CHECK();
   return CT_OK;
 }
@@ -719,10 +759,12 @@ ct_status tc_gemm16(const __half* Ah, const __half* Al, int64_t lda, const void*
   LaunchScope ls(K_TC_GEMM, s, 2.0 * M * N * K, 4.0 * (double)K * (M + N) + 4.0 * M * N * splits);
   // Two M tiles per CTA when M > 128: C is read and split once for all 256
   // reflectors (one M tile per CTA was measured 1.6x slower on a 50,000 x
-  // 12,544 x 256 product, although the 10-warp CTA is capped at 168
-  // registers and spills a little in its split warps)
+  // 12,544 x 256 product).  With raw B, four warps only split and two
+  // warpgroups per M tile drain 64 columns each (DW = 2): the V^T C class of
+  // the 256 x 256 system's factorization fell from 1.81 s to 1.48 s against
+  // DW = 1, whose split warps also hold 128 accumulators and spill.
   const bool two = M > kBM;
-  if (braw) return two ? launch_g16<2, true, 4>(maps, a, splits, s) : launch_g16<1, true, 6>(maps, a, splits, s);
+  if (braw) return two ? launch_g16<2, true, 4, 2>(maps, a, splits, s) : launch_g16<1, true, 6>(maps, a, splits, s);
   return two ? launch_g16<2, false, 4>(maps, a, splits, s) : launch_g16<1, false, 6>(maps, a, splits, s);
 }
 

@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(1024) k_rank_check(const S* __restrict__ F, in
 constexpr int kPB = 64;          // most right-hand sides for the persistent solve
 constexpr int kQB = 128;         // block rows
 constexpr int kQT = 512;         // threads per CTA
-constexpr int kQK = 32;          // right-hand sides per launch
+constexpr int kQK = 64;          // right-hand sides per launch (every R block read once for all)
+constexpr int kQP = 32;          // right-hand sides per pass of the partial products
 constexpr int kQG = kQT / kQB;   // column groups of the block operand (4)
 constexpr int kQL = kQB / kQG;   // columns per group (32)
 constexpr int kQS = kQB + 1;     // stride of the 128 x 128 shared tiles
@@ -232,16 +233,18 @@ __device__ __forceinline__ void row_partials(const float (&a)[kQL], const float*
     }
   }
 #pragma unroll
-  for (int c = 0; c < 4 * NC4; ++c) Ps[(g * kQK + c) * kQB + r] = acc[c];
+  for (int c = 0; c < 4 * NC4; ++c) Ps[(g * kQP + c) * kQB + r] = acc[c];
 }
 
 // The four partials of entry (r, c), summed in a fixed order.
 __device__ __forceinline__ float sum_parts(const float* __restrict__ Ps, int r, int c) {
-  return ((Ps[c * kQB + r] + Ps[(kQK + c) * kQB + r]) + Ps[(2 * kQK + c) * kQB + r]) +
-         Ps[(3 * kQK + c) * kQB + r];
+  return ((Ps[c * kQB + r] + Ps[(kQP + c) * kQB + r]) + Ps[(2 * kQP + c) * kQB + r]) +
+         Ps[(3 * kQP + c) * kQB + r];
 }
 
-template <bool TRANS, int NC4>
+// NH passes of 4 NC4 right-hand sides each (NH = 2: up to 64 columns, every
+// staged R block used for both passes).
+template <bool TRANS, int NC4, int NH>
 __global__ void __launch_bounds__(kQT, 1) k_trsm_persist(const float* __restrict__ F, int64_t ld, int64_t n,
                                                          float* __restrict__ B, int64_t ldb, int k,
                                                          int* __restrict__ flags, int* __restrict__ ticket,
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(kQT, 1) k_trsm_persist(const float* __restrict
   __shared__ int s_t, s_fail;
   const int tid = threadIdx.x, r = tid % kQB, g = tid / kQB;
   const int nb = (int)((n + kQB - 1) / kQB);
-  constexpr int kc4 = 4 * NC4;   // columns carried (>= k)
+  constexpr int kc4 = 4 * NC4 * NH;  // columns carried (>= k)
   for (;;) {
     if (tid == 0) {
       s_t = atomicAdd(ticket, 1);
@@ -340,21 +343,28 @@ __global__ void __launch_bounds__(kQT, 1) k_trsm_persist(const float* __restrict
       }
       if (q + 1 < deps) stage(q + 1);
       __syncthreads();
-      row_partials<NC4>(a, Xs, Ps, r, g, true);
-      __syncthreads();
-      for (int e = tid; e < kQB * kc4; e += kQT) {
-        const int rr = e % kQB, c = e / kQB;
-        Ys[rr * kXS + c] -= sum_parts(Ps, rr, c);
+#pragma unroll 1
+      for (int h = 0; h < NH; ++h) {
+        if (h > 0) __syncthreads();  // the previous pass's partials are consumed
+        row_partials<NC4>(a, Xs + h * kQP, Ps, r, g, true);
+        __syncthreads();
+        for (int e = tid; e < kQB * 4 * NC4; e += kQT) {
+          const int rr = e % kQB, c = e / kQB;
+          Ys[rr * kXS + h * kQP + c] -= sum_parts(Ps, rr, c);
+        }
       }
     }
     __syncthreads();  // Y_i complete
-    row_partials<NC4>(d, Ys, Ps, r, g, live);
-    __syncthreads();
-    for (int e = tid; e < kQB * kc4; e += kQT) {
-      const int rr = e % kQB, c = e / kQB;
-      if (rr < ni && c < k) B[i0 + rr + (int64_t)c * ldb] = sum_parts(Ps, rr, c);
+#pragma unroll 1
+    for (int h = 0; h < NH; ++h) {
+      row_partials<NC4>(d, Ys + h * kQP, Ps, r, g, live);
+      __syncthreads();
+      for (int e = tid; e < kQB * 4 * NC4; e += kQT) {
+        const int rr = e % kQB, c = h * kQP + e / kQB;
+        if (rr < ni && c < k) B[i0 + rr + (int64_t)c * ldb] = sum_parts(Ps, rr, c - h * kQP);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (tid == 0) {
       __threadfence();
       st_release_i32(flags + i, 1);
@@ -449,12 +459,13 @@ bool persist_enabled() {
   return on;
 }
 
-// One persistent launch per group of up to 32 columns (FP32 R and B).
+// One persistent launch per group of up to 64 columns (FP32 R and B).
 template <bool TRANS>
 const void* persist_kernel(int kc) {
-  if (kc <= 8) return (const void*)k_trsm_persist<TRANS, 2>;
-  if (kc <= 16) return (const void*)k_trsm_persist<TRANS, 4>;
-  return (const void*)k_trsm_persist<TRANS, 8>;
+  if (kc <= 8) return (const void*)k_trsm_persist<TRANS, 2, 1>;
+  if (kc <= 16) return (const void*)k_trsm_persist<TRANS, 4, 1>;
+  if (kc <= 32) return (const void*)k_trsm_persist<TRANS, 8, 1>;
+  return (const void*)k_trsm_persist<TRANS, 8, 2>;
 }
 
 ct_status trsm_persist(const ct_factor* f, float* B, int64_t ldb, int64_t k, bool transpose, cudaStream_t s) {

@@ -82,7 +82,7 @@ class BatchSystem(ctypes.Structure):
 
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("prec", ctypes.c_int)]
+    _fields_ = [("tile", ctypes.c_int), ("prec", ctypes.c_int), ("no_cache", ctypes.c_int)]
 
 
 class BatchReport(ctypes.Structure):
@@ -139,6 +139,7 @@ SIGNATURES = {
     "ct_gemm_status": ([_VP], _I),
     "ct_qr_solve_batched": ([_I, ctypes.POINTER(BatchSystem), ctypes.POINTER(BatchOpts),
                              ctypes.POINTER(BatchReport), _VP], _I),
+    "ct_qr_solve_batched_release": ([], None),
     "ct_surrogate_init": ([ctypes.POINTER(Geometry), ctypes.POINTER(SurrogateOpts), ctypes.POINTER(_VP)], _I),
     "ct_surrogate_num_params": ([_VP], _I64),
     "ct_surrogate_params": ([_VP, _VP, _I], _I),
@@ -509,21 +510,28 @@ def gemm_f16x3_tn(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = Non
     return C
 
 
+def qr_solve_batched_release() -> None:
+    """Free what ct_qr_solve_batched keeps on the device for its last batch shape."""
+    load().ct_qr_solve_batched_release()
+
+
 def gemm_status() -> int:
     return load().ct_gemm_status(_stream())
 
 
-def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True, prec: Prec = Prec.F64):
+def qr_solve_batched(As, Bs, tile: int = 0, check: bool = True, prec: Prec = Prec.F64, cache: bool = True):
     """Factor and solve a batch of systems in place (lists of column-major
     FP64 CUDA tensors; Bs entries may be None).  Rows [0, n) of every B hold X
-    afterwards.  Returns (status, BatchReport)."""
+    afterwards.  cache=False releases the batch's task list and graph before
+    returning (ct_batch_opts.no_cache).  Returns (status, BatchReport)."""
     arr = (BatchSystem * len(As))()
     for q, (A, B) in enumerate(zip(As, Bs)):
         m, n = A.shape
         arr[q] = BatchSystem(m, n, A.data_ptr(), _ld(A), B.data_ptr() if B is not None else None,
                              _ld(B) if B is not None else m, B.shape[1] if B is not None else 0)
     rep = BatchReport()
-    st = load().ct_qr_solve_batched(len(As), arr, ctypes.byref(BatchOpts(tile, int(prec))), ctypes.byref(rep),
+    st = load().ct_qr_solve_batched(len(As), arr, ctypes.byref(BatchOpts(tile, int(prec), 0 if cache else 1)),
+                                    ctypes.byref(rep),
                                     _stream())
     if check:
         _check(st, "ct_qr_solve_batched")

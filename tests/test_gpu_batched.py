@@ -243,3 +243,37 @@ def test_tile32_factor_of_ct_systems_with_noise_level_columns_matches_oracle(pos
     assert np.abs(R * sg[:, None] - Ro).max() <= 1e-11 * np.abs(Ro).max()
     fro, elem = _rel_err(Bt.cpu().numpy()[:g.n], Xo)
     assert fro <= 1e-10 and elem <= 1e-10, (fro, elem)
+
+
+def test_repeat_calls_replay_the_kept_plan_with_new_buffers():
+    """Calls with the same sizes reuse the task list and graph kept on the
+    device: each call's systems sit in fresh buffers (new pointers) with new
+    data, and every result matches the oracle; a call with other sizes, a call
+    after ct_qr_solve_batched_release and an uncached call do too."""
+    shapes = [(300, 120, 2), (520, 333, 1), (97, 97, 3)]
+
+    def run(seed, shp, **kw):
+        As, Bs, ref = [], [], []
+        for q, (m, n, k) in enumerate(shp):
+            A = I.random_matrix(m, n, seed=seed + q)
+            B = I.random_matrix(m, k, seed=seed + 50 + q)
+            As.append(ctqr.to_colmajor(A))
+            Bs.append(ctqr.to_colmajor(B))
+            ref.append((A, B))
+        st, rep = ctqr.qr_solve_batched(As, Bs, tile=32, **kw)
+        assert st == ctqr.CT_OK
+        torch.cuda.synchronize()
+        for (A, B), Bt, (m, n, k) in zip(ref, Bs, shp):
+            X = Bt.cpu().numpy()[:n]
+            Xo = O.lstsq(A, B)
+            assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-10, (seed, m, n)
+        return rep.tasks
+
+    t0 = run(1000, shapes)
+    assert run(2000, shapes) == t0 and run(3000, shapes) == t0
+    run(4000, shapes[:2])
+    ctqr.qr_solve_batched_release()
+    assert run(5000, shapes) == t0
+    assert run(6000, shapes, cache=False) == t0
+    ctqr.qr_solve_batched_release()
+    ctqr.qr_solve_batched_release()

@@ -363,7 +363,7 @@ def test_lambda_stacked_scan_matches_oracle(prec):
     assert np.linalg.norm(X.numpy() - Xo) / np.linalg.norm(Xo) <= 1e-10, rep
 
 
-@pytest.mark.parametrize("n,k", [(200, 3), (1000, 17), (257, 70)])
+@pytest.mark.parametrize("n,k", [(200, 3), (1000, 17), (257, 70), (1300, 40), (700, 64)])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_fp32_triangular_solve_matches_oracle(n, k, transpose):
     """ct_trsm_solve_f32 (the refinement's preconditioner solve, one
