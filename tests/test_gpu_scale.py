@@ -7,7 +7,7 @@ columns and more than 32 block rows of the FP32 triangular solve, the
 one-launch Q^T, the fused inner updates, the Cholesky-QR panel, and noisy data
 (so the refinement goes to CGLS) -- and a tall system has the 135,232 rows of
 the lambda-stacked 256 x 256 system (the per-column panel, Q^T block by block,
-the three-kernel inner update).  Tolerance: the 1e-10 relative error of the
+the inner update streamed through shared memory in chunks of rows).  Tolerance: the 1e-10 relative error of the
 reconstruction target, on every element of X (max norm over the max of
 |X_oracle|) and in the Frobenius norm.  The oracle's solution of each system
 is computed once per module (it takes seconds on the host cores)."""
