@@ -71,12 +71,19 @@ def parse():
     return p.parse_args()
 
 
-# ncu DRAM traffic (read + write) over algorithmic bytes, per kernel class,
-# each from one capture of that kernel on a smaller case of the same shape
-# family (launch, rows, columns in the value); None: not captured since the
-# kernel last changed.  The roofline's traffic is this ratio times the
+# ncu DRAM traffic (read + write) over algorithmic bytes, per (kernel class,
+# precision), each from one capture of that kernel on a smaller case of the
+# same shape family (launch, rows, columns in the value); absent: not
+# captured since the kernel last changed.  The roofline's traffic is this ratio times the
 # dominant class's algorithmic bytes per launch.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {
+    # k_tc_update16<2>, C -= V W' of a 134,976 x 768 block with K = 256 (the
+    # ninth tensor-core update launch of `bench.py --probe 135232 1024`, C
+    # larger than L2): 562.1 MB read + 360.9 MB written against 968.3 MB of
+    # algorithmic bytes (C read and written once, FP16 operand parts once)
+    ("tc_update", "f16x3"): {"ratio": 922.946816 / 968.2944,
+                  "capture": "k_tc_update16 on a 134976 x 768 x 256 block (ncu --set full)"},
+}
 
 
 def qr_flops(m, n):
@@ -523,7 +530,7 @@ def roofline(dom, prec, ms_step, peaks):
     roof["launches_per_step"] = dom["launches"]
     roof["share_of_step"] = dom["ms"] / ms_step
     roof["timed_in"] = "one extra step with CUDA events around every launch of the class"
-    ratio = TRAFFIC_RATIO.get(name)
+    ratio = TRAFFIC_RATIO.get((name, prec))
     if ratio is not None and dom["launches"]:
         roof["traffic"] = ratio["ratio"] * dom["bytes"] / dom["launches"]
         roof["traffic_source"] = ("ncu dram read + write of " + ratio["capture"] +
