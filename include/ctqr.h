@@ -488,6 +488,23 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
  * graph that ct_qr_solve_batched keeps for the last batch shape; the next call
  * plans again.  Safe to call at any time, also when nothing is kept. */
 void ct_qr_solve_batched_release(void);
+/* The tile-task list ct_qr_solve_batched executes for these systems with tile
+ * size `tile` (32 or 64), built on the host only (no device work; the
+ * systems' A and B pointers are not read and may be NULL).  The tasks are the
+ * GEQRT / UNMQR / TSQRT / TSMQR tasks of Table tasks_qr_ab and the solve
+ * tasks of Table tasks_solve_ab in the order the persistent launch takes
+ * them.  Each task is 25 int32 in `tasks` (caller-owned, room for max_tasks
+ * records; NULL: only the counts): type (0 GEQRT, 1 UNMQR, 2 TSQRT, 3 TSMQR,
+ * 4 UNMQR on B, 5 TSMQR on B, 6 Trsm_lunn, 7 Gemm_nn_mo), system, i, j, k,
+ * the number of dependencies nd and of increments ni, then six dependency
+ * counters (-1 past nd), the six versions they must reach before the task
+ * runs, and six counters the task increments when done (-1 past ni).  Counter
+ * 2p counts the writes of tile part p, counter 2p + 1 its reads; *ntasks and
+ * *nparts (may be NULL) receive the task and part counts.  CT_ERR_INVALID
+ * for malformed systems or too small a buffer, CT_ERR_UNSUPPORTED beyond
+ * 2^31 - 1 tasks. */
+ct_status ct_batch_plan(int count, const ct_batch_system* systems, int tile, int32_t* tasks, int64_t max_tasks,
+                        int64_t* ntasks, int* nparts);
 
 /* A factor kept beyond the process.  The paper computes the factorization
  * once and stores it so that every later batch of slices reuses it (Sec.

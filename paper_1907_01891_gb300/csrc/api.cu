@@ -1249,6 +1249,16 @@ ct_status ct_qr_solve_batched(int count, const ct_batch_system* systems, const c
 
 void ct_qr_solve_batched_release(void) { release_batch_cache(); }
 
+ct_status ct_batch_plan(int count, const ct_batch_system* systems, int tile, int32_t* tasks, int64_t max_tasks,
+                        int64_t* ntasks, int* nparts) {
+  if (count < 1 || !systems) return CT_ERR_INVALID;
+  for (int i = 0; i < count; ++i) {
+    const ct_batch_system& q = systems[i];
+    if (q.n < 1 || q.m < q.n || q.lda < q.m || q.k < 0 || (q.k > 0 && q.ldb < q.m)) return CT_ERR_INVALID;
+  }
+  return export_batch_plan(count, systems, tile, tasks, max_tasks, ntasks, nparts);
+}
+
 void ct_factor_destroy(ct_factor* f) {
   if (!f) return;
   cudaDeviceSynchronize();

@@ -360,6 +360,11 @@ ct_status tc_update_presplit(const float* Ah, const float* Al, int64_t lda, cons
 ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int* status, cudaStream_t s,
                     bool keep, double* ms_out, int* tasks_out = nullptr);
 void release_batch_cache();
+// The task list plan_batch builds (host only): kPlanRecord int32 per task,
+// see ct_batch_plan in ctqr.h.
+constexpr int kPlanRecord = 25;
+ct_status export_batch_plan(int count, const ct_batch_system* in, int tile, int32_t* out, int64_t max_tasks,
+                            int64_t* ntasks, int* nparts);
 // Tile tasks the batch would hold with tile size b (each task is ~100 bytes
 // of host and device memory).
 int64_t batch_task_count(int count, const ct_batch_system* in, int b);

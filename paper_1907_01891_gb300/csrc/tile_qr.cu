@@ -610,7 +610,7 @@ void plan_batch(int count, const ct_batch_system* in, int b, double* T_base, Bat
     S.kt = (int)((S.k + b - 1) / b);
     S.A = in[s].A;
     S.B = in[s].B;
-    S.T = T_base + toff;
+    S.T = T_base ? T_base + toff : nullptr;  // none when only the task list is wanted
     toff += (size_t)S.mt * S.nt * b * b;
     SysParts& sp = P[s];
     sp.mt = S.mt; sp.nt = S.nt; sp.kt = S.kt;
@@ -920,6 +920,30 @@ ct_status run_batch(int count, const ct_batch_system* in, int tile, int sms, int
   if (tile == 32) return run_batch_t<32>(count, in, sms, status, s, keep, ms_out, tasks_out);
   if (tile == 64) return run_batch_t<64>(count, in, sms, status, s, keep, ms_out, tasks_out);
   return CT_ERR_INVALID;
+}
+
+ct_status export_batch_plan(int count, const ct_batch_system* in, int tile, int32_t* out, int64_t max_tasks,
+                            int64_t* ntasks, int* nparts) {
+  if (tile != 32 && tile != 64) return CT_ERR_INVALID;
+  if (batch_task_count(count, in, tile) > INT32_MAX) return CT_ERR_UNSUPPORTED;
+  BatchPlan plan;
+  plan_batch(count, in, tile, nullptr, &plan);
+  if (ntasks) *ntasks = (int64_t)plan.tasks.size();
+  if (nparts) *nparts = plan.parts;
+  if (!out) return CT_OK;
+  if (max_tasks < (int64_t)plan.tasks.size()) return CT_ERR_INVALID;
+  static_assert(kMaxDeps == 6 && kMaxIncs == 6, "the exported record holds 6 dependencies and 6 increments");
+  for (size_t q = 0; q < plan.tasks.size(); ++q) {
+    const TileTask& t = plan.tasks[q];
+    int32_t* r = out + q * kPlanRecord;
+    r[0] = t.type; r[1] = t.sys; r[2] = t.i; r[3] = t.j; r[4] = t.k; r[5] = t.nd; r[6] = t.ni;
+    for (int d = 0; d < kMaxDeps; ++d) {
+      r[7 + d] = d < t.nd ? t.dep_c[d] : -1;
+      r[13 + d] = d < t.nd ? t.dep_v[d] : 0;
+    }
+    for (int d = 0; d < kMaxIncs; ++d) r[19 + d] = d < t.ni ? t.inc_c[d] : -1;
+  }
+  return CT_OK;
 }
 
 void release_batch_cache() {

@@ -140,6 +140,8 @@ SIGNATURES = {
     "ct_qr_solve_batched": ([_I, ctypes.POINTER(BatchSystem), ctypes.POINTER(BatchOpts),
                              ctypes.POINTER(BatchReport), _VP], _I),
     "ct_qr_solve_batched_release": ([], None),
+    "ct_batch_plan": ([_I, ctypes.POINTER(BatchSystem), _I, _VP, _I64, ctypes.POINTER(_I64),
+                       ctypes.POINTER(_I)], _I),
     "ct_surrogate_init": ([ctypes.POINTER(Geometry), ctypes.POINTER(SurrogateOpts), ctypes.POINTER(_VP)], _I),
     "ct_surrogate_num_params": ([_VP], _I64),
     "ct_surrogate_params": ([_VP, _VP, _I], _I),
@@ -508,6 +510,23 @@ def gemm_f16x3_tn(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = Non
     _check(load().ct_gemm_f16x3_tn(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
                                    1 if accumulate else 0, _stream()), "ct_gemm_f16x3_tn")
     return C
+
+
+def batch_plan(shapes, tile: int):
+    """The tile-task list of ct_qr_solve_batched for systems of the given
+    (m, n, k) sizes (host only, no GPU): an int32 array of ntasks x 25
+    records (ct_batch_plan) and the number of tile parts."""
+    import numpy as np
+    arr = (BatchSystem * len(shapes))()
+    for q, (m, n, k) in enumerate(shapes):
+        arr[q] = BatchSystem(m, n, None, m, None, m, k)
+    nt, npart = ctypes.c_int64(0), ctypes.c_int(0)
+    lib = load()
+    _check(lib.ct_batch_plan(len(shapes), arr, tile, None, 0, ctypes.byref(nt), ctypes.byref(npart)), "ct_batch_plan")
+    out = np.zeros((nt.value, 25), dtype=np.int32)
+    _check(lib.ct_batch_plan(len(shapes), arr, tile, out.ctypes.data, nt.value, ctypes.byref(nt),
+                             ctypes.byref(npart)), "ct_batch_plan")
+    return out, npart.value
 
 
 def qr_solve_batched_release() -> None:
